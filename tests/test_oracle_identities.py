@@ -1,0 +1,157 @@
+"""Closed forms and brute-force identities that pin the oracle's walk, mapping,
+integration and finalization (Secs. 4.2-4.4)."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import synth
+
+SIGMA = 5.670374419e-5
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _leaf_L(t):
+    ex = t.export()
+    L = np.zeros(t.w.n_leaves)
+    m = ex["leaf"] >= 0
+    L[ex["leaf"][m]] = ex["vals"][m, 0]
+    return L, ex
+
+
+def test_no_extinction_theta0_equals_brute_force(orc):
+    """kappa_ext = 0, theta -> 0: every leaf is accepted; beta R_i^-2 = r^-2 and
+    sum_h alpha_h = 1, so J = sum_k L_k / (16 pi^2 r_k^2) (own cell at R_0 = dx/2) and
+    F = -sum_k L_k / (4 pi r_k^2) sum_h alpha_kh n^h, for any binning."""
+    w = synth.random_uniform(8, seed=3, thick_frac=0.0, kappa_ext_scale=0.0, theta=1e-9)
+    t = orc.Tree(w)
+    L, _ = _leaf_L(t)
+    n, dx = 8, w.box_cm / 8
+    cen = synth.cell_centres(n, w.box_cm)
+    nhat = np.array([orc.pix2vec(2, h) for h in range(48)])
+    targets = np.array([0, 73, 300, 511])
+    J, F = t.evaluate(targets)
+    for q, tk in enumerate(targets):
+        d = cen - cen[tk]
+        r2 = (d * d).sum(1)
+        r2[tk] = (0.5 * dx) ** 2
+        Jb = (L / (16 * math.pi ** 2 * r2)).sum()
+        assert math.isclose(J[q], Jb + t.leaves()["jsrc"][tk], rel_tol=1e-12)
+        Fb = np.zeros(3)
+        for k in range(n ** 3):
+            if k == tk:
+                continue
+            o = np.round(d[k] / dx * 2).astype(np.int64)
+            c = orc.alpha_counts(48, orc.alpha_key(o, 2)) / 512.0
+            Fb -= L[k] / (4 * math.pi * r2[k]) * (c[:, None] * nhat).sum(0)
+        assert np.allclose(F[q], Fb, rtol=1e-11, atol=1e-12 * np.abs(Fb).max())
+
+
+def test_no_extinction_tree_sum(orc):
+    """kappa_ext = 0 at theta = 0.5: J = sum over accepted nodes of L_node / (16 pi^2 r_COL^2)."""
+    w = synth.gaussian_clump(16, kappa_ext_scale=0.0)
+    t = orc.Tree(w)
+    ex = t.export()
+    u = t.unit_cm
+    for tk in [0, 1234, 2080, 4095]:
+        ids = t.accepted(tk)
+        own = ex["leaf"][ids] == tk
+        c = ex["vals"][ids, 8:11]
+        tc = ex["centre"][t.accepted(tk)[own]][0]
+        r2 = (((c - tc) * u) ** 2).sum(1)
+        r2[own] = (0.5 * w.box_cm / 16) ** 2
+        Jb = (ex["vals"][ids, 0] / (16 * math.pi ** 2 * r2)).sum()
+        J, _ = t.evaluate([tk])
+        assert math.isclose(J[0], Jb, rel_tol=1e-12)
+
+
+def test_tree_error_within_5_percent(orc):
+    """theta = 0.5 against theta -> 0 (every leaf accepted), emission only: within 5 %."""
+    w = synth.gaussian_clump(16, kappa_ext_scale=0.0)
+    tg = np.arange(0, 4096, 13)
+    J, _ = orc.Tree(w).evaluate(tg)
+    w.params["theta"] = 1e-9
+    J0, _ = orc.Tree(w).evaluate(tg)
+    err = np.abs(J / J0 - 1)
+    assert err.max() < 0.05
+
+
+def test_point_source_inverse_square(orc):
+    w = synth.point_source(16, kappa0=0.0)
+    t = orc.Tree(w)
+    J, F = t.evaluate()
+    cen = synth.cell_centres(16, w.box_cm)
+    host = 8 + 16 * (8 + 16 * 8)
+    r2 = ((cen - cen[host]) ** 2).sum(1)
+    Lst = w.star_lum[0]
+    m = np.arange(16 ** 3) != host
+    assert np.allclose(J[m] * 16 * math.pi ** 2 * r2[m] / Lst, 1.0, rtol=1e-12)
+    # flux points away from the source, |F| <= L / (4 pi r^2)
+    d = cen[m] - cen[host]
+    cosang = (F[m] * d).sum(1) / np.linalg.norm(F[m], axis=1) / np.sqrt(r2[m])
+    assert cosang.min() > 0.9
+    assert (np.linalg.norm(F[m], axis=1) <= Lst / (4 * math.pi * r2[m]) * (1 + 1e-12)).all()
+
+
+@pytest.mark.parametrize("kappa", [1.0, 10.0])
+def test_point_source_extinction_fit(orc, kappa):
+    """Fitted kappa from J r^2 along an axis; the paper's own fits are in tests/golden."""
+    gold = {}
+    for line in open(os.path.join(HERE, "golden", "point_source_extinction.txt")):
+        if line.strip() and not line.startswith("#"):
+            a, b = line.split()
+            gold[float(a)] = float(b)
+    n = 32
+    w = synth.point_source(n, kappa0=kappa)
+    t = orc.Tree(w)
+    c = n // 2
+    tg = np.array([(c + k) + n * (c + n * c) for k in range(1, n - c)])
+    J, _ = t.evaluate(tg)
+    r = np.arange(1, n - c) * w.box_cm / n
+    slope = np.polyfit(r, np.log(J * r * r), 1)[0]
+    kfit = -slope / 1e-18
+    # this reading under-extincts by ~9 % at 32^3 (the paper's quadratic bins over-extinct by 3 %)
+    assert abs(kfit / kappa - 1) < 0.15
+    assert abs(kfit / gold[kappa] - 1) < 0.15
+
+
+def test_thin_sphere_closed_form(orc):
+    """Optically thin uniform sphere: J(centre) = j R, j = (sigma/pi) kappa rho T^4."""
+    n = 32
+    w = synth.homogeneous(n, 1.0, 1e-22, td=20.0, kappa0=1.0)
+    x = synth.cell_centres(n, w.box_cm) - 0.5 * w.box_cm
+    R = 0.4 * w.box_cm
+    w.rho = np.where((x * x).sum(1) < R * R, 1e-22, 0.0).astype(np.float32)
+    c = n // 2
+    J, F = orc.Tree(w).evaluate([c + n * (c + n * c)])
+    j = SIGMA / math.pi * 1e-22 * 20.0 ** 4
+    assert abs(J[0] / (j * R) - 1) < 0.05
+
+
+def test_long_characteristics_with_extinction(orc):
+    """Against brute-force long characteristics through the cells (exact extinction
+    along straight lines) on the 16^3 clump with kappa = 1 (central column tau ~ 0.8):
+    agreement at the method's accuracy. The method under-extincts (the own segment
+    never extinguishes, eq. tauthin), so it lies above the brute force."""
+    w = synth.gaussian_clump(16, kappa0=1.0)
+    t = orc.Tree(w)
+    L, _ = _leaf_L(t)
+    lv = t.leaves()
+    ak = lv["kappa"] * w.rho.astype(np.float64)
+    tg = np.arange(0, 4096, 61)
+    J, F = t.evaluate(tg)
+    Jb, Fb = orc.brute_lc(16, w.box_cm, L, ak, tg)
+    own = L[tg] / (16 * math.pi ** 2 * (0.5 * w.box_cm / 16) ** 2)
+    err = J / (Jb + own) - 1
+    assert err.min() > 0.0
+    assert np.median(err) < 0.06 and err.max() < 0.1
+
+
+def test_deep_thick_plateau(orc):
+    """Inside a large isothermal optically thick region J -> sigma T^4 / pi (App. B)."""
+    n = 16
+    w = synth.homogeneous(n, 1.0, 1e-17, td=30.0, kappa0=10.0)   # tau per cell ~ 6
+    c = n // 2
+    J, _ = orc.Tree(w).evaluate([c + n * (c + n * c)])
+    assert abs(J[0] / (SIGMA * 30.0 ** 4 / math.pi) - 1) < 0.1
