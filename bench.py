@@ -1,0 +1,395 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the TreeRay/RadPressure hot path on GB300.
+
+Workload: 128^3 uniform grid in a 2 pc box, lognormal turbulent density (P(k) ~ k^-4,
+sigma_ln rho = 1.5, mean 1e-20 g/cm^3, seed 2), T_d ~ U[10, 40] K (seed 3), Planck-mean
+opacity 0.1 (T/10 K)^2 cm^2/g, one 1e5 Lsun star at the box centre; N_pix = 48
+(--npix 192 for the second ray count), 20 geometric radial segments, theta = 0.5;
+gas temperature U[10, 100] K for the dust balance. Synthetic, seeded.
+
+One step is one pass of the whole hot path through the C ABI: tree build (leaf
+quantities, Morton sort, nodes, moments), ray evaluation of every cell (walk, mapping,
+integration, finalization), radiation pressure, and the dust-temperature solve.
+Metric: target-cell ray evaluations per second = cells x N_pix / step time.
+
+Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events on the
+launching stream; a 256 MiB buffer is written between steps to flush the 129 MB L2
+(outside the events). The evaluate kernel is timed separately for the roofline.
+--impl reference times the FP64 CPU oracle on the host cores on a bounded sample.
+Under torchrun every rank runs an independent replica (weak scaling, no collective
+on the data path); value = cells x N_pix x ranks / max-over-ranks step time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "target-cell ray evaluations/sec (cells x N_pix)"
+UNIT = "ray-evals/s"
+
+
+def workload(npix: int):
+    import synth
+    w = synth.turbulent_cloud(128, npix=npix)
+    return synth.with_gas(w, seed=7, tgas_lo=10.0, tgas_hi=100.0)
+
+
+def config(npix: int, extra=None):
+    c = {"workload": f"turb128_npix{npix}", "cells": 128 ** 3, "grid": "uniform 128^3, box 2 pc",
+         "density": "lognormal P(k)~k^-4 sigma_lnrho=1.5 mean 1e-20 g/cm^3",
+         "npix": npix, "nbins": 20, "theta": 0.5, "stars": 1,
+         "l2": "flushed between steps (256 MiB write); tree rebuilt every step",
+         "step": "build+evaluate+radpressure+dust_temperature"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out = ""
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for f in ("evaluate.cu", "internal.h"):
+        with open(os.path.join(ROOT, "paper_2204_09072_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload_name: str):
+    """DRAM bytes per evaluate launch from the committed ncu summary, if it was taken on
+    the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "evaluate_traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        if d.get("kernel_sha") == kernel_source_sha() and workload_name in d.get("bytes_per_launch", {}):
+            return float(d["bytes_per_launch"][workload_name])
+    except Exception:
+        pass
+    return None
+
+
+# Algorithmic bytes of the evaluate kernel: per visited node its 16 B geometry record;
+# per accepted node (own cell aside) its two 16 B value records and the 8 B angular-kernel
+# offset pair; 4 B per angular-kernel entry; per target 16 B own geometry, 32 B own values,
+# 8 B map lookups, 8 B J_src and 28 B of outputs.
+BYTES_VISIT, BYTES_ACCEPT, BYTES_ENTRY, BYTES_TARGET = 16, 40, 4, 92
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2204_09072_gb300 as tr
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    tr.lib()
+    dev = torch.device("cuda", local)
+    w = workload(args.npix)
+    n = w.n_leaves
+    npix = args.npix
+    ctx = tr.Context(w.params)
+    st = torch.cuda.Stream(device=dev)
+    rho = torch.as_tensor(w.rho, device=dev)
+    td = torch.as_tensor(w.td, device=dev)
+    tgas = torch.as_tensor(w.tgas, device=dev)
+    J = torch.empty(n, dtype=torch.float32, device=dev)
+    F = torch.empty(3 * n, dtype=torch.float64, device=dev)
+    u = torch.empty(n, dtype=torch.float32, device=dev)
+    a_rp = torch.empty(3 * n, dtype=torch.float32, device=dev)
+    force = torch.empty(3 * n, dtype=torch.float32, device=dev)
+    p_src = torch.empty(n, dtype=torch.float32, device=dev)
+    Td = torch.empty(n, dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(ev=None):
+        if ev:
+            ev[0].record(st)
+        ctx.build(w.box_cm, rho, td, n=w.uniform_n, star_pos=w.star_pos, star_lum=w.star_lum, stream=st)
+        if ev:
+            ev[1].record(st)
+        ctx.evaluate(J, F, stream=st)
+        if ev:
+            ev[2].record(st)
+        ctx.radpressure(J, F, u, a_rp, force, p_src, stream=st)
+        ctx.dust_temperature(tgas, J, Td, stream=st)
+        if ev:
+            ev[3].record(st)
+
+    with torch.cuda.stream(st):
+        for _ in range(args.warmup):
+            step()
+            flush.zero_()
+        ctx.check(st)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+        l0 = ctx.kernel_launches
+        with ClockSampler(local) as clk:
+            for k in range(args.steps):
+                flush.zero_()
+                step(evs[k])
+            torch.cuda.synchronize()
+        launches = ctx.kernel_launches - l0
+        ctx.check(st)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+    step_ms = [e[0].elapsed_time(e[3]) for e in evs]
+    eval_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    build_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    post_ms = [e[2].elapsed_time(e[3]) for e in evs]
+    ms = statistics.mean(step_ms)
+    ms_eval = statistics.mean(eval_ms)
+    if dist:
+        t = torch.tensor([ms, ms_eval], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, ms_eval = float(t[0]), float(t[1])
+    value = n * npix * world / (ms * 1e-3)
+
+    # ---- roofline of the evaluate kernel (algorithmic bytes / measured duration)
+    with torch.cuda.stream(st):
+        tot = ctx.walk_stats(stream=st).cpu().numpy().astype(np.int64)
+    visits, acc, ent = (int(x) for x in tot)
+    alg_bytes = (BYTES_VISIT * visits + BYTES_ACCEPT * (acc - n) + BYTES_ENTRY * ent
+                 + BYTES_TARGET * n)
+    peak, peak_kind = measured_peak()
+    achieved = alg_bytes / (ms_eval * 1e-3) / 1e9
+    traffic = ncu_traffic(f"turb128_npix{npix}")
+
+    # ---- end to end through the public API with host buffers
+    rho_h = torch.as_tensor(w.rho).pin_memory()
+    td_h = torch.as_tensor(w.td).pin_memory()
+    tg_h = torch.as_tensor(w.tgas).pin_memory()
+    J_h = torch.empty(n, dtype=torch.float32).pin_memory()
+    F_h = torch.empty(3 * n, dtype=torch.float64).pin_memory()
+    Td_h = torch.empty(n, dtype=torch.float32).pin_memory()
+    a_h = torch.empty(3 * n, dtype=torch.float32).pin_memory()
+    h2d = 3 * 4 * n
+    d2h = 4 * n + 24 * n + 4 * n + 12 * n
+
+    def e2e_step():
+        rho.copy_(rho_h, non_blocking=True)
+        td.copy_(td_h, non_blocking=True)
+        tgas.copy_(tg_h, non_blocking=True)
+        step()
+        J_h.copy_(J, non_blocking=True)
+        F_h.copy_(F, non_blocking=True)
+        Td_h.copy_(Td, non_blocking=True)
+        a_h.copy_(a_rp, non_blocking=True)
+
+    with torch.cuda.stream(st):
+        for _ in range(max(1, args.warmup)):
+            e2e_step()
+        st.synchronize()
+        e_ms = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            e2e_step()
+            e1.record(st)
+            st.synchronize()
+            e_ms.append(e0.elapsed_time(e1))
+    e2e_val = n * npix * world / (statistics.mean(e_ms) * 1e-3)
+    if dist:
+        t = torch.tensor([statistics.mean(e_ms)], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_val = n * npix * world / (float(t[0]) * 1e-3)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded lognormal turbulent cloud)",
+            "config": config(npix, {"parallelism": f"replicas x{world}",
+                                    "ms_build": statistics.mean(build_ms),
+                                    "ms_evaluate": ms_eval,
+                                    "ms_radpressure_dust": statistics.mean(post_ms)}),
+            "roofline": {"bound": "hbm", "kernel": "k_evaluate", "achieved": achieved,
+                         "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_kind": peak_kind, "traffic": traffic,
+                         "algorithmic_bytes_per_launch": alg_bytes,
+                         "walk": {"visits": visits, "accepted": acc, "alpha_entries": ent}},
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+        }
+        if cpu:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line))
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(w, seconds: float):
+    """The FP64 oracle as it stands, on the host cores, on a bounded sample of targets;
+    the full-workload time is its tree build plus the sample time scaled to every cell."""
+    import numpy as np
+
+    import oracle
+    import synth
+    oracle.build()
+    t0 = time.perf_counter()
+    tree = oracle.Tree(w)
+    t_build = time.perf_counter() - t0
+    cal = synth.sample_targets(w.n_leaves, 1024, seed=21)
+    t0 = time.perf_counter()
+    tree.evaluate(cal)
+    t_cal = time.perf_counter() - t0
+    m = int(min(w.n_leaves, max(1024, 1024 * seconds / max(t_cal, 1e-3))))
+    tg = synth.sample_targets(w.n_leaves, m, seed=22)
+    t0 = time.perf_counter()
+    J, F = tree.evaluate(tg)
+    tree.radpressure(J, F, tg)
+    oracle.dust_temperature(w.params, w.rho[tg], w.tgas[tg], J)
+    t_s = time.perf_counter() - t0
+    t_full = t_build + t_s * w.n_leaves / m
+    cores = os.cpu_count()
+    return {"value": w.n_leaves * w.params["npix"] / t_full, "unit": UNIT, "cores": cores,
+            "kind": "oracle",
+            "sample": f"{m} random cells of {w.n_leaves} (evaluate+radpressure+dust T, "
+                      f"{t_s:.1f} s) plus the full tree build ({t_build:.1f} s), scaled to all cells",
+            "threads": cores}
+
+
+def run_reference(args):
+    """The oracle timed as the reference arm: each step evaluates a bounded sample."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    import synth
+    oracle.build()
+    w = workload(args.npix)
+    tree = oracle.Tree(w)
+    m = args.ref_sample
+    times = []
+    for k in range(args.warmup + args.steps):
+        tg = synth.sample_targets(w.n_leaves, m, seed=100 + k)
+        t0 = time.perf_counter()
+        J, F = tree.evaluate(tg)
+        tree.radpressure(J, F, tg)
+        oracle.dust_temperature(w.params, w.rho[tg], w.tgas[tg], J)
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    ms = statistics.mean(times) * 1e3
+    value = m * args.npix / (ms * 1e-3)
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded lognormal turbulent cloud)",
+            "config": config(args.npix, {"sample_per_step": m}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{m} random cells per step (evaluate+radpressure+dust T)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--npix", type=int, default=48, choices=[12, 48, 192])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-sample", type=int, default=16384)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,224 @@
+/*
+ * treeray.h - C ABI of the GB300 (sm_103a) TreeRay/RadPressure hot path.
+ *
+ * Backwards ray tracing of infrared radiation from diffuse sources on an
+ * octree, after Klepitko, Walch, Wuensch, Seifried, Dinnbier & Haid (MNRAS 2023),
+ * "Tree-based solvers for adaptive mesh refinement code FLASH - III".
+ * Every cell and every star particle emits; for each target cell N_pix HEALPix
+ * rays are cast, the tree is walked under an opening criterion, accepted nodes
+ * are deposited into the radial segments of the rays they cover, each ray is
+ * integrated from the inside out and the rays are reduced to J, F, u and the
+ * radiation-pressure terms.
+ *
+ * Conventions
+ *  - Units are CGS. Grids are cubic; positions are in [0, box)^3.
+ *  - Leaves are given in the caller's order: x fastest for a uniform n^3 grid,
+ *    block-major then x fastest inside each 8^3 block for AMR grids. Every
+ *    per-leaf input and output array uses that order.
+ *  - "device" pointers are CUDA global-memory pointers on the context's device;
+ *    "host" pointers are ordinary host memory. The caller owns every array it
+ *    passes; the context owns the tree, the tables and its scratch memory.
+ *  - Calls that take a cudaStream_t enqueue their work on that stream and return
+ *    before it finishes, unless stated otherwise. Errors found by a kernel are
+ *    recorded in a device error word and reported by treeray_check().
+ *  - Functions return a treeray_status; treeray_last_error() gives the message.
+ *    No function aborts the process.
+ *  - A context is bound to the device that was current at treeray_create(); call
+ *    every function with that device current. Contexts are not thread-safe.
+ */
+#ifndef TREERAY_H
+#define TREERAY_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct treeray_ctx* treeray_t;
+typedef struct CUstream_st* treeray_stream_t; /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+    TREERAY_OK = 0,
+    TREERAY_EINVAL = 1,     /* bad argument or unsupported size */
+    TREERAY_ENOMEM = 2,     /* device or host allocation failed */
+    TREERAY_ECUDA = 3,      /* a CUDA runtime call failed */
+    TREERAY_ENOTBUILT = 4,  /* evaluate/radpressure/dust before a successful build */
+    TREERAY_ETIMEOUT = 5,   /* a bounded device loop ran out (stack overflow, table miss) */
+    TREERAY_ENOCONV = 6     /* the dust-temperature fixed point did not converge */
+} treeray_status;
+
+/*
+ * Method parameters.
+ *  npix            HEALPix rays per target, 12 * nside^2 with nside in {1, 2, 4}
+ *                  (Sec. 4.2 "Ray mapping").
+ *  nbins           radial evaluation points per ray, 1..64. Evaluation point i sits
+ *                  at R_i = R_0 (R_max/R_0)^(i/nbins), R_0 = half the target cell,
+ *                  R_max = sqrt(3) box; segment i is [R_i, R_(i+1)) and segment 0
+ *                  also holds [0, R_0) (Sec. 4.2, Fig. "ray bin").
+ *  theta           opening angle theta_lim: a node of edge E at distance d from the
+ *                  target (centre to centre) is opened iff E^2 >= theta^2 d^2, or if
+ *                  it contains the target; leaves are always accepted (Sec. 4).
+ *  kappa_model     0: grey kappa0 per gram of gas; 1: Planck mean
+ *                  0.1 cm^2/g (T/10 K)^2 capped at 150 K (Sec. 2).
+ *  kappa0          grey opacity, cm^2/g (kappa_model 0).
+ *  dust_to_gas     xi; enters only the gas-dust coupling of the dust temperature.
+ *  dust_emission   1: dust emits (eqs. lthinbnode, lthickbnode); 0: only stars emit
+ *                  (the point-source benchmark, Sec. 5.1).
+ *  kappa_ext_scale multiplies the extinction areas A~ (1 = the method; 0 = test switch).
+ *  alpha_s         sub-cube samples per axis of the angular kernel, a multiple of 4
+ *                  (8 is the default, 512 samples per node position).
+ */
+typedef struct {
+    int npix;
+    int nbins;
+    double theta;
+    int kappa_model;
+    double kappa0;
+    double dust_to_gas;
+    int dust_emission;
+    double kappa_ext_scale;
+    int alpha_s;
+} treeray_params;
+
+/*
+ * Grid description.
+ *  Uniform: n > 0 is the cells per axis (a power of two, 1..2^10); n_blocks = 0.
+ *  AMR:     n = 0; n_blocks > 0 blocks of 8^3 cells; blocks is a HOST array of
+ *           4 ints per block (bi, bj, bk, l): the block's cells sit at octree level l
+ *           (root = level 0, cell edge box / 2^l) with integer coordinates
+ *           8 (bi, bj, bk) + (x, y, z). The blocks must tile the box and form a
+ *           complete octree (every refined region split into 8).
+ *  box: box edge in cm.
+ */
+typedef struct {
+    int n;
+    int n_blocks;
+    const int32_t* blocks;
+    double box;
+} treeray_grid;
+
+/* Create a context on the current device: validates params and builds the
+ * HEALPix ray directions on the host. Returns TREERAY_EINVAL for bad params. */
+treeray_status treeray_create(const treeray_params* params, treeray_t* out);
+
+/* Destroy a context and free everything it owns. NULL is allowed. */
+treeray_status treeray_destroy(treeray_t ctx);
+
+/*
+ * Tree build (Sec. 4.1 and App. A): leaf quantities, Morton sort, node structure,
+ * node moments and the centre of luminosity, plus the angular-kernel table.
+ *  rho, Td         device float[N]: gas density (g/cm^3), dust temperature (K).
+ *  kappa           device float[N] opacity (cm^2/g) or NULL to use the params' model.
+ *  n_stars         number of point sources (0..4096).
+ *  star_pos        host double[3 n_stars] positions (cm); star_lum host double[n_stars]
+ *                  non-ionising luminosity L_src,IR (erg/s). A star heats the leaf whose
+ *                  half-open cell contains its position.
+ * Per leaf (Sec. 4.1.1): tau_b = rho kappa dx; thin iff tau_b < 1; thin: L = 4 sigma
+ * rho kappa T^4 dV, A~ = rho kappa dV; thick: L_ = (sigma/pi) T^4, A~; S = L_src
+ * e^(-tau_b/2); J_src = (1 - e^(-tau_b/2)) L_src / dx^2 (eq. jsrc);
+ * P_src = (1 - e^(-tau_b/2)) L_src / (c dx^2) (eq. psrc).
+ * The call synchronizes the stream once (to size the tree) and returns after the
+ * build is enqueued. Inputs may be freed after the stream has finished.
+ */
+treeray_status treeray_build(treeray_t ctx, const treeray_grid* grid, const float* rho,
+                             const float* Td, const float* kappa, int n_stars,
+                             const double* star_pos, const double* star_lum,
+                             treeray_stream_t stream);
+
+/*
+ * Ray evaluation (Secs. 4.2-4.4): walk, ray mapping with the angular kernel alpha and
+ * radial kernel beta = R_i^2 / r^2, segment merge, ray integration and finalization
+ * F = sum_h -F^h n^h, J = (1/4pi) sum_h F^h + J_src.
+ *  targets   device int32[n] caller leaf indices, or NULL for every leaf (then
+ *            n must equal the leaf count and row k of the outputs is leaf k).
+ *  J         device float[n], mean intensity (erg/s/cm^2/sr).
+ *  F         device double[3n], flux vector xyz interleaved (erg/s/cm^2).
+ */
+treeray_status treeray_evaluate(treeray_t ctx, const int32_t* targets, int64_t n, float* J,
+                                double* F, treeray_stream_t stream);
+
+/*
+ * Radiation energy density and pressure (Sec. 4.5) for every leaf (caller order):
+ *  u = 4 pi J / c; P_dot = (F/c) kappa rho (1 - e^-tau)/tau dV (the tau factor is 1 for
+ *  tau < 1e-4); a_rp = P_dot / (rho dV); force = P_dot; p_src from the build.
+ *  J device float[N], F device double[3N]; outputs device float: u[N], a_rp[3N],
+ *  force[3N], p_src[N]. Any output may be NULL.
+ */
+treeray_status treeray_radpressure(treeray_t ctx, const float* J, const double* F, float* u,
+                                   float* a_rp, float* force, float* p_src,
+                                   treeray_stream_t stream);
+
+/*
+ * Equilibrium dust temperature (Sec. 4.6, App. D) per leaf (caller order): the root of
+ *  Gamma_dust-gas + heat_extra + rho kappa(T_d) (4 pi J - 4 sigma T_d^4) = 0,
+ *  Gamma_dust-gas = 3.8e-33 sqrt(T) (T - T_d)(1 - 0.8 e^(-75/T)) n_H^2 (xi/0.01),
+ *  n_H = 0.7 rho / m_H, floor 2.7 K; found by bracketing and 60 bisections in ln T.
+ *  Tgas device float[N]; heat_extra device float[N] (erg/s/cm^3) or NULL; J device
+ *  float[N]; Td device float[N] output. rho (and kappa if given) from the build.
+ */
+treeray_status treeray_dust_temperature(treeray_t ctx, const float* Tgas, const float* heat_extra,
+                                        const float* J, float* Td, treeray_stream_t stream);
+
+/* Synchronize the stream and report errors recorded by kernels since the last check
+ * (TREERAY_ETIMEOUT for a bounded loop that ran out, TREERAY_ECUDA for CUDA errors). */
+treeray_status treeray_check(treeray_t ctx, treeray_stream_t stream);
+
+/* Number of leaves and nodes of the current tree (0 before a build). */
+int64_t treeray_leaf_count(treeray_t ctx);
+int64_t treeray_node_count(treeray_t ctx);
+
+/*
+ * Copy the tree to HOST arrays, nodes breadth first (level-major, Morton order within
+ * a level), for structure and moment checks. Any pointer may be NULL.
+ *  level int32[nn]; leaf int32[nn] (caller leaf index, -1 for h-nodes);
+ *  child0 int32[nn] (first sub-node id, -1 for leaves); centre int64[3nn] (geometric
+ *  centre in half-cells of the finest level); vals double[11nn] per node: thin L (+S),
+ *  thin A~, thin V, thick sum L_ V, thick A~, thick V, mass, xi, COL xyz (half-cells).
+ * Synchronizes the stream.
+ */
+treeray_status treeray_tree_export(treeray_t ctx, int32_t* level, int32_t* leaf, int32_t* child0,
+                                   int64_t* centre, double* vals, treeray_stream_t stream);
+
+/* Copy per-leaf build outputs to HOST double arrays (caller order): kappa, tau_b, J_src,
+ * P_src, and int32 thick flags. Any pointer may be NULL. Synchronizes the stream. */
+treeray_status treeray_leaf_export(treeray_t ctx, double* kappa, double* tau, double* jsrc,
+                                   double* psrc, int32_t* thick, treeray_stream_t stream);
+
+/*
+ * Accepted-node lists of the walk (structure check; slow, one warp per target).
+ *  targets device int32[n] caller leaf indices; counts device int32[n] receives each
+ *  target's number of accepted nodes; ids device int32[n * cap] receives the first
+ *  cap node ids of target q at ids[q * cap], in walk order.
+ */
+treeray_status treeray_accepted(treeray_t ctx, const int32_t* targets, int64_t n, int32_t cap,
+                                int32_t* counts, int32_t* ids, treeray_stream_t stream);
+
+/*
+ * Walk statistics for the roofline model: totals over the targets of nodes visited
+ * (tested against the opening criterion), nodes accepted (own cell included) and
+ * angular-kernel entries read. targets device int32[n] or NULL for every leaf;
+ * totals device int64[3], accumulated (the caller zeroes it).
+ */
+treeray_status treeray_walk_stats(treeray_t ctx, const int32_t* targets, int64_t n,
+                                  int64_t* totals, treeray_stream_t stream);
+
+/*
+ * Host-only: angular-kernel hit counts of key K (three ints) for npix rays and s samples
+ * per axis, written to counts[npix]. Needs no GPU; used to check the table builder.
+ */
+treeray_status treeray_alpha_counts_host(int npix, int s, const int64_t* K, int32_t* counts);
+
+/* Number of CUDA kernels this context has launched since it was created
+ * (instrumentation for benchmarks; counted on the host at each launch). */
+int64_t treeray_kernel_launches(treeray_t ctx);
+
+/* Message of the last error on this thread (empty string if none). */
+const char* treeray_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TREERAY_H */

@@ -79,6 +79,7 @@ def lib():
                                          P(C.c_double), P(C.c_int32)]
             L.or_accepted.argtypes = [C.c_void_p, C.c_int64, P(C.c_int32), C.c_int64]
             L.or_accepted.restype = C.c_int64
+            L.or_walk_stats.argtypes = [C.c_void_p, C.c_int64, P(C.c_int64)]
             L.or_target_radii.argtypes = [C.c_void_p, C.c_int64, P(C.c_double)]
             L.or_alpha_key.argtypes = [P(C.c_int64), C.c_int64, P(C.c_int64)]
             L.or_alpha_counts.argtypes = [C.c_int, C.c_int, P(C.c_int64), P(C.c_int)]
@@ -228,6 +229,12 @@ class Tree:
         ids = np.zeros(cap, np.int32)
         n = lib().or_accepted(self.h, int(leaf), _p(ids, C.c_int32), cap)
         return ids[:min(n, cap)].copy()
+
+    def walk_stats(self, leaf: int) -> np.ndarray:
+        """(visited nodes, accepted nodes, angular-kernel entries) of one target's walk."""
+        out = np.zeros(3, np.int64)
+        lib().or_walk_stats(self.h, int(leaf), _p(out, C.c_int64))
+        return out
 
     def radii(self, leaf: int) -> np.ndarray:
         R = np.zeros(self.params["nbins"] + 1)

@@ -1040,6 +1040,49 @@ int64_t or_accepted(const or_tree* t, int64_t leaf, int32_t* ids, int64_t cap) {
     return n;
 }
 
+/* Walk statistics of one target: nodes visited (tested against the opening
+ * criterion), nodes accepted (own cell included) and angular-kernel entries read by
+ * the accepted nodes other than the own cell. out[3]. */
+void or_walk_stats(or_tree* t, int64_t leaf, int64_t* out) {
+    const or_node* tn = &t->nodes[t->leaf_node[leaf]];
+    double th2 = t->p.theta * t->p.theta;
+    int stack[8 * 64 * 4];
+    int sp = 0;
+    int64_t visits = 0, acc = 0, ent = 0;
+    stack[sp++] = 0;
+    while (sp > 0) {
+        int id = stack[--sp];
+        const or_node* nd = &t->nodes[id];
+        ++visits;
+        int64_t o[3], d2 = 0;
+        int inside = 1;
+        for (int a = 0; a < 3; ++a) {
+            o[a] = nd->c[a] - tn->c[a];
+            d2 += o[a] * o[a];
+            if (2 * (o[a] < 0 ? -o[a] : o[a]) >= nd->E) inside = 0;
+        }
+        int open = nd->leaf < 0 && (inside || (double)(nd->E * nd->E) >= th2 * (double)d2);
+        if (open) {
+            for (int k = 7; k >= 0; --k) stack[sp++] = nd->child[k];
+        } else {
+            ++acc;
+            if (d2 != 0) {
+                int64_t K[3];
+                int owned = 0;
+                or_key(o, nd->E, K);
+                const int* l = or_alpha_get(&t->alpha, K, &owned);
+                int n = 0;
+                while (l[2 * n] >= 0) ++n;
+                ent += n;
+                if (owned) free((void*)l);
+            }
+        }
+    }
+    out[0] = visits;
+    out[1] = acc;
+    out[2] = ent;
+}
+
 /* Evaluation radii R_i (half-units) for a target leaf. */
 void or_target_radii(const or_tree* t, int64_t leaf, double* R) {
     or_radii(t->p.nbins, t->lmax, t->nodes[t->leaf_node[leaf]].E, R);

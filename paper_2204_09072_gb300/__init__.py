@@ -1,0 +1,251 @@
+"""GB300-native TreeRay/RadPressure hot path.
+
+Thin Python binding of the C ABI in ``include/treeray.h`` (``libtreeray.so``, built
+in-tree for sm_103a). Every function marshals arguments only: all steps of the path
+run in the library's CUDA kernels. PyTorch provides device memory and streams.
+There is no CPU fallback: if the library is missing or no GPU is present the calls
+raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from .build_lib import OUT as LIB_PATH
+from .build_lib import build as build_library
+
+__all__ = ["Params", "Grid", "Context", "TreeRayError", "lib", "alpha_counts_host",
+           "build_library", "LIB_PATH", "STATUS"]
+
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTBUILT", 5: "ETIMEOUT",
+          6: "ENOCONV"}
+
+
+class TreeRayError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"treeray {STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Params(C.Structure):
+    _fields_ = [("npix", C.c_int), ("nbins", C.c_int), ("theta", C.c_double),
+                ("kappa_model", C.c_int), ("kappa0", C.c_double), ("dust_to_gas", C.c_double),
+                ("dust_emission", C.c_int), ("kappa_ext_scale", C.c_double), ("alpha_s", C.c_int)]
+
+    @classmethod
+    def from_dict(cls, d: dict) -> "Params":
+        return cls(int(d["npix"]), int(d["nbins"]), float(d["theta"]), int(d["kappa_model"]),
+                   float(d["kappa0"]), float(d["dust_to_gas"]), int(d["dust_emission"]),
+                   float(d["kappa_ext_scale"]), int(d.get("alpha_s", 8)))
+
+
+class Grid(C.Structure):
+    _fields_ = [("n", C.c_int), ("n_blocks", C.c_int), ("blocks", C.POINTER(C.c_int32)),
+                ("box", C.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libtreeray.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library not built ({LIB_PATH}); run paper_2204_09072_gb300.build_library()")
+    L = C.CDLL(LIB_PATH)
+    vp, i64, i32p = C.c_void_p, C.c_int64, C.POINTER(C.c_int32)
+    L.treeray_create.argtypes = [C.POINTER(Params), C.POINTER(vp)]
+    L.treeray_destroy.argtypes = [vp]
+    L.treeray_build.argtypes = [vp, C.POINTER(Grid), vp, vp, vp, C.c_int, vp, vp, vp]
+    L.treeray_evaluate.argtypes = [vp, vp, i64, vp, vp, vp]
+    L.treeray_radpressure.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+    L.treeray_dust_temperature.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.treeray_check.argtypes = [vp, vp]
+    L.treeray_leaf_count.argtypes = [vp]
+    L.treeray_leaf_count.restype = i64
+    L.treeray_node_count.argtypes = [vp]
+    L.treeray_node_count.restype = i64
+    L.treeray_tree_export.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    L.treeray_leaf_export.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    L.treeray_accepted.argtypes = [vp, vp, i64, C.c_int32, vp, vp, vp]
+    L.treeray_alpha_counts_host.argtypes = [C.c_int, C.c_int, vp, i32p]
+    L.treeray_walk_stats.argtypes = [vp, vp, i64, vp, vp]
+    L.treeray_kernel_launches.argtypes = [vp]
+    L.treeray_kernel_launches.restype = i64
+    L.treeray_last_error.restype = C.c_char_p
+    for f in ("treeray_create", "treeray_destroy", "treeray_build", "treeray_evaluate",
+              "treeray_radpressure", "treeray_dust_temperature", "treeray_check",
+              "treeray_tree_export", "treeray_leaf_export", "treeray_accepted",
+              "treeray_alpha_counts_host", "treeray_walk_stats"):
+        getattr(L, f).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _raise(rc: int):
+    if rc != 0:
+        raise TreeRayError(rc, lib().treeray_last_error().decode())
+
+
+def _dev(t, dtype, name, allow_none=False):
+    """Device pointer of a contiguous CUDA tensor of the given dtype."""
+    if t is None:
+        if allow_none:
+            return None
+        raise ValueError(f"{name} is required")
+    if not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA tensor of {dtype}")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(s):
+    if s is None:
+        import torch
+        s = torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def alpha_counts_host(npix: int, s: int, K):
+    """Angular-kernel hit counts of key K (host-only call, needs no GPU)."""
+    import numpy as np
+    k = np.ascontiguousarray(K, dtype=np.int64)
+    out = np.zeros(npix, np.int32)
+    _raise(lib().treeray_alpha_counts_host(npix, s, C.c_void_p(k.ctypes.data),
+                                           out.ctypes.data_as(C.POINTER(C.c_int32))))
+    return out
+
+
+class Context:
+    """One treeray context (C: treeray_t) on the current CUDA device."""
+
+    def __init__(self, params: dict):
+        import torch
+        torch.cuda.init()
+        self.params = dict(params)
+        self._p = Params.from_dict(params)
+        h = C.c_void_p()
+        _raise(lib().treeray_create(C.byref(self._p), C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().treeray_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- C: treeray_build
+    def build(self, box: float, rho, Td, n: int = 0, blocks=None, kappa=None, star_pos=None,
+              star_lum=None, stream=None):
+        import numpy as np
+        import torch
+        g = Grid()
+        g.n = int(n)
+        g.box = float(box)
+        self._blocks = None
+        if blocks is not None:
+            self._blocks = np.ascontiguousarray(blocks, dtype=np.int32).reshape(-1)
+            g.n_blocks = self._blocks.size // 4
+            g.blocks = self._blocks.ctypes.data_as(C.POINTER(C.c_int32))
+        ns = 0 if star_lum is None else len(star_lum)
+        sp = np.ascontiguousarray(star_pos if ns else np.zeros((1, 3)), dtype=np.float64).reshape(-1)
+        sl = np.ascontiguousarray(star_lum if ns else np.zeros(1), dtype=np.float64)
+        _raise(lib().treeray_build(self.h, C.byref(g), _dev(rho, torch.float32, "rho"),
+                                   _dev(Td, torch.float32, "Td"),
+                                   _dev(kappa, torch.float32, "kappa", True), ns,
+                                   C.c_void_p(sp.ctypes.data), C.c_void_p(sl.ctypes.data),
+                                   _stream(stream)))
+
+    # -- C: treeray_evaluate
+    def evaluate(self, J, F, targets=None, stream=None):
+        import torch
+        n = J.numel()
+        _raise(lib().treeray_evaluate(self.h, _dev(targets, torch.int32, "targets", True), n,
+                                      _dev(J, torch.float32, "J"), _dev(F, torch.float64, "F"),
+                                      _stream(stream)))
+
+    # -- C: treeray_radpressure
+    def radpressure(self, J, F, u=None, a_rp=None, force=None, p_src=None, stream=None):
+        import torch
+        f32 = torch.float32
+        _raise(lib().treeray_radpressure(self.h, _dev(J, f32, "J"), _dev(F, torch.float64, "F"),
+                                         _dev(u, f32, "u", True), _dev(a_rp, f32, "a_rp", True),
+                                         _dev(force, f32, "force", True),
+                                         _dev(p_src, f32, "p_src", True), _stream(stream)))
+
+    # -- C: treeray_dust_temperature
+    def dust_temperature(self, Tgas, J, Td, heat_extra=None, stream=None):
+        import torch
+        f32 = torch.float32
+        _raise(lib().treeray_dust_temperature(self.h, _dev(Tgas, f32, "Tgas"),
+                                              _dev(heat_extra, f32, "heat_extra", True),
+                                              _dev(J, f32, "J"), _dev(Td, f32, "Td"),
+                                              _stream(stream)))
+
+    # -- C: treeray_check
+    def check(self, stream=None):
+        _raise(lib().treeray_check(self.h, _stream(stream)))
+
+    @property
+    def leaf_count(self) -> int:
+        return lib().treeray_leaf_count(self.h)
+
+    @property
+    def node_count(self) -> int:
+        return lib().treeray_node_count(self.h)
+
+    # -- C: treeray_walk_stats
+    def walk_stats(self, targets=None, stream=None):
+        """Totals (visited nodes, accepted nodes, angular-kernel entries) over the targets."""
+        import torch
+        n = self.leaf_count if targets is None else targets.numel()
+        tot = torch.zeros(3, dtype=torch.int64, device="cuda")
+        _raise(lib().treeray_walk_stats(self.h, _dev(targets, torch.int32, "targets", True), n,
+                                        _dev(tot, torch.int64, "totals"), _stream(stream)))
+        return tot
+
+    # -- C: treeray_kernel_launches
+    @property
+    def kernel_launches(self) -> int:
+        return lib().treeray_kernel_launches(self.h)
+
+    # -- C: treeray_tree_export
+    def tree_export(self, stream=None) -> dict:
+        import numpy as np
+        nn = self.node_count
+        lev = np.zeros(nn, np.int32)
+        leaf = np.zeros(nn, np.int32)
+        ch = np.zeros(nn, np.int32)
+        cen = np.zeros((nn, 3), np.int64)
+        vals = np.zeros((nn, 11))
+        p = lambda a: C.c_void_p(a.ctypes.data)
+        _raise(lib().treeray_tree_export(self.h, p(lev), p(leaf), p(ch), p(cen), p(vals),
+                                         _stream(stream)))
+        return dict(level=lev, leaf=leaf, child0=ch, centre=cen, vals=vals)
+
+    # -- C: treeray_leaf_export
+    def leaf_export(self, stream=None) -> dict:
+        import numpy as np
+        n = self.leaf_count
+        k, t, j, ps = (np.zeros(n) for _ in range(4))
+        th = np.zeros(n, np.int32)
+        p = lambda a: C.c_void_p(a.ctypes.data)
+        _raise(lib().treeray_leaf_export(self.h, p(k), p(t), p(j), p(ps), p(th), _stream(stream)))
+        return dict(kappa=k, tau=t, jsrc=j, psrc=ps, thick=th)
+
+    # -- C: treeray_accepted
+    def accepted(self, targets, cap: int = 8192, stream=None):
+        import torch
+        n = targets.numel()
+        counts = torch.zeros(n, dtype=torch.int32, device=targets.device)
+        ids = torch.full((n, cap), -1, dtype=torch.int32, device=targets.device)
+        _raise(lib().treeray_accepted(self.h, _dev(targets, torch.int32, "targets"), n, cap,
+                                      _dev(counts, torch.int32, "counts"),
+                                      _dev(ids, torch.int32, "ids"), _stream(stream)))
+        return counts, ids

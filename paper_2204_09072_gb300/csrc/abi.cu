@@ -1,0 +1,359 @@
+// C ABI of the treeray library: argument checking, context and table management.
+// The compute steps live in build.cu, evaluate.cu and post.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace tr {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string& msg) { g_err = msg; }
+
+void free_tables(DeviceTables& t) {
+    void* ptrs[] = {t.nhat, t.alpha_off, t.alpha_ent, t.bin_thr, t.R2,   t.Rh,
+                    t.open_max, t.str_lo, t.str_hi, t.scal, t.err, t.queue};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    t = DeviceTables{};
+}
+
+namespace {
+template <typename T>
+treeray_status upload(T** dst, const std::vector<T>& src, cudaStream_t s) {
+    if (*dst) cudaFree(*dst);
+    *dst = nullptr;
+    TR_CUDA(cudaMalloc((void**)dst, sizeof(T) * std::max<size_t>(src.size(), 1)));
+    if (!src.empty())
+        TR_CUDA(cudaMemcpyAsync(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice, s));
+    return TREERAY_OK;
+}
+}  // namespace
+
+// Per-grid tables: the alpha table (cached by grid shape) and, for every target level,
+// the integer thresholds of the walk's decisions:
+//   bin i      : d^2 >= ceil(R_i^2)                      (segment index, i >= 1)
+//   open       : d^2 <= open_max[level]  <=>  theta^2 d^2 <= E^2 in FP64
+//   straddle   : d^2 >= ceil((R_j + s)^2) -> the node's near edge lies beyond R_j;
+//                d^2 >= ceil((R_j - s)^2) (0 when R_j <= s) -> its far edge does,
+//                s = sqrt(3)/2 E (half the node's diagonal)
+treeray_status upload_tables(treeray_ctx* c, cudaStream_t s) {
+    const int L = c->lmax, nb = c->p.nbins;
+    if (c->tab_lmax == L && c->tab_amr == c->amr) {
+        c->built = true;  // tables depend only on the grid shape: reuse
+        return TREERAY_OK;
+    }
+    {
+        c->ht.npix = c->p.npix;
+        c->ht.nside = healpix_nside(c->p.npix);
+        c->ht.s = c->p.alpha_s;
+        build_alpha_table(c->ht, c->p.theta, L, c->amr);
+        treeray_status rc;
+        if ((rc = upload(&c->dt.alpha_off, c->ht.alpha_off, s)) != TREERAY_OK) return rc;
+        if ((rc = upload(&c->dt.alpha_ent, c->ht.alpha_ent, s)) != TREERAY_OK) return rc;
+    }
+    std::vector<int64_t> thr((size_t)(L + 1) * nb), omax(L + 1);
+    std::vector<float> R2((size_t)(L + 1) * nb), Rh((size_t)(L + 1) * nb);
+    std::vector<int64_t> slo((size_t)(L + 1) * (L + 1) * nb), shi(slo.size());
+    std::vector<double> R(nb + 1);
+    const double th2 = c->p.theta * c->p.theta;
+    const int64_t dmax = (int64_t)1 << 62;
+    for (int lv = 0; lv <= L; ++lv) {
+        const int64_t E = (int64_t)2 << (L - lv);
+        const double E2 = (double)(E * E);
+        // largest integer d2 with th2 * d2 <= E^2
+        int64_t x;
+        const double guess = E2 / th2;
+        if (!(guess < 4.0e18)) x = dmax;
+        else {
+            x = (int64_t)std::floor(guess);
+            while (x > 0 && th2 * (double)x > E2) --x;
+            while (x < dmax && th2 * (double)(x + 1) <= E2) ++x;
+        }
+        omax[lv] = x;
+    }
+    for (int lt = 0; lt <= L; ++lt) {
+        radii(nb, L, (int64_t)2 << (L - lt), R.data());
+        for (int i = 0; i < nb; ++i) {
+            thr[(size_t)lt * nb + i] = (int64_t)std::ceil(R[i] * R[i]);
+            R2[(size_t)lt * nb + i] = (float)(R[i] * R[i]);
+            Rh[(size_t)lt * nb + i] = (float)R[i];
+        }
+        for (int ln = 0; ln <= L; ++ln) {
+            const int64_t E = (int64_t)2 << (L - ln);
+            const double sd = (std::sqrt(3.0) * 0.5) * (double)E;
+            for (int j = 0; j < nb; ++j) {
+                const double up = R[j] + sd;
+                const double dn = R[j] - sd;
+                const size_t q = ((size_t)lt * (L + 1) + ln) * nb + j;
+                slo[q] = (int64_t)std::ceil(up * up);
+                shi[q] = dn <= 0.0 ? 0 : (int64_t)std::ceil(dn * dn);
+            }
+        }
+    }
+    treeray_status rc;
+    if ((rc = upload(&c->dt.bin_thr, thr, s)) != TREERAY_OK) return rc;
+    if ((rc = upload(&c->dt.R2, R2, s)) != TREERAY_OK) return rc;
+    if ((rc = upload(&c->dt.Rh, Rh, s)) != TREERAY_OK) return rc;
+    if ((rc = upload(&c->dt.open_max, omax, s)) != TREERAY_OK) return rc;
+    if ((rc = upload(&c->dt.str_lo, slo, s)) != TREERAY_OK) return rc;
+    if ((rc = upload(&c->dt.str_hi, shi, s)) != TREERAY_OK) return rc;
+    TR_CUDA(cudaStreamSynchronize(s));  // host vectors die on return
+    c->tab_lmax = L;
+    c->tab_amr = c->amr;
+    c->built = true;
+    return TREERAY_OK;
+}
+
+}  // namespace tr
+
+using namespace tr;
+
+namespace {
+treeray_status check_ctx(treeray_t c, bool need_tree) {
+    if (!c) {
+        set_error("null context");
+        return TREERAY_EINVAL;
+    }
+    if (need_tree && !c->built) {
+        set_error("no tree: call treeray_build first");
+        return TREERAY_ENOTBUILT;
+    }
+    return TREERAY_OK;
+}
+}  // namespace
+
+extern "C" {
+
+treeray_status treeray_create(const treeray_params* p, treeray_t* out) {
+    set_error("");
+    if (!p || !out) {
+        set_error("null argument");
+        return TREERAY_EINVAL;
+    }
+    *out = nullptr;
+    if (p->npix != 12 && p->npix != 48 && p->npix != 192) {
+        set_error("npix must be 12, 48 or 192");
+        return TREERAY_EINVAL;
+    }
+    if (p->nbins < 1 || p->nbins > kMaxBins) {
+        set_error("nbins must lie in 1..64");
+        return TREERAY_EINVAL;
+    }
+    if (!(p->theta > 0.0) || p->theta > 2.0) {
+        set_error("theta must lie in (0, 2]");
+        return TREERAY_EINVAL;
+    }
+    if (p->kappa_model != 0 && p->kappa_model != 1) {
+        set_error("kappa_model must be 0 or 1");
+        return TREERAY_EINVAL;
+    }
+    if (p->alpha_s < 4 || p->alpha_s > 16 || p->alpha_s % 4 != 0) {
+        set_error("alpha_s must be 4, 8, 12 or 16");
+        return TREERAY_EINVAL;
+    }
+    treeray_ctx* c = new (std::nothrow) treeray_ctx();
+    if (!c) {
+        set_error("out of host memory");
+        return TREERAY_ENOMEM;
+    }
+    c->p = *p;
+    cudaGetDevice(&c->device);
+    c->ht.npix = p->npix;
+    c->ht.nside = healpix_nside(p->npix);
+    c->ht.s = p->alpha_s;
+    std::vector<float> nh(3 * (size_t)p->npix);
+    for (int h = 0; h < p->npix; ++h) {
+        double v[3];
+        healpix_pix2vec(c->ht.nside, h, v);
+        for (int a = 0; a < 3; ++a) nh[3 * h + a] = (float)v[a];
+    }
+    c->ht.nhat = nh;
+    auto fail = [&](treeray_status rc) {
+        free_tables(c->dt);
+        delete c;
+        return rc;
+    };
+    treeray_status rc = upload(&c->dt.nhat, nh, nullptr);
+    if (rc != TREERAY_OK) return fail(rc);
+    if (cudaMalloc(&c->dt.scal, sizeof(double) * 4) != cudaSuccess ||
+        cudaMalloc(&c->dt.err, sizeof(unsigned)) != cudaSuccess ||
+        cudaMalloc(&c->dt.queue, sizeof(unsigned long long)) != cudaSuccess) {
+        set_error("device allocation failed");
+        return fail(TREERAY_ENOMEM);
+    }
+    if (cudaMemset(c->dt.err, 0, sizeof(unsigned)) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess) {
+        set_error("device initialisation failed");
+        return fail(TREERAY_ECUDA);
+    }
+    *out = c;
+    return TREERAY_OK;
+}
+
+treeray_status treeray_destroy(treeray_t c) {
+    if (!c) return TREERAY_OK;
+    free_tree(c->tree);
+    free_tables(c->dt);
+    delete c;
+    return TREERAY_OK;
+}
+
+treeray_status treeray_build(treeray_t c, const treeray_grid* g, const float* rho, const float* Td,
+                             const float* kappa, int n_stars, const double* star_pos,
+                             const double* star_lum, treeray_stream_t stream) {
+    treeray_status rc = check_ctx(c, false);
+    if (rc != TREERAY_OK) return rc;
+    if (!g) {
+        set_error("null grid");
+        return TREERAY_EINVAL;
+    }
+    return build_tree(c, g, rho, Td, kappa, n_stars, star_pos, star_lum, (cudaStream_t)stream);
+}
+
+treeray_status treeray_evaluate(treeray_t c, const int32_t* targets, int64_t n, float* J, double* F,
+                                treeray_stream_t stream) {
+    treeray_status rc = check_ctx(c, true);
+    if (rc != TREERAY_OK) return rc;
+    if (!J || !F || n < 0 || (!targets && n != c->nleaves)) {
+        set_error("evaluate: J and F required; n must equal the leaf count when targets is NULL");
+        return TREERAY_EINVAL;
+    }
+    if (n == 0) return TREERAY_OK;
+    return launch_evaluate(c, targets, n, J, F, (cudaStream_t)stream);
+}
+
+treeray_status treeray_radpressure(treeray_t c, const float* J, const double* F, float* u, float* a_rp,
+                                   float* force, float* p_src, treeray_stream_t stream) {
+    treeray_status rc = check_ctx(c, true);
+    if (rc != TREERAY_OK) return rc;
+    if (!J || !F) {
+        set_error("radpressure: J and F required");
+        return TREERAY_EINVAL;
+    }
+    return launch_radpressure(c, J, F, u, a_rp, force, p_src, (cudaStream_t)stream);
+}
+
+treeray_status treeray_dust_temperature(treeray_t c, const float* Tgas, const float* heat_extra,
+                                        const float* J, float* Td, treeray_stream_t stream) {
+    treeray_status rc = check_ctx(c, true);
+    if (rc != TREERAY_OK) return rc;
+    if (!Tgas || !J || !Td) {
+        set_error("dust_temperature: Tgas, J and Td required");
+        return TREERAY_EINVAL;
+    }
+    return launch_dust(c, Tgas, heat_extra, J, Td, (cudaStream_t)stream);
+}
+
+treeray_status treeray_check(treeray_t c, treeray_stream_t stream) {
+    treeray_status rc = check_ctx(c, false);
+    if (rc != TREERAY_OK) return rc;
+    TR_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    TR_CUDA(cudaGetLastError());
+    unsigned e = 0;
+    TR_CUDA(cudaMemcpy(&e, c->dt.err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (e) {
+        TR_CUDA(cudaMemset(c->dt.err, 0, sizeof(unsigned)));
+        std::string m = "device error:";
+        if (e & kErrStack) m += " walk stack overflow;";
+        if (e & kErrAlphaKey) m += " angular-kernel key outside the table;";
+        if (e & kErrOctree) m += " leaves do not form a complete octree;";
+        if (e & kErrTarget) m += " target index out of range;";
+        set_error(m);
+        return (e & kErrTarget) ? TREERAY_EINVAL : TREERAY_ETIMEOUT;
+    }
+    return TREERAY_OK;
+}
+
+int64_t treeray_leaf_count(treeray_t c) { return c && c->built ? c->nleaves : 0; }
+int64_t treeray_node_count(treeray_t c) { return c && c->built ? c->nnodes : 0; }
+
+treeray_status treeray_tree_export(treeray_t c, int32_t* level, int32_t* leaf, int32_t* child0,
+                                   int64_t* centre, double* vals, treeray_stream_t stream) {
+    treeray_status rc = check_ctx(c, true);
+    if (rc != TREERAY_OK) return rc;
+    const int64_t nn = c->nnodes;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<int4> geo(nn);
+    std::vector<int32_t> perm(c->nleaves);
+    std::vector<double> mom(11 * (size_t)nn);
+    TR_CUDA(cudaMemcpyAsync(geo.data(), c->tree.geo, sizeof(int4) * nn, cudaMemcpyDeviceToHost, s));
+    TR_CUDA(cudaMemcpyAsync(perm.data(), c->tree.perm, sizeof(int32_t) * c->nleaves, cudaMemcpyDeviceToHost, s));
+    TR_CUDA(cudaMemcpyAsync(mom.data(), c->tree.mom, sizeof(double) * 11 * nn, cudaMemcpyDeviceToHost, s));
+    TR_CUDA(cudaStreamSynchronize(s));
+    for (int64_t i = 0; i < nn; ++i) {
+        const int4 g = geo[i];
+        if (level) level[i] = g.z >> 24;
+        if (leaf) leaf[i] = g.w < 0 ? perm[-1 - g.w] : -1;
+        if (child0) child0[i] = g.w < 0 ? -1 : g.w;
+        if (centre) {
+            centre[3 * i] = g.x;
+            centre[3 * i + 1] = g.y;
+            centre[3 * i + 2] = g.z & 0xffffff;
+        }
+        if (vals)
+            for (int q = 0; q < 11; ++q) vals[11 * i + q] = mom[(size_t)q * nn + i];
+    }
+    return TREERAY_OK;
+}
+
+treeray_status treeray_leaf_export(treeray_t c, double* kappa, double* tau, double* jsrc, double* psrc,
+                                   int32_t* thick, treeray_stream_t stream) {
+    treeray_status rc = check_ctx(c, true);
+    if (rc != TREERAY_OK) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = (size_t)c->nleaves;
+    if (kappa) TR_CUDA(cudaMemcpyAsync(kappa, c->tree.kap, 8 * n, cudaMemcpyDeviceToHost, s));
+    if (tau) TR_CUDA(cudaMemcpyAsync(tau, c->tree.tau, 8 * n, cudaMemcpyDeviceToHost, s));
+    if (jsrc) TR_CUDA(cudaMemcpyAsync(jsrc, c->tree.jsrc, 8 * n, cudaMemcpyDeviceToHost, s));
+    if (psrc) TR_CUDA(cudaMemcpyAsync(psrc, c->tree.psrc, 8 * n, cudaMemcpyDeviceToHost, s));
+    if (thick) TR_CUDA(cudaMemcpyAsync(thick, c->tree.thickflag, 4 * n, cudaMemcpyDeviceToHost, s));
+    TR_CUDA(cudaStreamSynchronize(s));
+    return TREERAY_OK;
+}
+
+treeray_status treeray_accepted(treeray_t c, const int32_t* targets, int64_t n, int32_t cap,
+                                int32_t* counts, int32_t* ids, treeray_stream_t stream) {
+    treeray_status rc = check_ctx(c, true);
+    if (rc != TREERAY_OK) return rc;
+    if (!targets || !counts || !ids || n < 0 || cap < 1) {
+        set_error("accepted: targets, counts, ids and cap >= 1 required");
+        return TREERAY_EINVAL;
+    }
+    if (n == 0) return TREERAY_OK;
+    return launch_accepted(c, targets, n, cap, counts, ids, (cudaStream_t)stream);
+}
+
+treeray_status treeray_walk_stats(treeray_t c, const int32_t* targets, int64_t n, int64_t* totals,
+                                  treeray_stream_t stream) {
+    treeray_status rc = check_ctx(c, true);
+    if (rc != TREERAY_OK) return rc;
+    if (!totals || n < 0 || (!targets && n != c->nleaves)) {
+        set_error("walk_stats: totals required; n must equal the leaf count when targets is NULL");
+        return TREERAY_EINVAL;
+    }
+    if (n == 0) return TREERAY_OK;
+    return launch_walk_stats(c, targets, n, totals, (cudaStream_t)stream);
+}
+
+treeray_status treeray_alpha_counts_host(int npix, int s, const int64_t* K, int32_t* counts) {
+    if (healpix_nside(npix) < 0 || s < 4 || s % 4 != 0 || !K || !counts) {
+        set_error("alpha_counts_host: bad arguments");
+        return TREERAY_EINVAL;
+    }
+    alpha_counts(npix, s, K, counts);
+    return TREERAY_OK;
+}
+
+int64_t treeray_kernel_launches(treeray_t c) { return c ? c->launches : 0; }
+
+const char* treeray_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,457 @@
+// Ray evaluation (Secs. 4.2-4.4 of Klepitko et al. 2023): one warp per target.
+//
+// Walk: a shared-memory stack of child groups (the 8 sub-nodes of an opened node are
+// contiguous). Each step pops up to 4 groups, so the 32 lanes test 32 nodes at once;
+// opened nodes push their child group through a ballot compaction, accepted nodes
+// are deposited by their own lane. Open/accept, the segment index, the angular-kernel
+// key and straddled segment boundaries are decided in exact integer arithmetic on the
+// squared centre distance (thresholds built on the host in FP64).
+//
+// Deposit (Secs. 4.2.1-4.2.2): per (segment i, ray h) shared-memory accumulators
+//   thin:  L^ += a b L,  A^ += a b A~          (b = R_i^2 / r_COL^2, a = alpha_node(h))
+//   thick: L^ += a L_V,  A^ += A~,  V^ += a V,  Q^ += a b V, plus straddle flags.
+// Integration (Sec. 4.3): lane = ray, segments inside out, optical-depth prefix sum and
+// thick transmission product in FP64. Finalization (Sec. 4.4): FP64 warp reduction of
+// sum_h F^h and sum_h -F^h n^h.
+//
+// Internal units: lengths in half-cells of the finest level (u cm), luminosities in
+// L_scale erg/s; fluxes come out in L_scale / u^2 and are converted to CGS at the end.
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace tr {
+namespace {
+
+struct EvalArgs {
+    const int4* __restrict__ geo;
+    const float4* __restrict__ thin;
+    const float4* __restrict__ thick;
+    const int32_t* __restrict__ leaf_node;
+    const int32_t* __restrict__ perm;
+    const int32_t* __restrict__ inv_perm;
+    const int32_t* __restrict__ targets;
+    const double* __restrict__ jsrc;
+    const float* __restrict__ nhat;
+    const int32_t* __restrict__ aoff;
+    const uint32_t* __restrict__ aent;
+    const int64_t* __restrict__ bin_thr;
+    const float* __restrict__ R2;
+    const int64_t* __restrict__ open_max;
+    const int64_t* __restrict__ str_lo;
+    const int64_t* __restrict__ str_hi;
+    const double* __restrict__ scal;
+    unsigned* err;
+    unsigned long long* queue;
+    float* J;
+    double* F;
+    int32_t* acc_counts;   // accepted-list mode
+    int32_t* acc_ids;
+    unsigned long long* stats;  // accepted-list mode: totals of visits, accepted, entries
+    int acc_cap;
+    int64_t n;
+    int64_t nleaves;
+    int lmax, nbins, D, stack_cap, npix;
+    double u;
+};
+
+__device__ __forceinline__ int alpha_key(int o, int elog) {
+    // K = 8 o / E when integral, else the nearest odd integer (floor(4 o / E) * 2 + 1)
+    const int e = 8 * o;
+    if ((e & ((1 << elog) - 1)) == 0) return e >> elog;
+    return 2 * ((4 * o) >> elog) + 1;
+}
+
+__device__ __forceinline__ int bin_of(const int64_t* thr, int nbins, int64_t d2) {
+    int i = 0;
+    for (int step = 32; step > 0; step >>= 1)
+        if (i + step < nbins && d2 >= __ldg(thr + i + step)) i += step;
+    return i;
+}
+
+template <int NPIX, bool THICK, bool LIST>
+__global__ void __launch_bounds__(256) k_evaluate(EvalArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int nb = a.nbins;
+    const int cells = nb * NPIX;
+    const int nq = LIST ? 0 : (THICK ? 6 : 2);
+    // per-warp layout: [nq][nb][NPIX] floats, THICK: NPIX uint64 flags, then the stack
+    size_t per_warp = (size_t)nq * cells * 4 + (THICK && !LIST ? NPIX * 8 : 0) + (size_t)a.stack_cap * 4;
+    per_warp = (per_warp + 15) & ~size_t(15);
+    unsigned char* base = smem + per_warp * warp;
+    float* tL = reinterpret_cast<float*>(base);
+    float* tA = tL + cells;
+    float* tLk = tA + cells;
+    float* tAk = tLk + cells;
+    float* tVk = tAk + cells;
+    float* tQk = tVk + cells;
+    unsigned long long* flags = reinterpret_cast<unsigned long long*>(base + (size_t)nq * cells * 4);
+    int* stack = reinterpret_cast<int*>(base + (size_t)nq * cells * 4 + (THICK && !LIST ? NPIX * 8 : 0));
+    const unsigned full = 0xffffffffu;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const float omega = (float)(4.0 * kPi / NPIX);
+    const float inv_s3 = 1.0f / 512.0f;
+    const int W = 2 * a.D + 1;
+    (void)nw;
+
+    for (;;) {
+        long long q = 0;
+        if (lane == 0) q = (long long)atomicAdd(a.queue, 1ull);
+        q = __shfl_sync(full, q, 0);
+        if (q >= a.n) break;
+        int64_t s;
+        int64_t out;
+        if (a.targets) {
+            const int32_t k = a.targets[q];
+            if (k < 0 || k >= a.nleaves) {
+                if (lane == 0) atomicOr(a.err, kErrTarget);
+                continue;
+            }
+            s = a.inv_perm[k];
+            out = q;
+        } else {
+            s = q;
+            out = a.perm[s];
+        }
+        const int tnode = a.leaf_node[s];
+        const int4 tg = a.geo[tnode];
+        const int tx = tg.x, ty = tg.y, tz = tg.z & 0xffffff;
+        const int tl = tg.z >> 24;
+        const int64_t* thr = a.bin_thr + (int64_t)tl * nb;
+        const float* R2 = a.R2 + (int64_t)tl * nb;
+
+        if (!LIST) {
+            for (int i = lane; i < nq * cells; i += 32) tL[i] = 0.0f;
+            if (THICK)
+                for (int h = lane; h < NPIX; h += 32) flags[h] = 0ull;
+        }
+        int nacc = 0;
+        long long nvis = 0, nent = 0;
+        int sp = 0;
+        const int4 root = a.geo[0];
+        if (root.w >= 0) {
+            if (lane == 0) stack[0] = root.w;
+            sp = 1;
+        }
+        bool overflow = false;
+        __syncwarp();
+        while (sp > 0) {
+            const int ng = sp < 4 ? sp : 4;
+            const int g = lane >> 3;
+            const bool valid = g < ng;
+            const int node = valid ? stack[sp - ng + g] + (lane & 7) : 0;
+            __syncwarp();
+            sp -= ng;
+            bool open = false, acc = false;
+            int4 gg = make_int4(0, 0, 0, 0);
+            int ox = 0, oy = 0, oz = 0, lvl = 0;
+            int64_t d2 = 0;
+            if (valid) {
+                gg = __ldg(a.geo + node);
+                lvl = gg.z >> 24;
+                ox = gg.x - tx;
+                oy = gg.y - ty;
+                oz = (gg.z & 0xffffff) - tz;
+                d2 = (int64_t)ox * ox + (int64_t)oy * oy + (int64_t)oz * oz;
+                if (gg.w >= 0) {
+                    const int E = 2 << (a.lmax - lvl);
+                    const bool inside = 2 * abs(ox) < E && 2 * abs(oy) < E && 2 * abs(oz) < E;
+                    open = inside || d2 <= __ldg(a.open_max + lvl);
+                }
+                acc = !open;
+            }
+            const unsigned om = __ballot_sync(full, open);
+            if (open) {
+                const int pos = sp + __popc(om & lt_mask);
+                if (pos < a.stack_cap) stack[pos] = gg.w;
+            }
+            sp += __popc(om);
+            if (sp > a.stack_cap) {
+                overflow = true;
+                break;
+            }
+            if (LIST) {
+                const unsigned am = __ballot_sync(full, acc);
+                if (acc && a.acc_ids) {
+                    const int pos = nacc + __popc(am & lt_mask);
+                    if (pos < a.acc_cap) a.acc_ids[q * (int64_t)a.acc_cap + pos] = node;
+                }
+                nacc += __popc(am);
+                nvis += __popc(__ballot_sync(full, valid));
+                if (a.stats && acc && d2 != 0) {
+                    const int elog = a.lmax - lvl + 1;
+                    const int Kx = alpha_key(ox, elog), Ky = alpha_key(oy, elog), Kz = alpha_key(oz, elog);
+                    if (abs(Kx) <= a.D && abs(Ky) <= a.D && abs(Kz) <= a.D) {
+                        const int idx = ((Kz + a.D) * W + (Ky + a.D)) * W + (Kx + a.D);
+                        nent += __ldg(a.aoff + idx + 1) - __ldg(a.aoff + idx);
+                    }
+                }
+            } else if (acc && d2 != 0) {
+                // ---- map the accepted node onto the rays
+                const int i = bin_of(thr, nb, d2);
+                const float4 v0 = __ldg(a.thin + node);
+                const float4 v1 = __ldg(a.thick + node);
+                const float rx = (float)ox + v0.z, ry = (float)oy + v0.w, rz = (float)oz + v1.x;
+                const float beta = __ldg(R2 + i) / (rx * rx + ry * ry + rz * rz);
+                const int elog = a.lmax - lvl + 1;
+                const int Kx = alpha_key(ox, elog), Ky = alpha_key(oy, elog), Kz = alpha_key(oz, elog);
+                if (abs(Kx) > a.D || abs(Ky) > a.D || abs(Kz) > a.D) {
+                    atomicOr(a.err, kErrAlphaKey);
+                } else {
+                    const int idx = ((Kz + a.D) * W + (Ky + a.D)) * W + (Kx + a.D);
+                    const int e0 = __ldg(a.aoff + idx), e1 = __ldg(a.aoff + idx + 1);
+                    if (e1 == e0) atomicOr(a.err, kErrAlphaKey);
+                    const float bL = beta * v0.x, bA = beta * v0.y;
+                    bool thick_here = THICK && v1.w > 0.0f;
+                    unsigned long long fmask = 0ull;
+                    if (THICK && thick_here) {
+                        const int64_t* lo = a.str_lo + ((int64_t)tl * (a.lmax + 1) + lvl) * nb;
+                        const int64_t* hi = a.str_hi + ((int64_t)tl * (a.lmax + 1) + lvl) * nb;
+                        int ilo = 0, ihi = 0;
+                        for (int j = 1; j < nb; ++j) {
+                            ilo += d2 >= __ldg(lo + j);
+                            ihi += d2 >= __ldg(hi + j);
+                        }
+                        for (int j = ilo; j < ihi; ++j) fmask |= 1ull << j;
+                    }
+                    for (int e = e0; e < e1; ++e) {
+                        const uint32_t ent = __ldg(a.aent + e);
+                        const int h = (int)(ent & 0xffffu);
+                        const float w = (float)(ent >> 16) * inv_s3;
+                        const int cidx = i * NPIX + h;
+                        atomicAdd(tL + cidx, w * bL);
+                        atomicAdd(tA + cidx, w * bA);
+                        if (THICK && thick_here) {
+                            atomicAdd(tLk + cidx, w * v1.y);
+                            atomicAdd(tAk + cidx, v1.z);
+                            atomicAdd(tVk + cidx, w * v1.w);
+                            atomicAdd(tQk + cidx, w * beta * v1.w);
+                            if (fmask) atomicOr(flags + h, fmask);
+                        }
+                    }
+                }
+            }
+        }
+        overflow = __any_sync(full, overflow);
+        if (overflow) {
+            if (lane == 0) atomicOr(a.err, kErrStack);
+            continue;
+        }
+        if (LIST) {
+            if (a.acc_counts && lane == 0) a.acc_counts[q] = nacc;
+            if (a.stats) {
+                for (int off = 16; off > 0; off >>= 1) nent += __shfl_xor_sync(full, nent, off);
+                if (lane == 0) {
+                    atomicAdd(a.stats + 0, (unsigned long long)(nvis + 1));
+                    atomicAdd(a.stats + 1, (unsigned long long)nacc + (root.w >= 0 ? 0ull : 1ull));
+                    atomicAdd(a.stats + 2, (unsigned long long)nent);
+                }
+            }
+            __syncwarp();
+            continue;
+        }
+        __syncwarp();
+        // ---- own cell: bin 0 of every ray, alpha = 1/N_pix, beta = 1
+        {
+            const float4 v0 = __ldg(a.thin + tnode);
+            const float4 v1 = __ldg(a.thick + tnode);
+            unsigned long long fmask = 0ull;
+            if (THICK && v1.w > 0.0f) {
+                const int64_t* hi = a.str_hi + ((int64_t)tl * (a.lmax + 1) + tl) * nb;
+                int ihi = 0;
+                for (int j = 1; j < nb; ++j) ihi += 0 >= __ldg(hi + j);
+                for (int j = 0; j < ihi; ++j) fmask |= 1ull << j;
+            }
+            const float w = 1.0f / NPIX;
+            for (int h = lane; h < NPIX; h += 32) {
+                tL[h] += w * v0.x;
+                tA[h] += w * v0.y;
+                if (THICK && v1.w > 0.0f) {
+                    tLk[h] += w * v1.y;
+                    tAk[h] += v1.z;
+                    tVk[h] += w * v1.w;
+                    tQk[h] += w * v1.w;
+                    flags[h] |= fmask;
+                }
+            }
+        }
+        __syncwarp();
+        // ---- integrate each ray from the inside out (lane = ray)
+        double Js = 0.0, Fx = 0.0, Fy = 0.0, Fz = 0.0;
+        for (int h = lane; h < NPIX; h += 32) {
+            if (THICK) {
+                const unsigned long long fl = flags[h];
+                if (fl)
+                    for (int i = nb - 2; i >= 0; --i) {
+                        if (!((fl >> i) & 1ull)) continue;
+                        const int c0 = i * NPIX + h, c1 = (i + 1) * NPIX + h;
+                        const float T = __ldg(R2 + i) / __ldg(R2 + i + 1);
+                        tL[c0] += T * tL[c1];
+                        tA[c0] += T * tA[c1];
+                        tQk[c0] += T * tQk[c1];
+                        tLk[c0] += tLk[c1];
+                        tAk[c0] += tAk[c1];
+                        tVk[c0] += tVk[c1];
+                        tL[c1] = tA[c1] = tQk[c1] = tLk[c1] = tAk[c1] = tVk[c1] = 0.0f;
+                    }
+            }
+            double tcum = 0.0, ek = 1.0, Fh = 0.0;
+            for (int i = 0; i < nb; ++i) {
+                const int ci = i * NPIX + h;
+                const float R2i = __ldg(R2 + i);
+                const float Lth = tL[ci], Ath = tA[ci];
+                const float tth = i == 0 ? 0.0f : Ath / (omega * R2i);
+                float f = 0.0f, Fk = 0.0f, Akv = 0.0f, tk = 0.0f;
+                if (THICK) {
+                    const float Vk = tVk[ci];
+                    if (Vk > 0.0f) {
+                        const float cb = cbrtf(Vk);
+                        float wk = (tQk[ci] / Vk) * (cb * cb) / R2i;
+                        wk = fminf(wk, omega);
+                        f = wk / omega;
+                        Akv = tAk[ci];
+                        tk = (i == 0 || wk == 0.0f) ? 0.0f : Akv / (wk * R2i);
+                        Fk = wk * tLk[ci] / Vk;
+                    }
+                }
+                const float g = tth < 1e-4f ? 1.0f : -expm1f(-tth) / tth;
+                const float Fth = g * Lth / (4.0f * (float)kPi * R2i);
+                const float den = Ath + f * Akv;
+                const float Fs = den > 0.0f ? (Fth * Ath + Fk * f * Akv) / den : Fth + Fk;
+                const float eps = expf(-(float)tcum) * (float)ek;
+                Fh += (double)(eps * Fs);
+                tcum += (double)tth;
+                if (THICK && f > 0.0f) ek *= (double)((1.0f - f) + f * expf(-tk));
+            }
+            Js += Fh;
+            Fx -= Fh * (double)__ldg(a.nhat + 3 * h);
+            Fy -= Fh * (double)__ldg(a.nhat + 3 * h + 1);
+            Fz -= Fh * (double)__ldg(a.nhat + 3 * h + 2);
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            Js += __shfl_xor_sync(full, Js, off);
+            Fx += __shfl_xor_sync(full, Fx, off);
+            Fy += __shfl_xor_sync(full, Fy, off);
+            Fz += __shfl_xor_sync(full, Fz, off);
+        }
+        if (lane == 0) {
+            const double Fu = a.scal[0] / (a.u * a.u);  // internal flux unit in erg/s/cm^2
+            const int64_t k = a.perm[s];
+            a.J[out] = (float)(Js / (4.0 * kPi) * Fu + a.jsrc[k]);
+            a.F[3 * out] = Fx * Fu;
+            a.F[3 * out + 1] = Fy * Fu;
+            a.F[3 * out + 2] = Fz * Fu;
+        }
+        __syncwarp();
+    }
+}
+
+template <int NPIX, bool THICK, bool LIST>
+treeray_status launch_t(treeray_ctx* c, EvalArgs a, cudaStream_t s) {
+    const int nq = LIST ? 0 : (THICK ? 6 : 2);
+    size_t per_warp = (size_t)nq * a.nbins * NPIX * 4 + (THICK && !LIST ? NPIX * 8 : 0) + (size_t)a.stack_cap * 4;
+    per_warp = (per_warp + 15) & ~size_t(15);
+    int smem_optin = 0, sms = 0;
+    TR_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+    TR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+    // warps per block: up to 8 (thin) or 4 (thick) targets, limited by the per-block shared memory
+    int warps = THICK ? 4 : 8;
+    while (warps > 1 && per_warp * warps > (size_t)smem_optin) --warps;
+    if (per_warp * warps > (size_t)smem_optin) {
+        set_error("evaluate: the per-target ray tile (npix x nbins) exceeds shared memory");
+        return TREERAY_EINVAL;
+    }
+    const size_t smem = per_warp * warps;
+    auto kern = k_evaluate<NPIX, THICK, LIST>;
+    TR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    TR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem));
+    if (per_sm < 1) {
+        set_error("evaluate: kernel does not fit on an SM");
+        return TREERAY_EINVAL;
+    }
+    int64_t blocks = (int64_t)per_sm * sms;
+    const int64_t need = (a.n + warps - 1) / warps;
+    if (blocks > need) blocks = need;
+    if (blocks < 1) blocks = 1;
+    TR_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), s));
+    kern<<<(int)blocks, warps * 32, smem, s>>>(a);
+    c->launches += 1;
+    TR_CUDA(cudaGetLastError());
+    return TREERAY_OK;
+}
+
+template <bool LIST>
+treeray_status dispatch(treeray_ctx* c, EvalArgs a, cudaStream_t s) {
+    const bool thick = c->has_thick && !LIST;
+    switch (c->p.npix) {
+        case 12: return thick ? launch_t<12, true, LIST>(c, a, s) : launch_t<12, false, LIST>(c, a, s);
+        case 48: return thick ? launch_t<48, true, LIST>(c, a, s) : launch_t<48, false, LIST>(c, a, s);
+        case 192: return thick ? launch_t<192, true, LIST>(c, a, s) : launch_t<192, false, LIST>(c, a, s);
+    }
+    set_error("evaluate: npix must be 12, 48 or 192");
+    return TREERAY_EINVAL;
+}
+
+EvalArgs make_args(treeray_ctx* c, const int32_t* targets, int64_t n) {
+    EvalArgs a{};
+    a.geo = c->tree.geo;
+    a.thin = c->tree.thin;
+    a.thick = c->tree.thick;
+    a.leaf_node = c->tree.leaf_node;
+    a.perm = c->tree.perm;
+    a.inv_perm = c->tree.inv_perm;
+    a.targets = targets;
+    a.jsrc = c->tree.jsrc;
+    a.nhat = c->dt.nhat;
+    a.aoff = c->dt.alpha_off;
+    a.aent = c->dt.alpha_ent;
+    a.bin_thr = c->dt.bin_thr;
+    a.R2 = c->dt.R2;
+    a.open_max = c->dt.open_max;
+    a.str_lo = c->dt.str_lo;
+    a.str_hi = c->dt.str_hi;
+    a.scal = c->dt.scal;
+    a.err = c->dt.err;
+    a.queue = c->dt.queue;
+    a.n = n;
+    a.nleaves = c->nleaves;
+    a.lmax = c->lmax;
+    a.nbins = c->p.nbins;
+    a.D = c->ht.D;
+    a.npix = c->p.npix;
+    a.u = c->u;
+    // the stack holds at most 28 leftover groups per level plus one batch of pushes
+    a.stack_cap = 28 * (c->lmax + 1) + 40;
+    return a;
+}
+
+}  // namespace
+
+treeray_status launch_evaluate(treeray_ctx* c, const int32_t* targets, int64_t n, float* J, double* F,
+                               cudaStream_t s) {
+    EvalArgs a = make_args(c, targets, n);
+    a.J = J;
+    a.F = F;
+    return dispatch<false>(c, a, s);
+}
+
+treeray_status launch_accepted(treeray_ctx* c, const int32_t* targets, int64_t n, int32_t cap,
+                               int32_t* counts, int32_t* ids, cudaStream_t s) {
+    EvalArgs a = make_args(c, targets, n);
+    a.acc_counts = counts;
+    a.acc_ids = ids;
+    a.acc_cap = cap;
+    return dispatch<true>(c, a, s);
+}
+
+treeray_status launch_walk_stats(treeray_ctx* c, const int32_t* targets, int64_t n, int64_t* totals,
+                                 cudaStream_t s) {
+    EvalArgs a = make_args(c, targets, n);
+    a.stats = reinterpret_cast<unsigned long long*>(totals);
+    a.acc_cap = 0;
+    return dispatch<true>(c, a, s);
+}
+
+}  // namespace tr

@@ -1,0 +1,122 @@
+// Per-leaf epilogues: radiation energy density and pressure (Sec. 4.5) and the
+// equilibrium dust temperature (Sec. 4.6, App. D). Plain elementwise kernels in FP64.
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace tr {
+namespace {
+
+struct RpArgs {
+    const float* J;
+    const double* F;
+    const double* kap;
+    const double* tau;
+    const double* psrc;
+    const float* rho;
+    const int4* geo;
+    const int32_t* leaf_node;
+    const int32_t* inv_perm;
+    float *u, *a, *f, *p;
+    int64_t n;
+    double box;
+};
+
+// u = 4 pi J / c; P_dot = (F/c) kappa rho g(tau) dV with g = (1 - e^-tau)/tau (1 for tau < 1e-4);
+// a_RP = P_dot / (rho dV) = (F/c) kappa g
+__global__ void k_radpressure(RpArgs r) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= r.n) return;
+    const int lvl = r.geo[r.leaf_node[r.inv_perm[k]]].z >> 24;
+    const double dx = ldexp(r.box, -lvl);
+    const double dV = (dx * dx) * dx;
+    const double tau = r.tau[k];
+    const double g = tau < 1e-4 ? 1.0 : -expm1(-tau) / tau;
+    const double kap = r.kap[k];
+    const double kr = kap * (double)r.rho[k];
+    if (r.u) r.u[k] = (float)(4.0 * kPi * (double)r.J[k] / kLightC);
+    for (int ax = 0; ax < 3; ++ax) {
+        const double Fc = r.F[3 * k + ax] / kLightC;
+        if (r.f) r.f[3 * k + ax] = (float)(Fc * kr * g * dV);
+        if (r.a) r.a[3 * k + ax] = (float)(Fc * kap * g);
+    }
+    if (r.p) r.p[k] = (float)r.psrc[k];
+}
+
+struct DustArgs {
+    const float* rho;
+    const float* tgas;
+    const float* heat;
+    const float* J;
+    const float* kin;
+    float* Td;
+    int64_t n;
+    int model;
+    double kappa0, xi;
+};
+
+__device__ inline double kappa_of(const DustArgs& d, int64_t k, double T) {
+    if (d.kin) return (double)d.kin[k];
+    if (d.model == 0) return d.kappa0;
+    const double Tc = T < 150.0 ? T : 150.0;
+    return 1.0e-3 * (Tc * Tc);
+}
+
+// G(T) = Gamma_dust-gas + heat + rho kappa(T) (4 pi J - 4 sigma T^4)
+__device__ inline double balance(const DustArgs& d, int64_t k, double T, double rho, double Tg, double J,
+                                 double H) {
+    const double kap = kappa_of(d, k, T);
+    const double nH = kHydrogenFraction * rho / kHydrogenMass;
+    const double gd = 3.8e-33 * sqrt(Tg) * (Tg - T) * (1.0 - 0.8 * exp(-75.0 / Tg)) * (nH * nH) * (d.xi / 0.01);
+    const double T4 = (T * T) * (T * T);
+    return gd + H + rho * kap * (4.0 * kPi * J - 4.0 * kSigmaSB * T4);
+}
+
+// root by bracketing from the 2.7 K floor and 60 bisections in ln T
+__global__ void k_dust(DustArgs d) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= d.n) return;
+    const double rho = (double)d.rho[k], Tg = (double)d.tgas[k], J = (double)d.J[k];
+    const double H = d.heat ? (double)d.heat[k] : 0.0;
+    double T;
+    if (balance(d, k, kDustFloorK, rho, Tg, J, H) <= 0.0) {
+        T = kDustFloorK;
+    } else {
+        const double TJ = sqrt(sqrt(kPi * (J > 0.0 ? J : 0.0) / kSigmaSB));
+        double hi = Tg > TJ ? Tg : TJ;
+        if (hi < kDustFloorK) hi = kDustFloorK;
+        for (int it = 0; it < 64 && balance(d, k, hi, rho, Tg, J, H) > 0.0; ++it) hi *= 2.0;
+        double lo = kDustFloorK;
+        for (int it = 0; it < 60; ++it) {
+            const double mid = sqrt(lo * hi);
+            if (balance(d, k, mid, rho, Tg, J, H) > 0.0) lo = mid;
+            else hi = mid;
+        }
+        T = sqrt(lo * hi);
+    }
+    d.Td[k] = (float)T;
+}
+
+}  // namespace
+
+treeray_status launch_radpressure(treeray_ctx* c, const float* J, const double* F, float* u, float* a,
+                                  float* f, float* p, cudaStream_t s) {
+    RpArgs r{J, F, c->tree.kap, c->tree.tau, c->tree.psrc, c->tree.rho, c->tree.geo, c->tree.leaf_node,
+             c->tree.inv_perm, u, a, f, p, c->nleaves, c->box};
+    k_radpressure<<<(int)((c->nleaves + 255) / 256), 256, 0, s>>>(r);
+    c->launches += 1;
+    TR_CUDA(cudaGetLastError());
+    return TREERAY_OK;
+}
+
+treeray_status launch_dust(treeray_ctx* c, const float* Tgas, const float* heat, const float* J, float* Td,
+                           cudaStream_t s) {
+    DustArgs d{c->tree.rho, Tgas, heat, J, c->kin_given ? c->tree.kin : nullptr, Td, c->nleaves,
+               c->p.kappa_model, c->p.kappa0, c->p.dust_to_gas};
+    k_dust<<<(int)((c->nleaves + 127) / 128), 128, 0, s>>>(d);
+    c->launches += 1;
+    TR_CUDA(cudaGetLastError());
+    return TREERAY_OK;
+}
+
+}  // namespace tr

@@ -1,0 +1,182 @@
+"""GPU parity against the FP64 oracle, through the C ABI (marked gpu).
+
+Tree structure and node lists: bit-exact. FP64 node moments: bit-exact where only
++, x, / enter; within 1e-14 relative where exp or cbrt do (star luminosity S,
+J_src, P_src, xi, COL). Ray evaluation (FP32 bulk, FP64 prefix sums and
+reductions): J within 1e-4 relative, F within 1e-4 of max(|F|, 1e-2 x 4 pi J).
+"""
+import numpy as np
+import pytest
+
+import synth
+from gpu_util import build_ctx, evaluate, flux_err
+
+pytestmark = pytest.mark.gpu
+
+J_TOL = 1e-4
+F_TOL = 1e-4
+
+
+def _oracle(orc, w):
+    return orc.Tree(w)
+
+
+CASES = {
+    "clump16": lambda: synth.gaussian_clump(16),
+    "rand16_thick": lambda: synth.random_uniform(16, seed=5, thick_frac=0.15, n_stars=3),
+    "point16": lambda: synth.point_source(16, kappa0=1.0),
+    "blob16": lambda: synth.thick_blob(16),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_tree_bit_exact(orc, name):
+    w = CASES[name]()
+    o = _oracle(orc, w).export()
+    ctx, _ = build_ctx(w)
+    g = ctx.tree_export()
+    for k in ("level", "leaf", "child0", "centre"):
+        assert (g[k] == o[k]).all(), k
+    exact = [0, 1, 2, 3, 4, 5, 6] if len(w.star_lum) == 0 else [1, 2, 3, 4, 5, 6]
+    for q in exact:
+        assert (g["vals"][:, q] == o["vals"][:, q]).all(), q
+    assert np.allclose(g["vals"], o["vals"], rtol=1e-14, atol=0)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_leaf_quantities(orc, name):
+    w = CASES[name]()
+    o = _oracle(orc, w).leaves()
+    ctx, _ = build_ctx(w)
+    g = ctx.leaf_export()
+    for k in ("kappa", "tau", "thick"):
+        assert (g[k] == o[k]).all(), k
+    for k in ("jsrc", "psrc"):
+        assert np.allclose(g[k], o[k], rtol=1e-14, atol=0), k
+
+
+@pytest.mark.parametrize("name", ["clump16", "rand16_thick"])
+def test_accepted_lists_bit_exact(orc, name):
+    import torch
+    w = CASES[name]()
+    t = _oracle(orc, w)
+    ctx, _ = build_ctx(w)
+    tg = synth.sample_targets(w.n_leaves, 300, seed=1)
+    counts, ids = ctx.accepted(torch.as_tensor(tg, dtype=torch.int32, device="cuda:0"))
+    counts = counts.cpu().numpy()
+    ids = ids.cpu().numpy()
+    for q, k in enumerate(tg):
+        ref = np.sort(t.accepted(int(k)))
+        assert counts[q] == len(ref)
+        assert (np.sort(ids[q, :counts[q]]) == ref).all()
+
+
+def _parity(orc, w, targets=None, params=None):
+    if params is not None:
+        w.params = dict(params)
+    t = _oracle(orc, w)
+    Jr, Fr = t.evaluate(targets)
+    ctx, _ = build_ctx(w)
+    J, F = evaluate(ctx, targets)
+    ej = np.abs(J / Jr - 1)
+    ef = flux_err(F, Fr, Jr)
+    return ej, ef
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_evaluate_all_targets(orc, name):
+    ej, ef = _parity(orc, CASES[name]())
+    assert ej.max() <= J_TOL, (ej.max(), np.argmax(ej))
+    assert ef.max() <= F_TOL, (ef.max(), np.argmax(ef))
+
+
+def test_evaluate_clump32_all_targets(orc):
+    """The 32^3 Gaussian clump at 48 rays, 20 bins, theta 0.5 (every target)."""
+    ej, ef = _parity(orc, synth.gaussian_clump(32))
+    print(f"clump32: J max {ej.max():.2e} p99 {np.percentile(ej, 99):.2e}; "
+          f"F max {ef.max():.2e} p99 {np.percentile(ef, 99):.2e}")
+    assert ej.max() <= J_TOL and ef.max() <= F_TOL
+
+
+@pytest.mark.parametrize("npix", [12, 48, 192])
+def test_evaluate_ragged_subset_npix(orc, npix):
+    w = synth.random_uniform(16, seed=9, thick_frac=0.1, npix=npix, nbins=16)
+    tg = synth.sample_targets(w.n_leaves, 1001, seed=3)  # ragged count
+    ej, ef = _parity(orc, w, tg)
+    assert ej.max() <= J_TOL and ef.max() <= F_TOL
+
+
+@pytest.mark.parametrize("npix", [48, 192])
+def test_evaluate_turbulent128_sampled(orc, npix):
+    """Lognormal 128^3 cloud with a 1e5 Lsun star, sampled targets (full-size tree)."""
+    w = synth.turbulent_cloud(128, npix=npix)
+    tg = synth.sample_targets(w.n_leaves, 512, seed=4)
+    ej, ef = _parity(orc, w, tg)
+    print(f"turb128 npix {npix}: J max {ej.max():.2e}; F max {ef.max():.2e}")
+    assert ej.max() <= J_TOL and ef.max() <= F_TOL
+
+
+def test_radpressure_and_dust(orc):
+    import torch
+    w = synth.with_gas(synth.random_uniform(16, seed=2, thick_frac=0.1), heat_scale=1e-25)
+    t = _oracle(orc, w)
+    ctx, _ = build_ctx(w)
+    J, F = evaluate(ctx)
+    dev = "cuda:0"
+    Jt = torch.as_tensor(J, dtype=torch.float32, device=dev)
+    Ft = torch.as_tensor(F.reshape(-1), dtype=torch.float64, device=dev)
+    n = w.n_leaves
+    u, a, f, p = (torch.empty(k, dtype=torch.float32, device=dev) for k in (n, 3 * n, 3 * n, n))
+    ctx.radpressure(Jt, Ft, u, a, f, p)
+    ctx.check()
+    ur, ar, fr, pr = t.radpressure(Jt.double().cpu().numpy(), F)
+    assert np.allclose(u.cpu().numpy(), ur, rtol=1e-6, atol=0)
+    assert np.allclose(a.cpu().numpy().reshape(n, 3), ar, rtol=1e-6, atol=1e-30)
+    assert np.allclose(f.cpu().numpy().reshape(n, 3), fr, rtol=1e-6, atol=1e-30)
+    assert np.allclose(p.cpu().numpy(), pr, rtol=1e-6, atol=0)
+    tg = torch.as_tensor(w.tgas, device=dev)
+    ht = torch.as_tensor(w.heat_extra, device=dev)
+    Td = torch.empty(n, dtype=torch.float32, device=dev)
+    ctx.dust_temperature(tg, Jt, Td, heat_extra=ht)
+    ctx.check()
+    Tr = orc.dust_temperature(w.params, w.rho, w.tgas, Jt.double().cpu().numpy(), w.heat_extra)
+    assert np.allclose(Td.cpu().numpy(), Tr, rtol=2e-7, atol=0)
+
+
+def test_errors_are_reported():
+    import torch
+
+    import paper_2204_09072_gb300 as tr
+    with pytest.raises(tr.TreeRayError) as e:
+        tr.Context(synth.default_params(npix=50))
+    assert e.value.code == 1
+    ctx = tr.Context(synth.default_params())
+    J = torch.empty(4, dtype=torch.float32, device="cuda:0")
+    F = torch.empty(12, dtype=torch.float64, device="cuda:0")
+    with pytest.raises(tr.TreeRayError) as e:
+        ctx.evaluate(J, F, targets=torch.zeros(4, dtype=torch.int32, device="cuda:0"))
+    assert e.value.code == 4
+    w = synth.gaussian_clump(8)
+    ctx2, _ = build_ctx(w)
+    bad = torch.tensor([0, 5, 100000, 3], dtype=torch.int32, device="cuda:0")
+    ctx2.evaluate(J, F, targets=bad)
+    with pytest.raises(tr.TreeRayError) as e:
+        ctx2.check()
+    assert e.value.code == 1
+    # an incomplete AMR octree is rejected at build time
+    with pytest.raises(tr.TreeRayError):
+        ctx2.build(1.0, torch.ones(512, device="cuda:0"), torch.ones(512, device="cuda:0"),
+                   blocks=np.array([[0, 0, 0, 4]]))
+
+
+@pytest.mark.parametrize("name", ["clump16", "rand16_thick"])
+def test_walk_stats_exact(orc, name):
+    """Visited/accepted/angular-entry totals of the GPU walk equal the oracle's."""
+    import torch
+    w = CASES[name]()
+    t = _oracle(orc, w)
+    ctx, _ = build_ctx(w)
+    tg = synth.sample_targets(w.n_leaves, 200, seed=8)
+    ref = np.array([t.walk_stats(int(k)) for k in tg]).sum(0)
+    got = ctx.walk_stats(torch.as_tensor(tg, dtype=torch.int32, device="cuda:0")).cpu().numpy()
+    assert (got == ref).all(), (got, ref)
