@@ -90,7 +90,7 @@ def _grf(n: int, slope: float, rng: np.random.Generator) -> np.ndarray:
     k2[0, 0, 0] = 1.0
     amp = k2 ** (slope / 4.0)   # sqrt(P) = k^(slope/2)
     amp[0, 0, 0] = 0.0
-    g = np.fft.irfftn(fk * amp, s=(n, n, n))
+    g = np.fft.irfftn(fk * amp, s=(n, n, n), axes=(0, 1, 2))
     g -= g.mean()
     g /= g.std()
     return g.reshape(-1)
@@ -283,6 +283,7 @@ def amr_core(n_base_blocks: int = 2, max_level: int = 5, box_pc: float = 0.4,
     cell = np.indices((8, 8, 8)).reshape(3, -1).T[:, ::-1].astype(np.int32)  # x fastest
     ijk = (blocks[:, None, :3] * 8 + cell[None, :, :]).reshape(-1, 3).astype(np.int32)
     lev = np.repeat(blocks[:, 3], 512).astype(np.int32)
+    lmax = int(lev.max())  # the deepest leaf level actually present
     cen = (ijk.astype(np.float64) + 0.5) * (box / (2.0 ** lev))[:, None]
     rho = density(cen)
     r = np.sqrt(((cen - 0.5 * box) ** 2).sum(-1))

@@ -23,6 +23,7 @@ def _oracle(orc, w):
 
 CASES = {
     "clump16": lambda: synth.gaussian_clump(16),
+    "amr": lambda: synth.amr_core(n_base_blocks=2, max_level=2, target_leaves=24 * 512, n_stars=3),
     "rand16_thick": lambda: synth.random_uniform(16, seed=5, thick_frac=0.15, n_stars=3),
     "point16": lambda: synth.point_source(16, kappa0=1.0),
     "blob16": lambda: synth.thick_blob(16),
