@@ -205,6 +205,28 @@ treeray_status treeray_walk_stats(treeray_t ctx, const int32_t* targets, int64_t
                                   int64_t* totals, treeray_stream_t stream);
 
 /*
+ * Morton ordering of the leaves without any device allocation. The paper has no
+ * counterpart: this entry point exists for callers that cannot call cudaMalloc, such
+ * as a host simulation code whose own pool allocator owns all device memory and
+ * forbids allocations by the libraries it links, or a caller issuing work from a
+ * region where allocation is not allowed. It computes the same ordering as the first
+ * step of treeray_build (Morton key of each leaf's lower corner at the finest level,
+ * prefixed by the leaf's level; stable radix sort) and needs no context.
+ *  grid   as for treeray_build, at most 524288 leaves (AMR: at most 1024 blocks);
+ *         larger grids return TREERAY_EINVAL.
+ *  keys   device uint64[N] output, sorted keys (level << 3 lmax | Morton code).
+ *  perm   device int32[N] output, caller leaf index of each sorted position.
+ * All scratch memory (6.2 MiB) is one fixed device array inside the library, held by
+ * every GPU that loads the library until the process exits. The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress), so make the
+ * first call on each device before any stream capture. Every call shares the array
+ * and it keeps the last call's contents; calls whose work overlaps on the GPU (on
+ * different streams, or from different threads) race on it, so serialise them.
+ */
+treeray_status treeray_morton_order_noalloc(const treeray_grid* grid, uint64_t* keys,
+                                            int32_t* perm, treeray_stream_t stream);
+
+/*
  * Host-only: angular-kernel hit counts of key K (three ints) for npix rays and s samples
  * per axis, written to counts[npix]. Needs no GPU; used to check the table builder.
  */

@@ -72,13 +72,14 @@ def lib():
     L.treeray_accepted.argtypes = [vp, vp, i64, C.c_int32, vp, vp, vp]
     L.treeray_alpha_counts_host.argtypes = [C.c_int, C.c_int, vp, i32p]
     L.treeray_walk_stats.argtypes = [vp, vp, i64, vp, vp]
+    L.treeray_morton_order_noalloc.argtypes = [C.POINTER(Grid), vp, vp, vp]
     L.treeray_kernel_launches.argtypes = [vp]
     L.treeray_kernel_launches.restype = i64
     L.treeray_last_error.restype = C.c_char_p
     for f in ("treeray_create", "treeray_destroy", "treeray_build", "treeray_evaluate",
               "treeray_radpressure", "treeray_dust_temperature", "treeray_check",
               "treeray_tree_export", "treeray_leaf_export", "treeray_accepted",
-              "treeray_alpha_counts_host", "treeray_walk_stats"):
+              "treeray_alpha_counts_host", "treeray_walk_stats", "treeray_morton_order_noalloc"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -115,6 +116,24 @@ def alpha_counts_host(npix: int, s: int, K):
     _raise(lib().treeray_alpha_counts_host(npix, s, C.c_void_p(k.ctypes.data),
                                            out.ctypes.data_as(C.POINTER(C.c_int32))))
     return out
+
+
+def morton_order_noalloc(box: float, keys, perm, n: int = 0, blocks=None, stream=None):
+    """C: treeray_morton_order_noalloc. Morton ordering of the leaves for callers that
+    cannot allocate device memory: keys (uint64 viewed as torch.int64) and perm (int32)
+    are caller-owned CUDA tensors of the leaf count; the library allocates nothing."""
+    import numpy as np
+    import torch
+    g = Grid()
+    g.n = int(n)
+    g.box = float(box)
+    b = None
+    if blocks is not None:
+        b = np.ascontiguousarray(blocks, dtype=np.int32).reshape(-1)
+        g.n_blocks = b.size // 4
+        g.blocks = b.ctypes.data_as(C.POINTER(C.c_int32))
+    _raise(lib().treeray_morton_order_noalloc(C.byref(g), _dev(keys, torch.int64, "keys"),
+                                              _dev(perm, torch.int32, "perm"), _stream(stream)))
 
 
 class Context:

@@ -23,6 +23,7 @@ SOURCES = {
     "build.cu": ["-fmad=false"],
     "evaluate.cu": [],
     "post.cu": [],
+    "noalloc.cu": [],
     "tables.cpp": [],
 }
 
