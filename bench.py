@@ -318,11 +318,16 @@ def cpu_baseline(w, seconds: float):
     t0 = time.perf_counter()
     tree = oracle.Tree(w)
     t_build = time.perf_counter() - t0
-    cal = synth.sample_targets(w.n_leaves, 1024, seed=21)
-    t0 = time.perf_counter()
-    tree.evaluate(cal)
-    t_cal = time.perf_counter() - t0
-    m = int(min(w.n_leaves, max(1024, 1024 * seconds / max(t_cal, 1e-3))))
+    m = 4096
+    while True:  # grow the calibration sample until it takes a measurable time
+        cal = synth.sample_targets(w.n_leaves, m, seed=21)
+        t0 = time.perf_counter()
+        tree.evaluate(cal)
+        t_cal = time.perf_counter() - t0
+        if t_cal > 0.5 or m >= w.n_leaves:
+            break
+        m = min(w.n_leaves, m * 4)
+    m = int(min(w.n_leaves, max(1024, m * seconds / max(t_cal, 1e-3))))
     tg = synth.sample_targets(w.n_leaves, m, seed=22)
     t0 = time.perf_counter()
     J, F = tree.evaluate(tg)
@@ -336,6 +341,33 @@ def cpu_baseline(w, seconds: float):
             "sample": f"{m} random cells of {w.n_leaves} (evaluate+radpressure+dust T, "
                       f"{t_s:.1f} s) plus the full tree build ({t_build:.1f} s), scaled to all cells",
             "threads": cores}
+
+
+def run_profile(args):
+    """Profiling driver for ncu: build the full tree once, then launch the evaluate
+    kernel on a seeded subset of targets: two warm-up launches, then one more."""
+    import numpy as np
+    import torch
+
+    import paper_2204_09072_gb300 as tr
+    import synth
+    w = workload(args.npix)
+    ctx = tr.Context(w.params)
+    dev = torch.device("cuda:0")
+    rho = torch.as_tensor(w.rho, device=dev)
+    td = torch.as_tensor(w.td, device=dev)
+    ctx.build(w.box_cm, rho, td, n=w.uniform_n, star_pos=w.star_pos, star_lum=w.star_lum)
+    m = min(args.profile_targets, w.n_leaves)
+    tg = torch.as_tensor(np.sort(synth.sample_targets(w.n_leaves, m, seed=5)).astype(np.int32),
+                         device=dev)
+    J = torch.empty(m, dtype=torch.float32, device=dev)
+    F = torch.empty(3 * m, dtype=torch.float64, device=dev)
+    for _ in range(3):
+        ctx.evaluate(J, F, targets=tg)
+    ctx.check()
+    print(json.dumps({"profile": "evaluate", "workload": f"turb128_npix{args.npix}", "targets": m,
+                      "J_mean": float(J.double().mean())}))
+    ctx.close()
 
 
 def run_reference(args):
@@ -382,10 +414,15 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-sample", type=int, default=16384)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-evaluate", action="store_true",
+                    help="ncu driver: evaluate kernel only, on --profile-targets cells")
+    ap.add_argument("--profile-targets", type=int, default=262144)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
-    if args.impl == "reference":
+    if args.profile_evaluate:
+        run_profile(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
