@@ -18,7 +18,7 @@ static thread_local std::string g_err;
 void set_error(const std::string& msg) { g_err = msg; }
 
 void free_tables(DeviceTables& t) {
-    void* ptrs[] = {t.nhat, t.alpha_off, t.alpha_ent, t.bin_thr, t.R2,   t.Rh,
+    void* ptrs[] = {t.nhat, t.alpha_off, t.alpha_ent, t.bin_thr, t.R2,   t.Rh, t.lvlp,
                     t.open_max, t.str_lo, t.str_hi, t.scal, t.err, t.queue};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -61,6 +61,7 @@ treeray_status upload_tables(treeray_ctx* c, cudaStream_t s) {
     }
     std::vector<int64_t> thr((size_t)(L + 1) * nb), omax(L + 1);
     std::vector<float> R2((size_t)(L + 1) * nb), Rh((size_t)(L + 1) * nb);
+    std::vector<float2> lvlp(L + 1);
     std::vector<int64_t> slo((size_t)(L + 1) * (L + 1) * nb), shi(slo.size());
     std::vector<double> R(nb + 1);
     const double th2 = c->p.theta * c->p.theta;
@@ -81,6 +82,8 @@ treeray_status upload_tables(treeray_ctx* c, cudaStream_t s) {
     }
     for (int lt = 0; lt <= L; ++lt) {
         radii(nb, L, (int64_t)2 << (L - lt), R.data());
+        lvlp[lt] = make_float2((float)(1.0 / (R[0] * R[0])),
+                               (float)(0.5 * nb / std::log2(R[nb] / R[0])));
         for (int i = 0; i < nb; ++i) {
             thr[(size_t)lt * nb + i] = (int64_t)std::ceil(R[i] * R[i]);
             R2[(size_t)lt * nb + i] = (float)(R[i] * R[i]);
@@ -103,6 +106,7 @@ treeray_status upload_tables(treeray_ctx* c, cudaStream_t s) {
     if ((rc = upload(&c->dt.R2, R2, s)) != TREERAY_OK) return rc;
     if ((rc = upload(&c->dt.Rh, Rh, s)) != TREERAY_OK) return rc;
     if ((rc = upload(&c->dt.open_max, omax, s)) != TREERAY_OK) return rc;
+    if ((rc = upload(&c->dt.lvlp, lvlp, s)) != TREERAY_OK) return rc;
     if ((rc = upload(&c->dt.str_lo, slo, s)) != TREERAY_OK) return rc;
     if ((rc = upload(&c->dt.str_hi, shi, s)) != TREERAY_OK) return rc;
     TR_CUDA(cudaStreamSynchronize(s));  // host vectors die on return

@@ -80,37 +80,58 @@ __global__ void k_rs_hist(const uint64_t* keys, int64_t n, int shift, uint32_t* 
     for (int d = threadIdx.x; d < 256; d += blockDim.x) hist[(int64_t)d * nb + blockIdx.x] = h[d];
 }
 
-// exclusive scan of m counters in place, one block of 1024 threads
-__global__ void k_rs_scan(uint32_t* a, int64_t m) {
-    __shared__ uint32_t part[1024];
+// Block-wide exclusive scan of one value per thread (256 threads); returns the total.
+__device__ inline uint32_t block_scan_256(uint32_t v, uint32_t* sh, uint32_t* out_excl) {
     const int t = threadIdx.x;
-    const int64_t chunk = (m + 1023) / 1024;
-    const int64_t lo = t * chunk, hi = min(m, lo + chunk);
-    uint32_t s = 0;
-    for (int64_t i = lo; i < hi; ++i) s += a[i];
-    part[t] = s;
+    sh[t] = v;
     __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        uint32_t v = t >= off ? part[t - off] : 0u;
+    for (int off = 1; off < 256; off <<= 1) {
+        const uint32_t x = t >= off ? sh[t - off] : 0u;
         __syncthreads();
-        part[t] += v;
+        sh[t] += x;
         __syncthreads();
     }
-    uint32_t run = part[t] - s;
-    for (int64_t i = lo; i < hi; ++i) {
-        const uint32_t v = a[i];
-        a[i] = run;
-        run += v;
+    *out_excl = sh[t] - v;
+    const uint32_t total = sh[255];
+    __syncthreads();
+    return total;
+}
+
+// Row d of the histogram ([256 digits][nb blocks]): exclusive scan in place, row total
+// to rowsum[d]. One block of 256 threads per digit.
+__global__ void __launch_bounds__(256) k_rs_scan_rows(uint32_t* hist, int nb, uint32_t* rowsum) {
+    __shared__ uint32_t sh[256];
+    uint32_t* row = hist + (int64_t)blockIdx.x * nb;
+    const int per = (nb + 255) / 256;
+    const int lo = threadIdx.x * per, hi = min(nb, lo + per);
+    uint32_t s = 0;
+    for (int i = lo; i < hi; ++i) s += row[i];
+    uint32_t ex;
+    const uint32_t total = block_scan_256(s, sh, &ex);
+    for (int i = lo; i < hi; ++i) {
+        const uint32_t v = row[i];
+        row[i] = ex;
+        ex += v;
     }
+    if (threadIdx.x == 0) rowsum[blockIdx.x] = total;
+}
+
+// exclusive scan of the 256 digit totals in place (one block of 256 threads)
+__global__ void __launch_bounds__(256) k_rs_scan_digits(uint32_t* rowsum) {
+    __shared__ uint32_t sh[256];
+    uint32_t ex;
+    block_scan_256(rowsum[threadIdx.x], sh, &ex);
+    rowsum[threadIdx.x] = ex;
 }
 
 __global__ void __launch_bounds__(kSortThreads) k_rs_scatter(const uint64_t* kin, const int32_t* vin,
                                                              uint64_t* kout, int32_t* vout, int64_t n,
-                                                             int shift, const uint32_t* hist, int nb) {
+                                                             int shift, const uint32_t* hist, int nb,
+                                                             const uint32_t* digit_base) {
     __shared__ uint32_t base[256];
     __shared__ uint32_t wc[kSortThreads / 32][257];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    for (int d = t; d < 256; d += blockDim.x) base[d] = hist[(int64_t)d * nb + blockIdx.x];
+    for (int d = t; d < 256; d += blockDim.x) base[d] = digit_base[d] + hist[(int64_t)d * nb + blockIdx.x];
     const unsigned lt_mask = (1u << lane) - 1u;
     for (int c = 0; c < kSortTile / kSortThreads; ++c) {
         for (int i = t; i < (kSortThreads / 32) * 257; i += blockDim.x) (&wc[0][0])[i] = 0;
@@ -593,8 +614,9 @@ treeray_status build_tree(treeray_ctx* c, const treeray_grid* gr, const float* r
     const int nbk = nblk(N, kSortTile);
     const int64_t nh = 256 * (int64_t)nbk;
     int64_t ch = T.cap_hist;
-    if ((rc = grow(&T.hist, &ch, nh)) != TREERAY_OK) return rc;
-    T.cap_hist = std::max(T.cap_hist, nh);
+    if ((rc = grow(&T.hist, &ch, nh + 256)) != TREERAY_OK) return rc;
+    T.cap_hist = std::max(T.cap_hist, nh + 256);
+    uint32_t* digit_base = T.hist + nh;
     const int bits = 3 * lmax + 5;
     uint64_t* ka = T.keys;
     int32_t* va = T.perm;
@@ -604,9 +626,11 @@ treeray_status build_tree(treeray_ctx* c, const treeray_grid* gr, const float* r
     for (int shift = 0; shift < bits; shift += 8, ++passes) {
         k_rs_hist<<<nbk, kSortThreads, 0, st>>>(ka, N, shift, T.hist, nbk);
         ++c->launches;
-        k_rs_scan<<<1, 1024, 0, st>>>(T.hist, nh);
+        k_rs_scan_rows<<<256, 256, 0, st>>>(T.hist, nbk, digit_base);
         ++c->launches;
-        k_rs_scatter<<<nbk, kSortThreads, 0, st>>>(ka, va, kb, vb, N, shift, T.hist, nbk);
+        k_rs_scan_digits<<<1, 256, 0, st>>>(digit_base);
+        ++c->launches;
+        k_rs_scatter<<<nbk, kSortThreads, 0, st>>>(ka, va, kb, vb, N, shift, T.hist, nbk, digit_base);
         ++c->launches;
         std::swap(ka, kb);
         std::swap(va, vb);
@@ -650,6 +674,10 @@ treeray_status build_tree(treeray_ctx* c, const treeray_grid* gr, const float* r
         c->level_off[l] = (int)nn;
         c->level_cnt[l] = (int)nent[l];
         nn += nent[l];
+    }
+    if (nn >= ((int64_t)1 << 27)) {
+        set_error("grid: more than 2^27 tree nodes");
+        return TREERAY_EINVAL;
     }
     c->nnodes = nn;
     int64_t cn = T.cap_nodes;

@@ -40,6 +40,7 @@ struct EvalArgs {
     const int64_t* __restrict__ open_max;
     const int64_t* __restrict__ str_lo;
     const int64_t* __restrict__ str_hi;
+    const float2* __restrict__ lvlp;    // per target level: 1 / R_0^2, 0.5 / log2(g)
     const double* __restrict__ scal;
     unsigned* err;
     unsigned long long* queue;
@@ -62,46 +63,35 @@ __device__ __forceinline__ int alpha_key(int o, int elog) {
     return 2 * ((4 * o) >> elog) + 1;
 }
 
-__device__ __forceinline__ int bin_of(const int64_t* thr, int nbins, int64_t d2) {
-    int i = 0;
-    for (int step = 32; step > 0; step >>= 1)
-        if (i + step < nbins && d2 >= __ldg(thr + i + step)) i += step;
-    return i;
+// Largest j in [1, nb-1] with d2 >= arr[j] (arr non-decreasing), else 0, starting from a
+// guess: the fix-up loops make the result exact whatever the guess.
+__device__ __forceinline__ int fixup(int g, int64_t d2, const int64_t* __restrict__ arr, int nb) {
+    g = max(0, min(g, nb - 1));
+    while (g + 1 < nb && d2 >= __ldg(arr + g + 1)) ++g;
+    while (g > 0 && d2 < __ldg(arr + g)) --g;
+    return g;
 }
 
-template <int NPIX, bool THICK, bool LIST>
-__global__ void __launch_bounds__(256) k_evaluate(EvalArgs a) {
+// Guess of the segment holding squared distance x2 for a target level with R_0^2 = 1/inv_r02
+// and geometric ratio g: 0.5 log2(x2 / R_0^2) / log2(g).
+__device__ __forceinline__ int guess_bin(float x2, float2 lp) {
+    return x2 > 0.0f ? (int)(__log2f(x2 * lp.x) * lp.y) : 0;
+}
+
+// Accepted-list / walk-statistics mode: the walk alone, one warp per target.
+__global__ void __launch_bounds__(256) k_walk_list(EvalArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int nb = a.nbins;
-    const int cells = nb * NPIX;
-    const int nq = LIST ? 0 : (THICK ? 6 : 2);
-    // per-warp layout: [nq][nb][NPIX] floats, THICK: NPIX uint64 flags, then the stack
-    size_t per_warp = (size_t)nq * cells * 4 + (THICK && !LIST ? NPIX * 8 : 0) + (size_t)a.stack_cap * 4;
-    per_warp = (per_warp + 15) & ~size_t(15);
-    unsigned char* base = smem + per_warp * warp;
-    float* tL = reinterpret_cast<float*>(base);
-    float* tA = tL + cells;
-    float* tLk = tA + cells;
-    float* tAk = tLk + cells;
-    float* tVk = tAk + cells;
-    float* tQk = tVk + cells;
-    unsigned long long* flags = reinterpret_cast<unsigned long long*>(base + (size_t)nq * cells * 4);
-    int* stack = reinterpret_cast<int*>(base + (size_t)nq * cells * 4 + (THICK && !LIST ? NPIX * 8 : 0));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int* stack = reinterpret_cast<int*>(smem) + (size_t)warp * a.stack_cap;
     const unsigned full = 0xffffffffu;
     const unsigned lt_mask = (1u << lane) - 1u;
-    const float omega = (float)(4.0 * kPi / NPIX);
-    const float inv_s3 = 1.0f / 512.0f;
     const int W = 2 * a.D + 1;
-    (void)nw;
-
     for (;;) {
         long long q = 0;
         if (lane == 0) q = (long long)atomicAdd(a.queue, 1ull);
         q = __shfl_sync(full, q, 0);
         if (q >= a.n) break;
         int64_t s;
-        int64_t out;
         if (a.targets) {
             const int32_t k = a.targets[q];
             if (k < 0 || k >= a.nleaves) {
@@ -109,23 +99,11 @@ __global__ void __launch_bounds__(256) k_evaluate(EvalArgs a) {
                 continue;
             }
             s = a.inv_perm[k];
-            out = q;
         } else {
             s = q;
-            out = a.perm[s];
         }
-        const int tnode = a.leaf_node[s];
-        const int4 tg = a.geo[tnode];
+        const int4 tg = a.geo[a.leaf_node[s]];
         const int tx = tg.x, ty = tg.y, tz = tg.z & 0xffffff;
-        const int tl = tg.z >> 24;
-        const int64_t* thr = a.bin_thr + (int64_t)tl * nb;
-        const float* R2 = a.R2 + (int64_t)tl * nb;
-
-        if (!LIST) {
-            for (int i = lane; i < nq * cells; i += 32) tL[i] = 0.0f;
-            if (THICK)
-                for (int h = lane; h < NPIX; h += 32) flags[h] = 0ull;
-        }
         int nacc = 0;
         long long nvis = 0, nent = 0;
         int sp = 0;
@@ -171,25 +149,158 @@ __global__ void __launch_bounds__(256) k_evaluate(EvalArgs a) {
                 overflow = true;
                 break;
             }
-            if (LIST) {
-                const unsigned am = __ballot_sync(full, acc);
-                if (acc && a.acc_ids) {
-                    const int pos = nacc + __popc(am & lt_mask);
-                    if (pos < a.acc_cap) a.acc_ids[q * (int64_t)a.acc_cap + pos] = node;
+            const unsigned am = __ballot_sync(full, acc);
+            if (acc && a.acc_ids) {
+                const int pos = nacc + __popc(am & lt_mask);
+                if (pos < a.acc_cap) a.acc_ids[q * (int64_t)a.acc_cap + pos] = node;
+            }
+            nacc += __popc(am);
+            nvis += __popc(__ballot_sync(full, valid));
+            if (a.stats && acc && d2 != 0) {
+                const int elog = a.lmax - lvl + 1;
+                const int Kx = alpha_key(ox, elog), Ky = alpha_key(oy, elog), Kz = alpha_key(oz, elog);
+                if (abs(Kx) <= a.D && abs(Ky) <= a.D && abs(Kz) <= a.D) {
+                    const int idx = ((Kz + a.D) * W + (Ky + a.D)) * W + (Kx + a.D);
+                    nent += __ldg(a.aoff + idx + 1) - __ldg(a.aoff + idx);
                 }
-                nacc += __popc(am);
-                nvis += __popc(__ballot_sync(full, valid));
-                if (a.stats && acc && d2 != 0) {
-                    const int elog = a.lmax - lvl + 1;
-                    const int Kx = alpha_key(ox, elog), Ky = alpha_key(oy, elog), Kz = alpha_key(oz, elog);
-                    if (abs(Kx) <= a.D && abs(Ky) <= a.D && abs(Kz) <= a.D) {
-                        const int idx = ((Kz + a.D) * W + (Ky + a.D)) * W + (Kx + a.D);
-                        nent += __ldg(a.aoff + idx + 1) - __ldg(a.aoff + idx);
-                    }
+            }
+        }
+        overflow = __any_sync(full, overflow);
+        if (overflow) {
+            if (lane == 0) atomicOr(a.err, kErrStack);
+            continue;
+        }
+        if (a.acc_counts && lane == 0) a.acc_counts[q] = nacc;
+        if (a.stats) {
+            for (int off = 16; off > 0; off >>= 1) nent += __shfl_xor_sync(full, nent, off);
+            if (lane == 0) {
+                atomicAdd(a.stats + 0, (unsigned long long)(nvis + 1));
+                atomicAdd(a.stats + 1, (unsigned long long)nacc + (root.w >= 0 ? 0ull : 1ull));
+                atomicAdd(a.stats + 2, (unsigned long long)nent);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// Evaluation kernel: a team of WPT warps per target shares one block-wide walk stack and
+// one (segment x ray) tile in shared memory; the block processes one target at a time
+// and takes the next from a global work counter (persistent grid).
+//   walk:    each step the team pops up to 4 WPT child groups (32 WPT nodes), tests them,
+//            appends the opened nodes' child groups to the shared stack (one shared-memory
+//            atomic per warp) and deposits the accepted ones (one node per thread, its
+//            angular-kernel entries in a loop, shared-memory atomics into the tile);
+//   rays:    one thread per ray integrates the segments inside out in FP32 (optical-depth
+//            prefix in FP64 once it passes 40), then the team reduces J and F in FP64.
+template <int NPIX, bool THICK, int WPT>
+__global__ void __launch_bounds__(WPT * 32) k_evaluate(EvalArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int NT = WPT * 32;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nb = a.nbins;
+    const int cells = nb * NPIX;
+    constexpr int nq = THICK ? 6 : 2;
+    // layout: tile [nq][nb][NPIX] f32 | THICK: flags [NPIX] u64 | stack [cap] i32
+    float* tL = reinterpret_cast<float*>(smem);
+    float* tA = tL + cells;
+    float* tLk = tA + cells;
+    float* tAk = tLk + cells;
+    float* tVk = tAk + cells;
+    float* tQk = tVk + cells;
+    unsigned long long* flags = reinterpret_cast<unsigned long long*>(smem + (size_t)nq * cells * 4);
+    int* stack = reinterpret_cast<int*>(smem + (size_t)nq * cells * 4 + (THICK ? NPIX * 8 : 0));
+    __shared__ int s_sp, s_overflow;
+    __shared__ long long s_q;
+    __shared__ double s_red[4][WPT];
+    const unsigned full = 0xffffffffu;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const float omega = (float)(4.0 * kPi / NPIX);
+    const float inv_s3 = 1.0f / 512.0f;
+    const int W = 2 * a.D + 1;
+    const int4 root = a.geo[0];
+
+    for (;;) {
+        if (tid == 0) s_q = (long long)atomicAdd(a.queue, 1ull);
+        __syncthreads();
+        const long long q = s_q;
+        if (q >= a.n) break;
+        int64_t s;
+        int64_t out;
+        if (a.targets) {
+            const int32_t k = a.targets[q];
+            if (k < 0 || k >= a.nleaves) {
+                if (tid == 0) atomicOr(a.err, kErrTarget);
+                __syncthreads();
+                continue;
+            }
+            s = a.inv_perm[k];
+            out = q;
+        } else {
+            s = q;
+            out = a.perm[s];
+        }
+        const int tnode = a.leaf_node[s];
+        const int4 tg = a.geo[tnode];
+        const int tx = tg.x, ty = tg.y, tz = tg.z & 0xffffff;
+        const int tl = tg.z >> 24;
+        const int64_t* thr = a.bin_thr + (int64_t)tl * nb;
+        const float* R2 = a.R2 + (int64_t)tl * nb;
+        const float2 lp = __ldg(a.lvlp + tl);
+
+        for (int i = tid; i < nq * cells; i += NT) tL[i] = 0.0f;
+        if (THICK)
+            for (int h = tid; h < NPIX; h += NT) flags[h] = 0ull;
+        if (tid == 0) {
+            s_overflow = 0;
+            s_sp = 0;
+            if (root.w >= 0) {
+                stack[0] = root.w;
+                s_sp = 1;
+            }
+        }
+        __syncthreads();
+        for (;;) {
+            const int sp = s_sp;
+            if (sp == 0 || s_overflow) break;
+            const int ng = sp < 4 * WPT ? sp : 4 * WPT;
+            const int g = tid >> 3;
+            const bool valid = g < ng;
+            const int node = valid ? stack[sp - ng + g] + (tid & 7) : 0;
+            __syncthreads();  // every pop is read before the stack is reused
+            if (tid == 0) s_sp = sp - ng;
+            __syncthreads();
+            bool open = false, acc = false;
+            int4 gg = make_int4(0, 0, 0, 0);
+            int ox = 0, oy = 0, oz = 0, lvl = 0;
+            int64_t d2 = 0;
+            if (valid) {
+                gg = __ldg(a.geo + node);
+                lvl = gg.z >> 24;
+                ox = gg.x - tx;
+                oy = gg.y - ty;
+                oz = (gg.z & 0xffffff) - tz;
+                d2 = (int64_t)ox * ox + (int64_t)oy * oy + (int64_t)oz * oz;
+                if (gg.w >= 0) {
+                    const int E = 2 << (a.lmax - lvl);
+                    const bool inside = 2 * abs(ox) < E && 2 * abs(oy) < E && 2 * abs(oz) < E;
+                    open = inside || d2 <= __ldg(a.open_max + lvl);
                 }
-            } else if (acc && d2 != 0) {
+                acc = !open && d2 != 0;  // the own cell is deposited after the walk
+            }
+            const unsigned om = __ballot_sync(full, open);
+            if (om) {
+                int pos0 = 0;
+                if (lane == 0) pos0 = atomicAdd(&s_sp, __popc(om));
+                pos0 = __shfl_sync(full, pos0, 0);
+                if (open) {
+                    const int pos = pos0 + __popc(om & lt_mask);
+                    if (pos < a.stack_cap) stack[pos] = gg.w;
+                    else s_overflow = 1;
+                }
+            }
+            if (acc) {
                 // ---- map the accepted node onto the rays
-                const int i = bin_of(thr, nb, d2);
+                const int i = fixup(guess_bin((float)d2, lp), d2, thr, nb);
                 const float4 v0 = __ldg(a.thin + node);
                 const float4 v1 = __ldg(a.thick + node);
                 const float rx = (float)ox + v0.z, ry = (float)oy + v0.w, rz = (float)oz + v1.x;
@@ -202,57 +313,47 @@ __global__ void __launch_bounds__(256) k_evaluate(EvalArgs a) {
                     const int idx = ((Kz + a.D) * W + (Ky + a.D)) * W + (Kx + a.D);
                     const int e0 = __ldg(a.aoff + idx), e1 = __ldg(a.aoff + idx + 1);
                     if (e1 == e0) atomicOr(a.err, kErrAlphaKey);
-                    const float bL = beta * v0.x, bA = beta * v0.y;
-                    bool thick_here = THICK && v1.w > 0.0f;
+                    const float bL = beta * v0.x * inv_s3, bA = beta * v0.y * inv_s3;
+                    const bool thick_here = THICK && v1.w > 0.0f;
                     unsigned long long fmask = 0ull;
                     if (THICK && thick_here) {
                         const int64_t* lo = a.str_lo + ((int64_t)tl * (a.lmax + 1) + lvl) * nb;
                         const int64_t* hi = a.str_hi + ((int64_t)tl * (a.lmax + 1) + lvl) * nb;
-                        int ilo = 0, ihi = 0;
-                        for (int j = 1; j < nb; ++j) {
-                            ilo += d2 >= __ldg(lo + j);
-                            ihi += d2 >= __ldg(hi + j);
-                        }
+                        const float d = sqrtf((float)d2);
+                        const float sd = 0.8660254f * (float)(2 << (a.lmax - lvl));
+                        const float dl = fmaxf(d - sd, 0.0f), dh = d + sd;
+                        const int ilo = fixup(guess_bin(dl * dl, lp), d2, lo, nb);
+                        const int ihi = fixup(guess_bin(dh * dh, lp), d2, hi, nb);
                         for (int j = ilo; j < ihi; ++j) fmask |= 1ull << j;
                     }
+                    float* cL = tL + i * NPIX;
+                    float* cA = tA + i * NPIX;
                     for (int e = e0; e < e1; ++e) {
                         const uint32_t ent = __ldg(a.aent + e);
                         const int h = (int)(ent & 0xffffu);
-                        const float w = (float)(ent >> 16) * inv_s3;
-                        const int cidx = i * NPIX + h;
-                        atomicAdd(tL + cidx, w * bL);
-                        atomicAdd(tA + cidx, w * bA);
+                        const float w = (float)(ent >> 16);
+                        atomicAdd(cL + h, w * bL);
+                        atomicAdd(cA + h, w * bA);
                         if (THICK && thick_here) {
-                            atomicAdd(tLk + cidx, w * v1.y);
+                            const int cidx = i * NPIX + h;
+                            const float wn = w * inv_s3;
+                            atomicAdd(tLk + cidx, wn * v1.y);
                             atomicAdd(tAk + cidx, v1.z);
-                            atomicAdd(tVk + cidx, w * v1.w);
-                            atomicAdd(tQk + cidx, w * beta * v1.w);
+                            atomicAdd(tVk + cidx, wn * v1.w);
+                            atomicAdd(tQk + cidx, wn * beta * v1.w);
                             if (fmask) atomicOr(flags + h, fmask);
                         }
                     }
                 }
             }
+            __syncthreads();
         }
-        overflow = __any_sync(full, overflow);
-        if (overflow) {
-            if (lane == 0) atomicOr(a.err, kErrStack);
+        if (s_overflow) {
+            if (tid == 0) atomicOr(a.err, kErrStack);
+            __syncthreads();
             continue;
         }
-        if (LIST) {
-            if (a.acc_counts && lane == 0) a.acc_counts[q] = nacc;
-            if (a.stats) {
-                for (int off = 16; off > 0; off >>= 1) nent += __shfl_xor_sync(full, nent, off);
-                if (lane == 0) {
-                    atomicAdd(a.stats + 0, (unsigned long long)(nvis + 1));
-                    atomicAdd(a.stats + 1, (unsigned long long)nacc + (root.w >= 0 ? 0ull : 1ull));
-                    atomicAdd(a.stats + 2, (unsigned long long)nent);
-                }
-            }
-            __syncwarp();
-            continue;
-        }
-        __syncwarp();
-        // ---- own cell: bin 0 of every ray, alpha = 1/N_pix, beta = 1
+        // ---- own cell: segment 0 of every ray, alpha = 1/N_pix, beta = 1
         {
             const float4 v0 = __ldg(a.thin + tnode);
             const float4 v1 = __ldg(a.thick + tnode);
@@ -264,7 +365,7 @@ __global__ void __launch_bounds__(256) k_evaluate(EvalArgs a) {
                 for (int j = 0; j < ihi; ++j) fmask |= 1ull << j;
             }
             const float w = 1.0f / NPIX;
-            for (int h = lane; h < NPIX; h += 32) {
+            for (int h = tid; h < NPIX; h += NT) {
                 tL[h] += w * v0.x;
                 tA[h] += w * v0.y;
                 if (THICK && v1.w > 0.0f) {
@@ -276,10 +377,10 @@ __global__ void __launch_bounds__(256) k_evaluate(EvalArgs a) {
                 }
             }
         }
-        __syncwarp();
-        // ---- integrate each ray from the inside out (lane = ray)
+        __syncthreads();
+        // ---- integrate each ray from the inside out (one thread per ray)
         double Js = 0.0, Fx = 0.0, Fy = 0.0, Fz = 0.0;
-        for (int h = lane; h < NPIX; h += 32) {
+        for (int h = tid; h < NPIX; h += NT) {
             if (THICK) {
                 const unsigned long long fl = flags[h];
                 if (fl)
@@ -296,18 +397,22 @@ __global__ void __launch_bounds__(256) k_evaluate(EvalArgs a) {
                         tL[c1] = tA[c1] = tQk[c1] = tLk[c1] = tAk[c1] = tVk[c1] = 0.0f;
                     }
             }
-            double tcum = 0.0, ek = 1.0, Fh = 0.0;
+            float tcum = 0.0f, ek = 1.0f, Fh = 0.0f;
+            double tcum_d = 0.0;
+            bool deep = false;
             for (int i = 0; i < nb; ++i) {
                 const int ci = i * NPIX + h;
-                const float R2i = __ldg(R2 + i);
                 const float Lth = tL[ci], Ath = tA[ci];
-                const float tth = i == 0 ? 0.0f : Ath / (omega * R2i);
+                const float Vk = THICK ? tVk[ci] : 0.0f;
+                if (Lth == 0.0f && Ath == 0.0f && Vk == 0.0f) continue;  // empty segment
+                const float R2i = __ldg(R2 + i);
+                const float inv_R2 = 1.0f / R2i;
+                const float tth = i == 0 ? 0.0f : Ath * inv_R2 * (1.0f / omega);
                 float f = 0.0f, Fk = 0.0f, Akv = 0.0f, tk = 0.0f;
-                if (THICK) {
-                    const float Vk = tVk[ci];
+                if constexpr (THICK) {
                     if (Vk > 0.0f) {
                         const float cb = cbrtf(Vk);
-                        float wk = (tQk[ci] / Vk) * (cb * cb) / R2i;
+                        float wk = (tQk[ci] / Vk) * (cb * cb) * inv_R2;
                         wk = fminf(wk, omega);
                         f = wk / omega;
                         Akv = tAk[ci];
@@ -316,54 +421,72 @@ __global__ void __launch_bounds__(256) k_evaluate(EvalArgs a) {
                     }
                 }
                 const float g = tth < 1e-4f ? 1.0f : -expm1f(-tth) / tth;
-                const float Fth = g * Lth / (4.0f * (float)kPi * R2i);
+                const float Fth = g * Lth * inv_R2 * (float)(1.0 / (4.0 * kPi));
                 const float den = Ath + f * Akv;
                 const float Fs = den > 0.0f ? (Fth * Ath + Fk * f * Akv) / den : Fth + Fk;
-                const float eps = expf(-(float)tcum) * (float)ek;
-                Fh += (double)(eps * Fs);
-                tcum += (double)tth;
-                if (THICK && f > 0.0f) ek *= (double)((1.0f - f) + f * expf(-tk));
+                const float eps = expf(deep ? -(float)tcum_d : -tcum) * ek;
+                Fh += eps * Fs;
+                // optical-depth prefix: FP32, promoted to FP64 once the ray passes tau = 40
+                if (!deep) {
+                    tcum += tth;
+                    if (tcum > 40.0f) {
+                        deep = true;
+                        tcum_d = (double)tcum;
+                    }
+                } else {
+                    tcum_d += (double)tth;
+                }
+                if (THICK && f > 0.0f) ek *= (1.0f - f) + f * expf(-tk);
             }
-            Js += Fh;
-            Fx -= Fh * (double)__ldg(a.nhat + 3 * h);
-            Fy -= Fh * (double)__ldg(a.nhat + 3 * h + 1);
-            Fz -= Fh * (double)__ldg(a.nhat + 3 * h + 2);
+            Js += (double)Fh;
+            Fx -= (double)Fh * (double)__ldg(a.nhat + 3 * h);
+            Fy -= (double)Fh * (double)__ldg(a.nhat + 3 * h + 1);
+            Fz -= (double)Fh * (double)__ldg(a.nhat + 3 * h + 2);
         }
-        for (int off = 16; off > 0; off >>= 1) {
-            Js += __shfl_xor_sync(full, Js, off);
-            Fx += __shfl_xor_sync(full, Fx, off);
-            Fy += __shfl_xor_sync(full, Fy, off);
-            Fz += __shfl_xor_sync(full, Fz, off);
+        // ---- team reduction in FP64 (only warps that hold rays contribute)
+        if (warp * 32 < NPIX) {
+            for (int off = 16; off > 0; off >>= 1) {
+                Js += __shfl_xor_sync(full, Js, off);
+                Fx += __shfl_xor_sync(full, Fx, off);
+                Fy += __shfl_xor_sync(full, Fy, off);
+                Fz += __shfl_xor_sync(full, Fz, off);
+            }
+            if (lane == 0) {
+                s_red[0][warp] = Js;
+                s_red[1][warp] = Fx;
+                s_red[2][warp] = Fy;
+                s_red[3][warp] = Fz;
+            }
         }
-        if (lane == 0) {
+        __syncthreads();
+        if (tid == 0) {
+            double r[4] = {0.0, 0.0, 0.0, 0.0};
+            for (int w = 0; w < WPT && w * 32 < NPIX; ++w)
+                for (int c = 0; c < 4; ++c) r[c] += s_red[c][w];
             const double Fu = a.scal[0] / (a.u * a.u);  // internal flux unit in erg/s/cm^2
             const int64_t k = a.perm[s];
-            a.J[out] = (float)(Js / (4.0 * kPi) * Fu + a.jsrc[k]);
-            a.F[3 * out] = Fx * Fu;
-            a.F[3 * out + 1] = Fy * Fu;
-            a.F[3 * out + 2] = Fz * Fu;
+            a.J[out] = (float)(r[0] / (4.0 * kPi) * Fu + a.jsrc[k]);
+            a.F[3 * out] = r[1] * Fu;
+            a.F[3 * out + 1] = r[2] * Fu;
+            a.F[3 * out + 2] = r[3] * Fu;
         }
-        __syncwarp();
+        __syncthreads();
     }
 }
 
-template <int NPIX, bool THICK, bool LIST>
-treeray_status launch_t(treeray_ctx* c, EvalArgs a, cudaStream_t s) {
-    const int nq = LIST ? 0 : (THICK ? 6 : 2);
-    size_t per_warp = (size_t)nq * a.nbins * NPIX * 4 + (THICK && !LIST ? NPIX * 8 : 0) + (size_t)a.stack_cap * 4;
-    per_warp = (per_warp + 15) & ~size_t(15);
+template <typename K>
+treeray_status launch_persistent(treeray_ctx* c, K kern, size_t per_warp, int max_warps, int64_t n,
+                                 unsigned long long* queue, cudaStream_t s, const EvalArgs& a) {
     int smem_optin = 0, sms = 0;
     TR_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
     TR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
-    // warps per block: up to 8 (thin) or 4 (thick) targets, limited by the per-block shared memory
-    int warps = THICK ? 4 : 8;
+    int warps = max_warps;
     while (warps > 1 && per_warp * warps > (size_t)smem_optin) --warps;
     if (per_warp * warps > (size_t)smem_optin) {
         set_error("evaluate: the per-target ray tile (npix x nbins) exceeds shared memory");
         return TREERAY_EINVAL;
     }
     const size_t smem = per_warp * warps;
-    auto kern = k_evaluate<NPIX, THICK, LIST>;
     TR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     TR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem));
@@ -372,26 +495,61 @@ treeray_status launch_t(treeray_ctx* c, EvalArgs a, cudaStream_t s) {
         return TREERAY_EINVAL;
     }
     int64_t blocks = (int64_t)per_sm * sms;
-    const int64_t need = (a.n + warps - 1) / warps;
+    const int64_t need = (n + warps - 1) / warps;
     if (blocks > need) blocks = need;
     if (blocks < 1) blocks = 1;
-    TR_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), s));
+    TR_CUDA(cudaMemsetAsync(queue, 0, sizeof(unsigned long long), s));
     kern<<<(int)blocks, warps * 32, smem, s>>>(a);
     c->launches += 1;
     TR_CUDA(cudaGetLastError());
     return TREERAY_OK;
 }
 
-template <bool LIST>
-treeray_status dispatch(treeray_ctx* c, EvalArgs a, cudaStream_t s) {
-    const bool thick = c->has_thick && !LIST;
+template <int NPIX, bool THICK>
+treeray_status launch_t(treeray_ctx* c, const EvalArgs& a, cudaStream_t s) {
+    constexpr int WPT = 4;  // warps per target team
+    constexpr int nq = THICK ? 6 : 2;
+    EvalArgs b = a;
+    // the team stack holds at most one batch of pushes (32 WPT groups) per level
+    b.stack_cap = 32 * WPT * (c->lmax + 1) + 64;
+    const size_t smem = (size_t)nq * a.nbins * NPIX * 4 + (THICK ? NPIX * 8 : 0) + (size_t)b.stack_cap * 4;
+    int smem_optin = 0, sms = 0;
+    TR_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+    TR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+    if (smem + 1024 > (size_t)smem_optin) {
+        set_error("evaluate: the per-target ray tile (npix x nbins) exceeds shared memory");
+        return TREERAY_EINVAL;
+    }
+    auto kern = k_evaluate<NPIX, THICK, WPT>;
+    TR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    TR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WPT * 32, smem));
+    if (per_sm < 1) {
+        set_error("evaluate: kernel does not fit on an SM");
+        return TREERAY_EINVAL;
+    }
+    int64_t blocks = (int64_t)per_sm * sms;
+    if (blocks > a.n) blocks = a.n;
+    TR_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), s));
+    kern<<<(int)blocks, WPT * 32, smem, s>>>(b);
+    c->launches += 1;
+    TR_CUDA(cudaGetLastError());
+    return TREERAY_OK;
+}
+
+treeray_status dispatch_eval(treeray_ctx* c, const EvalArgs& a, cudaStream_t s) {
+    const bool thick = c->has_thick;
     switch (c->p.npix) {
-        case 12: return thick ? launch_t<12, true, LIST>(c, a, s) : launch_t<12, false, LIST>(c, a, s);
-        case 48: return thick ? launch_t<48, true, LIST>(c, a, s) : launch_t<48, false, LIST>(c, a, s);
-        case 192: return thick ? launch_t<192, true, LIST>(c, a, s) : launch_t<192, false, LIST>(c, a, s);
+        case 12: return thick ? launch_t<12, true>(c, a, s) : launch_t<12, false>(c, a, s);
+        case 48: return thick ? launch_t<48, true>(c, a, s) : launch_t<48, false>(c, a, s);
+        case 192: return thick ? launch_t<192, true>(c, a, s) : launch_t<192, false>(c, a, s);
     }
     set_error("evaluate: npix must be 12, 48 or 192");
     return TREERAY_EINVAL;
+}
+
+treeray_status dispatch_list(treeray_ctx* c, const EvalArgs& a, cudaStream_t s) {
+    return launch_persistent(c, k_walk_list, (size_t)a.stack_cap * 4, 8, a.n, a.queue, s, a);
 }
 
 EvalArgs make_args(treeray_ctx* c, const int32_t* targets, int64_t n) {
@@ -412,6 +570,7 @@ EvalArgs make_args(treeray_ctx* c, const int32_t* targets, int64_t n) {
     a.open_max = c->dt.open_max;
     a.str_lo = c->dt.str_lo;
     a.str_hi = c->dt.str_hi;
+    a.lvlp = c->dt.lvlp;
     a.scal = c->dt.scal;
     a.err = c->dt.err;
     a.queue = c->dt.queue;
@@ -434,7 +593,7 @@ treeray_status launch_evaluate(treeray_ctx* c, const int32_t* targets, int64_t n
     EvalArgs a = make_args(c, targets, n);
     a.J = J;
     a.F = F;
-    return dispatch<false>(c, a, s);
+    return dispatch_eval(c, a, s);
 }
 
 treeray_status launch_accepted(treeray_ctx* c, const int32_t* targets, int64_t n, int32_t cap,
@@ -443,7 +602,7 @@ treeray_status launch_accepted(treeray_ctx* c, const int32_t* targets, int64_t n
     a.acc_counts = counts;
     a.acc_ids = ids;
     a.acc_cap = cap;
-    return dispatch<true>(c, a, s);
+    return dispatch_list(c, a, s);
 }
 
 treeray_status launch_walk_stats(treeray_ctx* c, const int32_t* targets, int64_t n, int64_t* totals,
@@ -451,7 +610,7 @@ treeray_status launch_walk_stats(treeray_ctx* c, const int32_t* targets, int64_t
     EvalArgs a = make_args(c, targets, n);
     a.stats = reinterpret_cast<unsigned long long*>(totals);
     a.acc_cap = 0;
-    return dispatch<true>(c, a, s);
+    return dispatch_list(c, a, s);
 }
 
 }  // namespace tr

@@ -62,34 +62,49 @@ __device__ inline double kappa_of(const DustArgs& d, int64_t k, double T) {
     return 1.0e-3 * (Tc * Tc);
 }
 
+// Per-cell constants of G(T) that do not depend on T_d, kept in the evaluation order
+// of the full expression so that G is rounded exactly as if written out:
+// gd = ((((3.8e-33 sqrt(Tg)) (Tg - T)) (1 - 0.8 e^(-75/Tg))) n_H^2) (xi / 0.01)
+struct Cell {
+    double c1;   // 3.8e-33 sqrt(Tg)
+    double c2;   // 1 - 0.8 exp(-75 / Tg)
+    double nH2;  // n_H^2
+    double Tg, rho, J, H;
+};
+
 // G(T) = Gamma_dust-gas + heat + rho kappa(T) (4 pi J - 4 sigma T^4)
-__device__ inline double balance(const DustArgs& d, int64_t k, double T, double rho, double Tg, double J,
-                                 double H) {
+__device__ inline double balance(const DustArgs& d, int64_t k, const Cell& c, double T) {
     const double kap = kappa_of(d, k, T);
-    const double nH = kHydrogenFraction * rho / kHydrogenMass;
-    const double gd = 3.8e-33 * sqrt(Tg) * (Tg - T) * (1.0 - 0.8 * exp(-75.0 / Tg)) * (nH * nH) * (d.xi / 0.01);
+    const double gd = c.c1 * (c.Tg - T) * c.c2 * c.nH2 * (d.xi / 0.01);
     const double T4 = (T * T) * (T * T);
-    return gd + H + rho * kap * (4.0 * kPi * J - 4.0 * kSigmaSB * T4);
+    return gd + c.H + c.rho * kap * (4.0 * kPi * c.J - 4.0 * kSigmaSB * T4);
 }
 
 // root by bracketing from the 2.7 K floor and 60 bisections in ln T
 __global__ void k_dust(DustArgs d) {
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= d.n) return;
-    const double rho = (double)d.rho[k], Tg = (double)d.tgas[k], J = (double)d.J[k];
-    const double H = d.heat ? (double)d.heat[k] : 0.0;
+    Cell c;
+    c.rho = (double)d.rho[k];
+    c.Tg = (double)d.tgas[k];
+    c.J = (double)d.J[k];
+    c.H = d.heat ? (double)d.heat[k] : 0.0;
+    c.c1 = 3.8e-33 * sqrt(c.Tg);
+    c.c2 = 1.0 - 0.8 * exp(-75.0 / c.Tg);
+    const double nH = kHydrogenFraction * c.rho / kHydrogenMass;
+    c.nH2 = nH * nH;
     double T;
-    if (balance(d, k, kDustFloorK, rho, Tg, J, H) <= 0.0) {
+    if (balance(d, k, c, kDustFloorK) <= 0.0) {
         T = kDustFloorK;
     } else {
-        const double TJ = sqrt(sqrt(kPi * (J > 0.0 ? J : 0.0) / kSigmaSB));
-        double hi = Tg > TJ ? Tg : TJ;
+        const double TJ = sqrt(sqrt(kPi * (c.J > 0.0 ? c.J : 0.0) / kSigmaSB));
+        double hi = c.Tg > TJ ? c.Tg : TJ;
         if (hi < kDustFloorK) hi = kDustFloorK;
-        for (int it = 0; it < 64 && balance(d, k, hi, rho, Tg, J, H) > 0.0; ++it) hi *= 2.0;
+        for (int it = 0; it < 64 && balance(d, k, c, hi) > 0.0; ++it) hi *= 2.0;
         double lo = kDustFloorK;
         for (int it = 0; it < 60; ++it) {
             const double mid = sqrt(lo * hi);
-            if (balance(d, k, mid, rho, Tg, J, H) > 0.0) lo = mid;
+            if (balance(d, k, c, mid) > 0.0) lo = mid;
             else hi = mid;
         }
         T = sqrt(lo * hi);
