@@ -183,6 +183,8 @@ __global__ void __launch_bounds__(256) k_walk_list(EvalArgs a) {
     }
 }
 
+constexpr int kOwnerCap = 512;  // entries per warp and walk step spread one per lane
+
 // Evaluation kernel: a team of WPT warps per target shares one block-wide walk stack and
 // one (segment x ray) tile in shared memory; the block processes one target at a time
 // and takes the next from a global work counter (persistent grid).
@@ -200,7 +202,8 @@ __global__ void __launch_bounds__(WPT * 32) k_evaluate(EvalArgs a) {
     const int nb = a.nbins;
     const int cells = nb * NPIX;
     constexpr int nq = THICK ? 6 : 2;
-    // layout: tile [nq][nb][NPIX] f32 | THICK: flags [NPIX] u64 | stack [cap] i32
+    // layout: tile [nq][nb][NPIX] f32 | THICK: flags [NPIX] u64 | stack [cap] i32 |
+    //         per warp: node buffer int4[32], entry owners u8[kOwnerCap]
     float* tL = reinterpret_cast<float*>(smem);
     float* tA = tL + cells;
     float* tLk = tA + cells;
@@ -209,6 +212,10 @@ __global__ void __launch_bounds__(WPT * 32) k_evaluate(EvalArgs a) {
     float* tQk = tVk + cells;
     unsigned long long* flags = reinterpret_cast<unsigned long long*>(smem + (size_t)nq * cells * 4);
     int* stack = reinterpret_cast<int*>(smem + (size_t)nq * cells * 4 + (THICK ? NPIX * 8 : 0));
+    int4* nodebuf = reinterpret_cast<int4*>(stack + a.stack_cap) + warp * 32;
+    unsigned char* owner =
+        reinterpret_cast<unsigned char*>(reinterpret_cast<int4*>(stack + a.stack_cap) + WPT * 32) +
+        warp * kOwnerCap;
     __shared__ int s_sp, s_overflow;
     __shared__ long long s_q;
     __shared__ double s_red[4][WPT];
@@ -298,8 +305,13 @@ __global__ void __launch_bounds__(WPT * 32) k_evaluate(EvalArgs a) {
                     else s_overflow = 1;
                 }
             }
+            // ---- map the accepted nodes onto the rays. Per node (one per thread): segment,
+            // beta, angular-kernel key. The thin deposits of the warp's nodes are then
+            // spread one angular-kernel entry per lane (a node's entries are distinct rays
+            // of one segment); thick deposits stay with the node's thread.
+            int ne = 0, ebase = 0, cbase = 0;
+            float bL = 0.0f, bA = 0.0f;
             if (acc) {
-                // ---- map the accepted node onto the rays
                 const int i = fixup(guess_bin((float)d2, lp), d2, thr, nb);
                 const float4 v0 = __ldg(a.thin + node);
                 const float4 v1 = __ldg(a.thick + node);
@@ -313,10 +325,12 @@ __global__ void __launch_bounds__(WPT * 32) k_evaluate(EvalArgs a) {
                     const int idx = ((Kz + a.D) * W + (Ky + a.D)) * W + (Kx + a.D);
                     const int e0 = __ldg(a.aoff + idx), e1 = __ldg(a.aoff + idx + 1);
                     if (e1 == e0) atomicOr(a.err, kErrAlphaKey);
-                    const float bL = beta * v0.x * inv_s3, bA = beta * v0.y * inv_s3;
-                    const bool thick_here = THICK && v1.w > 0.0f;
-                    unsigned long long fmask = 0ull;
-                    if (THICK && thick_here) {
+                    ne = e1 - e0;
+                    ebase = e0;
+                    cbase = i * NPIX;
+                    bL = beta * v0.x * inv_s3;
+                    bA = beta * v0.y * inv_s3;
+                    if (THICK && v1.w > 0.0f) {
                         const int64_t* lo = a.str_lo + ((int64_t)tl * (a.lmax + 1) + lvl) * nb;
                         const int64_t* hi = a.str_hi + ((int64_t)tl * (a.lmax + 1) + lvl) * nb;
                         const float d = sqrtf((float)d2);
@@ -324,25 +338,53 @@ __global__ void __launch_bounds__(WPT * 32) k_evaluate(EvalArgs a) {
                         const float dl = fmaxf(d - sd, 0.0f), dh = d + sd;
                         const int ilo = fixup(guess_bin(dl * dl, lp), d2, lo, nb);
                         const int ihi = fixup(guess_bin(dh * dh, lp), d2, hi, nb);
+                        unsigned long long fmask = 0ull;
                         for (int j = ilo; j < ihi; ++j) fmask |= 1ull << j;
-                    }
-                    float* cL = tL + i * NPIX;
-                    float* cA = tA + i * NPIX;
-                    for (int e = e0; e < e1; ++e) {
-                        const uint32_t ent = __ldg(a.aent + e);
-                        const int h = (int)(ent & 0xffffu);
-                        const float w = (float)(ent >> 16);
-                        atomicAdd(cL + h, w * bL);
-                        atomicAdd(cA + h, w * bA);
-                        if (THICK && thick_here) {
+                        for (int e = e0; e < e1; ++e) {
+                            const uint32_t ent = __ldg(a.aent + e);
+                            const int h = (int)(ent & 0xffffu);
                             const int cidx = i * NPIX + h;
-                            const float wn = w * inv_s3;
+                            const float wn = (float)(ent >> 16) * inv_s3;
                             atomicAdd(tLk + cidx, wn * v1.y);
                             atomicAdd(tAk + cidx, v1.z);
                             atomicAdd(tVk + cidx, wn * v1.w);
                             atomicAdd(tQk + cidx, wn * beta * v1.w);
                             if (fmask) atomicOr(flags + h, fmask);
                         }
+                    }
+                }
+            }
+            // warp-level exclusive scan of the entry counts
+            int inc = ne;
+            for (int off = 1; off < 32; off <<= 1) {
+                const int t = __shfl_up_sync(full, inc, off);
+                if (lane >= off) inc += t;
+            }
+            const int tw = __shfl_sync(full, inc, 31);
+            if (tw > 0) {
+                const int pre = inc - ne;
+                if (tw <= kOwnerCap) {
+                    if (ne > 0) {
+                        nodebuf[lane] = make_int4(cbase, ebase - pre, __float_as_int(bL), __float_as_int(bA));
+                        for (int k = 0; k < ne; ++k) owner[pre + k] = (unsigned char)lane;
+                    }
+                    __syncwarp();
+                    for (int r = lane; r < tw; r += 32) {
+                        const int4 nd = nodebuf[owner[r]];
+                        const uint32_t ent = __ldg(a.aent + nd.y + r);
+                        const int c = nd.x + (int)(ent & 0xffffu);
+                        const float w = (float)(ent >> 16);
+                        atomicAdd(tL + c, w * __int_as_float(nd.z));
+                        atomicAdd(tA + c, w * __int_as_float(nd.w));
+                    }
+                    __syncwarp();
+                } else {
+                    for (int e = ebase; e < ebase + ne; ++e) {
+                        const uint32_t ent = __ldg(a.aent + e);
+                        const int c = cbase + (int)(ent & 0xffffu);
+                        const float w = (float)(ent >> 16);
+                        atomicAdd(tL + c, w * bL);
+                        atomicAdd(tA + c, w * bA);
                     }
                 }
             }
@@ -512,7 +554,8 @@ treeray_status launch_t(treeray_ctx* c, const EvalArgs& a, cudaStream_t s) {
     EvalArgs b = a;
     // the team stack holds at most one batch of pushes (32 WPT groups) per level
     b.stack_cap = 32 * WPT * (c->lmax + 1) + 64;
-    const size_t smem = (size_t)nq * a.nbins * NPIX * 4 + (THICK ? NPIX * 8 : 0) + (size_t)b.stack_cap * 4;
+    const size_t smem = (size_t)nq * a.nbins * NPIX * 4 + (THICK ? NPIX * 8 : 0) + (size_t)b.stack_cap * 4 +
+                        (size_t)WPT * (32 * 16 + kOwnerCap);
     int smem_optin = 0, sms = 0;
     TR_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
     TR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
