@@ -161,6 +161,32 @@ treeray_status treeray_radpressure(treeray_t ctx, const float* J, const double* 
 treeray_status treeray_dust_temperature(treeray_t ctx, const float* Tgas, const float* heat_extra,
                                         const float* J, float* Td, treeray_stream_t stream);
 
+/*
+ * New dust temperatures on the grid of the last treeray_build (same densities, opacity
+ * input and stars): recompute the leaf quantities, node moments and centres of
+ * luminosity (Sec. 4.1) without rebuilding keys or structure. Td device float[N].
+ * Asynchronous and free of host synchronisation (it can be captured in a CUDA graph).
+ */
+treeray_status treeray_refresh(treeray_t ctx, const float* Td, treeray_stream_t stream);
+
+/*
+ * Dust-temperature / IR-field fixed point on the grid of the last treeray_build: repeat
+ *   T_d -> tree moments -> J (treeray_evaluate) -> T_new (treeray_dust_temperature)
+ * until max_k |T_new - T_d| / T_d < tol (the paper couples T_d and the IR field with a
+ * lag of one hydro step, Sec. 4.6; converging the coupling is the fixed point's job).
+ *  Tgas device float[N]; heat_extra device float[N] or NULL; Td device float[N]: the
+ *  initial guess on entry, the converged temperatures on return.
+ *  max_iter   iteration limit; tol relative tolerance (e.g. 1e-4).
+ *  unroll     0: one host round trip per iteration; k > 0: the loop runs as a CUDA
+ *             graph of k iterations replayed until a device flag reports convergence
+ *             (iterations past convergence do nothing).
+ *  iters      host int: iterations performed (the converging one included).
+ * Synchronous: returns when done. TREERAY_ENOCONV when max_iter is reached first.
+ */
+treeray_status treeray_fixed_point(treeray_t ctx, const float* Tgas, const float* heat_extra,
+                                   float* Td, int max_iter, double tol, int unroll, int* iters,
+                                   treeray_stream_t stream);
+
 /* Synchronize the stream and report errors recorded by kernels since the last check
  * (TREERAY_ETIMEOUT for a bounded loop that ran out, TREERAY_ECUDA for CUDA errors). */
 treeray_status treeray_check(treeray_t ctx, treeray_stream_t stream);

@@ -271,3 +271,25 @@ def brute_lc(n: int, box: float, Lcell, ak, targets, with_ext: bool = True):
     lib().or_brute_lc(n, box, _p(Lcell, C.c_double), _p(ak, C.c_double), len(t), _p(t, C.c_int64),
                       int(with_ext), _p(J, C.c_double), _p(F, C.c_double))
     return J, F
+
+
+def fixed_point(w, tgas, td0, heat=None, max_iter: int = 200, tol: float = 1e-4, threads: int = 0):
+    """Dust-temperature / IR-field fixed point (Sec. 4.6 balance iterated with the
+    transfer solution): T_d -> tree -> J -> T_new until max |T_new - T_d| / T_d < tol.
+    T_d is kept in float32 between iterations, as the inputs of the method are FP32
+    fields. Returns (T_d float32, iterations, list of per-iteration max changes)."""
+    import copy
+    ww = copy.copy(w)
+    td = np.ascontiguousarray(td0, np.float32).copy()
+    hist = []
+    for it in range(1, max_iter + 1):
+        ww.td = td
+        J, _ = Tree(ww).evaluate(threads=threads)
+        tn = dust_temperature(ww.params, ww.rho, tgas, J.astype(np.float32).astype(np.float64), heat,
+                              ww.kappa).astype(np.float32)
+        rel = float(np.max(np.abs(tn.astype(np.float64) - td) / td))
+        hist.append(rel)
+        td = tn
+        if rel < tol:
+            return td, it, hist
+    return td, -max_iter, hist

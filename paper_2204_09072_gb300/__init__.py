@@ -72,6 +72,9 @@ def lib():
     L.treeray_accepted.argtypes = [vp, vp, i64, C.c_int32, vp, vp, vp]
     L.treeray_alpha_counts_host.argtypes = [C.c_int, C.c_int, vp, i32p]
     L.treeray_walk_stats.argtypes = [vp, vp, i64, vp, vp]
+    L.treeray_refresh.argtypes = [vp, vp, vp]
+    L.treeray_fixed_point.argtypes = [vp, vp, vp, vp, C.c_int, C.c_double, C.c_int,
+                                      C.POINTER(C.c_int), vp]
     L.treeray_morton_order_noalloc.argtypes = [C.POINTER(Grid), vp, vp, vp]
     L.treeray_kernel_launches.argtypes = [vp]
     L.treeray_kernel_launches.restype = i64
@@ -79,7 +82,8 @@ def lib():
     for f in ("treeray_create", "treeray_destroy", "treeray_build", "treeray_evaluate",
               "treeray_radpressure", "treeray_dust_temperature", "treeray_check",
               "treeray_tree_export", "treeray_leaf_export", "treeray_accepted",
-              "treeray_alpha_counts_host", "treeray_walk_stats", "treeray_morton_order_noalloc"):
+              "treeray_alpha_counts_host", "treeray_walk_stats", "treeray_morton_order_noalloc",
+              "treeray_refresh", "treeray_fixed_point"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -206,6 +210,27 @@ class Context:
                                               _dev(heat_extra, f32, "heat_extra", True),
                                               _dev(J, f32, "J"), _dev(Td, f32, "Td"),
                                               _stream(stream)))
+
+    # -- C: treeray_refresh
+    def refresh(self, Td, stream=None):
+        import torch
+        _raise(lib().treeray_refresh(self.h, _dev(Td, torch.float32, "Td"), _stream(stream)))
+
+    # -- C: treeray_fixed_point
+    def fixed_point(self, Tgas, Td, heat_extra=None, max_iter=200, tol=1e-4, unroll=4,
+                    stream=None, raise_on_noconv=True) -> int:
+        """Iterate T_d to the fixed point in place; returns the iteration count."""
+        import torch
+        f32 = torch.float32
+        it = C.c_int(0)
+        rc = lib().treeray_fixed_point(self.h, _dev(Tgas, f32, "Tgas"),
+                                       _dev(heat_extra, f32, "heat_extra", True),
+                                       _dev(Td, f32, "Td"), int(max_iter), float(tol), int(unroll),
+                                       C.byref(it), _stream(stream))
+        if rc == 6 and not raise_on_noconv:
+            return -it.value
+        _raise(rc)
+        return it.value
 
     # -- C: treeray_check
     def check(self, stream=None):

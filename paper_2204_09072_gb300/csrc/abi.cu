@@ -204,6 +204,13 @@ treeray_status treeray_create(const treeray_params* p, treeray_t* out) {
 
 treeray_status treeray_destroy(treeray_t c) {
     if (!c) return TREERAY_OK;
+    if (c->fp_Tnew) cudaFree(c->fp_Tnew);
+    if (c->fp_J) cudaFree(c->fp_J);
+    if (c->fp_F) cudaFree(c->fp_F);
+    if (c->fp_flags) cudaFree(c->fp_flags);
+    if (c->fp_stream) cudaStreamDestroy(c->fp_stream);
+    for (cudaEvent_t e : c->fp_ev)
+        if (e) cudaEventDestroy(e);
     free_tree(c->tree);
     free_tables(c->dt);
     delete c;
@@ -254,6 +261,107 @@ treeray_status treeray_dust_temperature(treeray_t c, const float* Tgas, const fl
         return TREERAY_EINVAL;
     }
     return launch_dust(c, Tgas, heat_extra, J, Td, (cudaStream_t)stream);
+}
+
+treeray_status treeray_refresh(treeray_t c, const float* Td, treeray_stream_t stream) {
+    treeray_status rc = check_ctx(c, true);
+    if (rc != TREERAY_OK) return rc;
+    if (!Td) {
+        set_error("refresh: Td required");
+        return TREERAY_EINVAL;
+    }
+    if (c->p.kappa_model == 1) c->force_thick = true;
+    return refresh_tree(c, Td, nullptr, (cudaStream_t)stream);
+}
+
+namespace {
+// one fixed-point iteration: T_d -> tree moments -> J -> T_new -> largest change, T_d <- T_new
+treeray_status fp_iteration(treeray_t c, const float* Tgas, const float* heat, float* Td, double tol,
+                            int max_iter, cudaStream_t s) {
+    const int* skip = c->fp_flags;
+    treeray_status rc;
+    if ((rc = refresh_tree(c, Td, skip, s)) != TREERAY_OK) return rc;
+    if ((rc = launch_evaluate_skip(c, c->fp_J, c->fp_F, skip, s)) != TREERAY_OK) return rc;
+    if ((rc = launch_dust_skip(c, Tgas, heat, c->fp_J, c->fp_Tnew, skip, s)) != TREERAY_OK) return rc;
+    return launch_fp_update(c, c->fp_Tnew, Td, tol, max_iter, s);
+}
+}  // namespace
+
+treeray_status treeray_fixed_point(treeray_t c, const float* Tgas, const float* heat_extra, float* Td,
+                                   int max_iter, double tol, int unroll, int* iters,
+                                   treeray_stream_t stream) {
+    treeray_status rc = check_ctx(c, true);
+    if (rc != TREERAY_OK) return rc;
+    if (!Tgas || !Td || max_iter < 1 || !(tol > 0.0) || unroll < 0 || unroll > 64) {
+        set_error("fixed_point: Tgas and Td required, max_iter >= 1, tol > 0, unroll in 0..64");
+        return TREERAY_EINVAL;
+    }
+    const int64_t N = c->nleaves;
+    if (c->fp_cap < N) {
+        if (c->fp_Tnew) cudaFree(c->fp_Tnew);
+        if (c->fp_J) cudaFree(c->fp_J);
+        if (c->fp_F) cudaFree(c->fp_F);
+        c->fp_Tnew = nullptr;
+        c->fp_J = nullptr;
+        c->fp_F = nullptr;
+        c->fp_cap = 0;
+        TR_CUDA(cudaMalloc(&c->fp_Tnew, sizeof(float) * N));
+        TR_CUDA(cudaMalloc(&c->fp_J, sizeof(float) * N));
+        TR_CUDA(cudaMalloc(&c->fp_F, sizeof(double) * 3 * N));
+        c->fp_cap = N;
+    }
+    if (!c->fp_flags) TR_CUDA(cudaMalloc(&c->fp_flags, sizeof(int) * 4));
+    if (!c->fp_stream) TR_CUDA(cudaStreamCreateWithFlags(&c->fp_stream, cudaStreamNonBlocking));
+    for (cudaEvent_t& e : c->fp_ev)
+        if (!e) TR_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    if (c->p.kappa_model == 1) c->force_thick = true;
+    cudaStream_t us = (cudaStream_t)stream, fs = c->fp_stream;
+    TR_CUDA(cudaMemsetAsync(c->fp_flags, 0, sizeof(int) * 4, us));
+    TR_CUDA(cudaEventRecord(c->fp_ev[0], us));
+    TR_CUDA(cudaStreamWaitEvent(fs, c->fp_ev[0], 0));
+    int host_flags[2] = {0, 0};
+    if (unroll > 0) {
+        // a CUDA graph of `unroll` iterations, replayed until the device flag stops it;
+        // iterations after convergence return at once, so the result equals a plain loop
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        TR_CUDA(cudaStreamBeginCapture(fs, cudaStreamCaptureModeThreadLocal));
+        for (int u = 0; u < unroll && rc == TREERAY_OK; ++u) rc = fp_iteration(c, Tgas, heat_extra, Td, tol, max_iter, fs);
+        cudaError_t ce = cudaStreamEndCapture(fs, &graph);
+        if (rc != TREERAY_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        TR_CUDA(ce);
+        ce = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        TR_CUDA(ce);
+        const int launches = (max_iter + unroll - 1) / unroll;
+        for (int k = 0; k < launches; ++k) {
+            ce = cudaGraphLaunch(exec, fs);
+            if (ce == cudaSuccess) ce = cudaMemcpyAsync(host_flags, c->fp_flags, sizeof(int) * 2,
+                                                         cudaMemcpyDeviceToHost, fs);
+            if (ce == cudaSuccess) ce = cudaStreamSynchronize(fs);
+            if (ce != cudaSuccess || host_flags[0]) break;
+        }
+        cudaGraphExecDestroy(exec);
+        TR_CUDA(ce);
+    } else {
+        for (int k = 0; k < max_iter; ++k) {
+            if ((rc = fp_iteration(c, Tgas, heat_extra, Td, tol, max_iter, fs)) != TREERAY_OK) return rc;
+            TR_CUDA(cudaMemcpyAsync(host_flags, c->fp_flags, sizeof(int) * 2, cudaMemcpyDeviceToHost, fs));
+            TR_CUDA(cudaStreamSynchronize(fs));
+            if (host_flags[0]) break;
+        }
+    }
+    TR_CUDA(cudaEventRecord(c->fp_ev[1], fs));
+    TR_CUDA(cudaStreamWaitEvent(us, c->fp_ev[1], 0));
+    if (iters) *iters = host_flags[1];
+    if (host_flags[0] != 1) {
+        set_error("fixed_point: no convergence within max_iter");
+        return TREERAY_ENOCONV;
+    }
+    return TREERAY_OK;
 }
 
 treeray_status treeray_check(treeray_t c, treeray_stream_t stream) {

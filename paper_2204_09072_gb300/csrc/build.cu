@@ -303,12 +303,13 @@ struct MomArgs {
     int32_t* thick;
     float* rho_copy;
     float* kin_copy;
+    const int* skip;     // fixed-point mode: return at once when *skip != 0
 };
 
 // b-node quantities (Sec. 4.1.1); expression order fixed (see the file header)
 __global__ void k_leaf_moments(MomArgs a) {
     const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (s >= a.nleaves) return;
+    if (s >= a.nleaves || (a.skip && *a.skip)) return;
     const int64_t k = a.perm[s];
     const int64_t node = a.leaf_node[s];
     int l;
@@ -389,9 +390,10 @@ __global__ void k_leaf_moments(MomArgs a) {
 }
 
 // upward propagation (App. A) for the internal nodes of one level
-__global__ void k_internal_moments(const int4* geo, double* mom, int64_t nn, int64_t off, int64_t cnt) {
+__global__ void k_internal_moments(const int4* geo, double* mom, int64_t nn, int64_t off, int64_t cnt,
+                                   const int* skip) {
     const int64_t i = off + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= off + cnt) return;
+    if (i >= off + cnt || (skip && *skip)) return;
     const int4 g = geo[i];
     if (g.w < 0) return;
     double Lt = 0.0, At = 0.0, Vt = 0.0, LVk = 0.0, Ak = 0.0, Vk = 0.0, m = 0.0;
@@ -437,7 +439,8 @@ __global__ void k_internal_moments(const int4* geo, double* mom, int64_t nn, int
 
 // luminosity scale: a power of two at or above the largest of the root's thin luminosity
 // and its thick L_ V / u, so that FP32 node records stay far from overflow
-__global__ void k_scale(const double* mom, int64_t nn, double u, double* scal) {
+__global__ void k_scale(const double* mom, int64_t nn, double u, double* scal, const int* skip) {
+    if (skip && *skip) return;
     double m = mom[0];
     const double t = mom[3 * nn] / u;
     if (t > m) m = t;
@@ -453,9 +456,9 @@ __global__ void k_scale(const double* mom, int64_t nn, double u, double* scal) {
 // FP32 walk records in internal units: luminosity / L_scale, area / u^2, volume / u^3,
 // thick sum L_ V / (L_scale u), COL offsets from the geometric centre in half-cells
 __global__ void k_pack(const int4* geo, const double* mom, int64_t nn, double u, const double* scal,
-                       float4* thin, float4* thick) {
+                       float4* thin, float4* thick, const int* skip) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= nn) return;
+    if (i >= nn || (skip && *skip)) return;
     const double Ls = scal[0];
     const double u2 = u * u, u3 = u2 * u;
     const int4 g = geo[i];
@@ -729,18 +732,18 @@ treeray_status build_tree(treeray_ctx* c, const treeray_grid* gr, const float* r
     MomArgs m{lg, T.perm, T.leaf_node, rho, Td, kappa, dstars, n_stars, gr->box,
               c->p.kappa_model, c->p.kappa0, c->p.kappa_ext_scale, c->p.dust_emission, nn, N,
               T.mom, T.geo, T.kap, T.tau, T.jsrc, T.psrc, T.thickflag, T.rho,
-              kappa ? T.kin : nullptr};
+              kappa ? T.kin : nullptr, nullptr};
     k_leaf_moments<<<nblk(N, 128), 128, 0, st>>>(m);
     ++c->launches;
     for (int l = lmax - 1; l >= 0; --l)
         if (nent[l] > 0) {
             k_internal_moments<<<nblk(nent[l], 128), 128, 0, st>>>(T.geo, T.mom, nn, c->level_off[l],
-                                                                   nent[l]);
+                                                                   nent[l], nullptr);
             ++c->launches;
         }
-    k_scale<<<1, 1, 0, st>>>(T.mom, nn, c->u, c->dt.scal);
+    k_scale<<<1, 1, 0, st>>>(T.mom, nn, c->u, c->dt.scal, nullptr);
     ++c->launches;
-    k_pack<<<nblk(nn, 256), 256, 0, st>>>(T.geo, T.mom, nn, c->u, c->dt.scal, T.thin, T.thick);
+    k_pack<<<nblk(nn, 256), 256, 0, st>>>(T.geo, T.mom, nn, c->u, c->dt.scal, T.thin, T.thick, nullptr);
     ++c->launches;
     TR_CUDA(cudaGetLastError());
     double root_vk = 0.0;
@@ -753,8 +756,38 @@ treeray_status build_tree(treeray_ctx* c, const treeray_grid* gr, const float* r
         return TREERAY_EINVAL;
     }
     c->has_thick = root_vk > 0.0;
+    c->grid_n = gr->n;
+    c->n_stars = n_stars;
     c->kin_given = kappa != nullptr;
     return upload_tables(c, st);
+}
+
+// New dust temperatures on the same grid, densities, opacities and stars: leaf
+// quantities, node moments, the luminosity scale and the walk records are recomputed;
+// keys, structure and tables are kept. No host synchronisation, so the sequence can be
+// captured in a CUDA graph. With skip != nullptr every kernel returns at once while
+// *skip != 0 (the fixed point has converged).
+treeray_status refresh_tree(treeray_ctx* c, const float* Td, const int* skip, cudaStream_t st) {
+    DeviceTree& T = c->tree;
+    const int64_t N = c->nleaves, nn = c->nnodes;
+    LeafGrid lg{c->amr ? 0 : c->grid_n, c->lmax, T.blocks};
+    MomArgs m{lg, T.perm, T.leaf_node, T.rho, Td, c->kin_given ? T.kin : nullptr, T.stars, c->n_stars,
+              c->box, c->p.kappa_model, c->p.kappa0, c->p.kappa_ext_scale, c->p.dust_emission, nn, N,
+              T.mom, T.geo, T.kap, T.tau, T.jsrc, T.psrc, T.thickflag, T.rho, nullptr, skip};
+    k_leaf_moments<<<nblk(N, 128), 128, 0, st>>>(m);
+    ++c->launches;
+    for (int l = c->lmax - 1; l >= 0; --l)
+        if (c->level_cnt[l] > 0) {
+            k_internal_moments<<<nblk(c->level_cnt[l], 128), 128, 0, st>>>(T.geo, T.mom, nn, c->level_off[l],
+                                                                           c->level_cnt[l], skip);
+            ++c->launches;
+        }
+    k_scale<<<1, 1, 0, st>>>(T.mom, nn, c->u, c->dt.scal, skip);
+    ++c->launches;
+    k_pack<<<nblk(nn, 256), 256, 0, st>>>(T.geo, T.mom, nn, c->u, c->dt.scal, T.thin, T.thick, skip);
+    ++c->launches;
+    TR_CUDA(cudaGetLastError());
+    return TREERAY_OK;
 }
 
 }  // namespace tr

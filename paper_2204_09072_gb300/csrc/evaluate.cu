@@ -49,6 +49,7 @@ struct EvalArgs {
     int32_t* acc_counts;   // accepted-list mode
     int32_t* acc_ids;
     unsigned long long* stats;  // accepted-list mode: totals of visits, accepted, entries
+    const int* skip;            // fixed-point mode: return at once when *skip != 0
     int acc_cap;
     int64_t n;
     int64_t nleaves;
@@ -225,6 +226,7 @@ __global__ void __launch_bounds__(WPT * 32) k_evaluate(EvalArgs a) {
     const float inv_s3 = 1.0f / 512.0f;
     const int W = 2 * a.D + 1;
     const int4 root = a.geo[0];
+    if (a.skip && *a.skip) return;
 
     for (;;) {
         if (tid == 0) s_q = (long long)atomicAdd(a.queue, 1ull);
@@ -581,7 +583,7 @@ treeray_status launch_t(treeray_ctx* c, const EvalArgs& a, cudaStream_t s) {
 }
 
 treeray_status dispatch_eval(treeray_ctx* c, const EvalArgs& a, cudaStream_t s) {
-    const bool thick = c->has_thick;
+    const bool thick = c->has_thick || c->force_thick;
     switch (c->p.npix) {
         case 12: return thick ? launch_t<12, true>(c, a, s) : launch_t<12, false>(c, a, s);
         case 48: return thick ? launch_t<48, true>(c, a, s) : launch_t<48, false>(c, a, s);
@@ -636,6 +638,14 @@ treeray_status launch_evaluate(treeray_ctx* c, const int32_t* targets, int64_t n
     EvalArgs a = make_args(c, targets, n);
     a.J = J;
     a.F = F;
+    return dispatch_eval(c, a, s);
+}
+
+treeray_status launch_evaluate_skip(treeray_ctx* c, float* J, double* F, const int* skip, cudaStream_t s) {
+    EvalArgs a = make_args(c, nullptr, c->nleaves);
+    a.J = J;
+    a.F = F;
+    a.skip = skip;
     return dispatch_eval(c, a, s);
 }
 

@@ -114,6 +114,16 @@ struct treeray_ctx {
     int level_cnt[tr::kMaxLevel + 2] = {0};
     bool has_thick = false;
     bool kin_given = false;
+    bool force_thick = false;  // fixed point: thin/thick classes may change between refreshes
+    int grid_n = 0, n_stars = 0;
+    // fixed-point scratch
+    float* fp_Tnew = nullptr;
+    float* fp_J = nullptr;
+    double* fp_F = nullptr;
+    int* fp_flags = nullptr;       // [0] done (1 converged, 2 out of iterations), [1] iterations, [2] max change bits
+    int64_t fp_cap = 0;
+    cudaStream_t fp_stream = nullptr;
+    cudaEvent_t fp_ev[2] = {nullptr, nullptr};
     int64_t launches = 0;  // kernels launched by this context
     // table cache key
     int tab_lmax = -1;
@@ -137,6 +147,12 @@ treeray_status launch_radpressure(treeray_ctx* c, const float* J, const double* 
 treeray_status launch_dust(treeray_ctx* c, const float* Tgas, const float* heat, const float* J,
                            float* Td, cudaStream_t s);
 treeray_status upload_tables(treeray_ctx* c, cudaStream_t s);
+treeray_status refresh_tree(treeray_ctx* c, const float* Td, const int* skip, cudaStream_t s);
+treeray_status launch_evaluate_skip(treeray_ctx* c, float* J, double* F, const int* skip, cudaStream_t s);
+treeray_status launch_dust_skip(treeray_ctx* c, const float* Tgas, const float* heat, const float* J,
+                                float* Td, const int* skip, cudaStream_t s);
+treeray_status launch_fp_update(treeray_ctx* c, const float* Tnew, float* Td, double tol, int max_iter,
+                                cudaStream_t s);
 void free_tree(tr::DeviceTree& t);
 void free_tables(tr::DeviceTables& t);
 }  // namespace tr

@@ -2,6 +2,8 @@
 // equilibrium dust temperature (Sec. 4.6, App. D). Plain elementwise kernels in FP64.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "internal.h"
 
 namespace tr {
@@ -44,6 +46,7 @@ __global__ void k_radpressure(RpArgs r) {
 }
 
 struct DustArgs {
+    const int* skip;
     const float* rho;
     const float* tgas;
     const float* heat;
@@ -83,7 +86,7 @@ __device__ inline double balance(const DustArgs& d, int64_t k, const Cell& c, do
 // root by bracketing from the 2.7 K floor and 60 bisections in ln T
 __global__ void k_dust(DustArgs d) {
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (k >= d.n) return;
+    if (k >= d.n || (d.skip && *d.skip)) return;
     Cell c;
     c.rho = (double)d.rho[k];
     c.Tg = (double)d.tgas[k];
@@ -126,10 +129,56 @@ treeray_status launch_radpressure(treeray_ctx* c, const float* J, const double* 
 
 treeray_status launch_dust(treeray_ctx* c, const float* Tgas, const float* heat, const float* J, float* Td,
                            cudaStream_t s) {
-    DustArgs d{c->tree.rho, Tgas, heat, J, c->kin_given ? c->tree.kin : nullptr, Td, c->nleaves,
+    return launch_dust_skip(c, Tgas, heat, J, Td, nullptr, s);
+}
+
+treeray_status launch_dust_skip(treeray_ctx* c, const float* Tgas, const float* heat, const float* J,
+                                float* Td, const int* skip, cudaStream_t s) {
+    DustArgs d{skip, c->tree.rho, Tgas, heat, J, c->kin_given ? c->tree.kin : nullptr, Td, c->nleaves,
                c->p.kappa_model, c->p.kappa0, c->p.dust_to_gas};
     k_dust<<<(int)((c->nleaves + 127) / 128), 128, 0, s>>>(d);
     c->launches += 1;
+    TR_CUDA(cudaGetLastError());
+    return TREERAY_OK;
+}
+
+namespace {
+// Largest relative change max_k |T_new - T| / T of one fixed-point iteration (as the
+// bits of a non-negative float, whose integer order is the float order); T <- T_new.
+__global__ void k_fp_delta(const float* Tnew, float* T, int64_t n, int* flags) {
+    if (flags[0]) return;
+    float m = 0.0f;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const float t0 = T[k], t1 = Tnew[k];
+        m = fmaxf(m, fabsf(t1 - t0) / t0);
+        T[k] = t1;
+    }
+    for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<unsigned*>(flags + 2), __float_as_uint(m));
+}
+
+// count the iteration; converged (1) when the largest change is below tol, out of
+// iterations (2) at max_iter
+__global__ void k_fp_check(int* flags, float tol, int max_iter) {
+    if (flags[0]) return;
+    flags[1] += 1;
+    const float m = __uint_as_float((unsigned)flags[2]);
+    if (m < tol) flags[0] = 1;
+    else if (flags[1] >= max_iter) flags[0] = 2;
+    flags[2] = 0;
+}
+}  // namespace
+
+treeray_status launch_fp_update(treeray_ctx* c, const float* Tnew, float* Td, double tol, int max_iter,
+                                cudaStream_t s) {
+    int sms = 0;
+    TR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+    int64_t blocks = std::min<int64_t>((c->nleaves + 255) / 256, (int64_t)sms * 8);
+    if (blocks < 1) blocks = 1;
+    k_fp_delta<<<(int)blocks, 256, 0, s>>>(Tnew, Td, c->nleaves, c->fp_flags);
+    k_fp_check<<<1, 1, 0, s>>>(c->fp_flags, (float)tol, max_iter);
+    c->launches += 2;
     TR_CUDA(cudaGetLastError());
     return TREERAY_OK;
 }
