@@ -176,6 +176,11 @@ def run_ours(args):
     p_src = torch.empty(n, dtype=torch.float32, device=dev)
     Td = torch.empty(n, dtype=torch.float32, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    # one-time set-up outside the timed region: build once and let the autotuner pick the
+    # evaluate kernel's warps per target for this tree
+    with torch.cuda.stream(st):
+        ctx.build(w.box_cm, rho, td, n=w.uniform_n, star_pos=w.star_pos, star_lum=w.star_lum, stream=st)
+        best_wpt, tune_ms = ctx.autotune(65536, stream=st)
 
     def step(ev=None):
         if ev:
@@ -288,7 +293,9 @@ def run_ours(args):
             "config": config(npix, {"parallelism": f"replicas x{world}",
                                     "ms_build": statistics.mean(build_ms),
                                     "ms_evaluate": ms_eval,
-                                    "ms_radpressure_dust": statistics.mean(post_ms)}),
+                                    "ms_radpressure_dust": statistics.mean(post_ms),
+                                    "warps_per_target": best_wpt,
+                                    "autotune_ms_wpt2_4_8": tune_ms}),
             "roofline": {"bound": "hbm", "kernel": "k_evaluate", "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_kind": peak_kind, "traffic": traffic,

@@ -187,6 +187,39 @@ treeray_status treeray_fixed_point(treeray_t ctx, const float* Tgas, const float
                                    float* Td, int max_iter, double tol, int unroll, int* iters,
                                    treeray_stream_t stream);
 
+/*
+ * Warps per target for the evaluate kernel, chosen by timing (autotuner): the evaluate
+ * kernel runs a team of 2, 4 or 8 warps per target sharing one walk stack and one ray
+ * tile; each choice is launched twice on n_sample targets of the current tree (a fixed
+ * stride permutation of the leaves) and the second launch is timed. The fastest choice is
+ * kept by the context. best_wpt (host int) and ms (host float[3], times for 2, 4, 8)
+ * may be NULL. Synchronous.
+ */
+treeray_status treeray_autotune(treeray_t ctx, int64_t n_sample, int* best_wpt, float* ms,
+                                treeray_stream_t stream);
+
+/* Set the evaluate kernel's warps per target (2, 4 or 8) by hand; 4 is the default. */
+treeray_status treeray_set_warps_per_target(treeray_t ctx, int wpt);
+
+/*
+ * Batches: many independent boxes (contexts with built trees, the same npix and nbins,
+ * any grids and parameters otherwise) evaluated by one persistent launch whose work
+ * counter spans the targets of all boxes, so uneven boxes balance across the GPU.
+ * A batch records the boxes' trees when created; rebuilding a box invalidates it
+ * (destroy and create again). Contexts must outlive the batch.
+ */
+typedef struct treeray_batch* treeray_batch_t;
+treeray_status treeray_batch_create(const treeray_t* ctxs, int n_boxes, treeray_batch_t* out);
+treeray_status treeray_batch_destroy(treeray_batch_t batch);
+/*
+ * Evaluate every leaf of every box (Secs. 4.2-4.4, as treeray_evaluate with targets NULL).
+ *  J, F       host arrays of n_boxes device pointers: J[k] float[N_k], F[k] double[3 N_k].
+ *  use_graph  1: the launch is captured once into a CUDA graph (per set of output
+ *             pointers) and replayed; 0: plain launch.
+ */
+treeray_status treeray_batch_evaluate(treeray_batch_t batch, float* const* J, double* const* F,
+                                      int use_graph, treeray_stream_t stream);
+
 /* Synchronize the stream and report errors recorded by kernels since the last check
  * (TREERAY_ETIMEOUT for a bounded loop that ran out, TREERAY_ECUDA for CUDA errors). */
 treeray_status treeray_check(treeray_t ctx, treeray_stream_t stream);

@@ -14,7 +14,7 @@ import os
 from .build_lib import OUT as LIB_PATH
 from .build_lib import build as build_library
 
-__all__ = ["Params", "Grid", "Context", "TreeRayError", "lib", "alpha_counts_host",
+__all__ = ["Params", "Grid", "Context", "Batch", "TreeRayError", "lib", "alpha_counts_host",
            "build_library", "LIB_PATH", "STATUS"]
 
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTBUILT", 5: "ETIMEOUT",
@@ -75,6 +75,11 @@ def lib():
     L.treeray_refresh.argtypes = [vp, vp, vp]
     L.treeray_fixed_point.argtypes = [vp, vp, vp, vp, C.c_int, C.c_double, C.c_int,
                                       C.POINTER(C.c_int), vp]
+    L.treeray_autotune.argtypes = [vp, i64, C.POINTER(C.c_int), C.POINTER(C.c_float), vp]
+    L.treeray_set_warps_per_target.argtypes = [vp, C.c_int]
+    L.treeray_batch_create.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(vp)]
+    L.treeray_batch_destroy.argtypes = [vp]
+    L.treeray_batch_evaluate.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.c_int, vp]
     L.treeray_morton_order_noalloc.argtypes = [C.POINTER(Grid), vp, vp, vp]
     L.treeray_kernel_launches.argtypes = [vp]
     L.treeray_kernel_launches.restype = i64
@@ -83,7 +88,9 @@ def lib():
               "treeray_radpressure", "treeray_dust_temperature", "treeray_check",
               "treeray_tree_export", "treeray_leaf_export", "treeray_accepted",
               "treeray_alpha_counts_host", "treeray_walk_stats", "treeray_morton_order_noalloc",
-              "treeray_refresh", "treeray_fixed_point"):
+              "treeray_refresh", "treeray_fixed_point", "treeray_autotune",
+              "treeray_set_warps_per_target", "treeray_batch_create", "treeray_batch_destroy",
+              "treeray_batch_evaluate"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -232,6 +239,18 @@ class Context:
         _raise(rc)
         return it.value
 
+    # -- C: treeray_autotune
+    def autotune(self, n_sample: int = 65536, stream=None):
+        """Time 2, 4 and 8 warps per target; keeps the fastest. Returns (best, [ms2, ms4, ms8])."""
+        best = C.c_int(0)
+        ms = (C.c_float * 3)()
+        _raise(lib().treeray_autotune(self.h, int(n_sample), C.byref(best), ms, _stream(stream)))
+        return best.value, list(ms)
+
+    # -- C: treeray_set_warps_per_target
+    def set_warps_per_target(self, wpt: int):
+        _raise(lib().treeray_set_warps_per_target(self.h, int(wpt)))
+
     # -- C: treeray_check
     def check(self, stream=None):
         _raise(lib().treeray_check(self.h, _stream(stream)))
@@ -293,3 +312,33 @@ class Context:
                                       _dev(counts, torch.int32, "counts"),
                                       _dev(ids, torch.int32, "ids"), _stream(stream)))
         return counts, ids
+
+
+class Batch:
+    """C: treeray_batch_t. Independent boxes evaluated by one persistent launch."""
+
+    def __init__(self, contexts):
+        self.contexts = list(contexts)
+        arr = (C.c_void_p * len(self.contexts))(*[c.h.value for c in self.contexts])
+        h = C.c_void_p()
+        _raise(lib().treeray_batch_create(arr, len(self.contexts), C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().treeray_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- C: treeray_batch_evaluate
+    def evaluate(self, Js, Fs, use_graph: bool = True, stream=None):
+        import torch
+        n = len(self.contexts)
+        jp = (C.c_void_p * n)(*[_dev(j, torch.float32, "J").value for j in Js])
+        fp = (C.c_void_p * n)(*[_dev(f, torch.float64, "F").value for f in Fs])
+        _raise(lib().treeray_batch_evaluate(self.h, jp, fp, int(bool(use_graph)), _stream(stream)))

@@ -18,12 +18,15 @@
 // L_scale erg/s; fluxes come out in L_scale / u^2 and are converted to CGS at the end.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <new>
+#include <vector>
+
 #include "internal.h"
 
 namespace tr {
-namespace {
 
-struct EvalArgs {
+struct __align__(16) EvalArgs {
     const int4* __restrict__ geo;
     const float4* __restrict__ thin;
     const float4* __restrict__ thick;
@@ -56,6 +59,9 @@ struct EvalArgs {
     int lmax, nbins, D, stack_cap, npix;
     double u;
 };
+
+namespace {
+
 
 __device__ __forceinline__ int alpha_key(int o, int elog) {
     // K = 8 o / E when integral, else the nearest odd integer (floor(4 o / E) * 2 + 1)
@@ -196,7 +202,8 @@ constexpr int kOwnerCap = 512;  // entries per warp and walk step spread one per
 //   rays:    one thread per ray integrates the segments inside out in FP32 (optical-depth
 //            prefix in FP64 once it passes 40), then the team reduces J and F in FP64.
 template <int NPIX, bool THICK, int WPT>
-__global__ void __launch_bounds__(WPT * 32) k_evaluate(EvalArgs a) {
+__global__ void __launch_bounds__(WPT * 32) k_evaluate(EvalArgs a, const EvalArgs* __restrict__ boxes,
+                                                       const int64_t* __restrict__ box_start, int nbox) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int NT = WPT * 32;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -224,37 +231,63 @@ __global__ void __launch_bounds__(WPT * 32) k_evaluate(EvalArgs a) {
     const unsigned lt_mask = (1u << lane) - 1u;
     const float omega = (float)(4.0 * kPi / NPIX);
     const float inv_s3 = 1.0f / 512.0f;
-    const int W = 2 * a.D + 1;
-    const int4 root = a.geo[0];
     if (a.skip && *a.skip) return;
+    // the per-box descriptor lives in shared memory: copied once (one box) or per target (a
+    // batch of boxes whose targets share one work counter)
+    __shared__ __align__(16) EvalArgs s_box;
+    __shared__ int s_b;
+    const EvalArgs& A = s_box;
+    if (!boxes) {
+        for (int w = tid; w < (int)(sizeof(EvalArgs) / 8); w += NT)
+            reinterpret_cast<unsigned long long*>(&s_box)[w] = reinterpret_cast<const unsigned long long*>(&a)[w];
+    }
 
     for (;;) {
         if (tid == 0) s_q = (long long)atomicAdd(a.queue, 1ull);
         __syncthreads();
-        const long long q = s_q;
+        long long q = s_q;
         if (q >= a.n) break;
+        if (boxes) {
+            if (tid == 0) {
+                int lo = 0, hi = nbox - 1;  // last box with box_start[b] <= q
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (box_start[mid] <= q) lo = mid;
+                    else hi = mid - 1;
+                }
+                s_b = lo;
+            }
+            __syncthreads();
+            const EvalArgs* src = boxes + s_b;
+            for (int w = tid; w < (int)(sizeof(EvalArgs) / 8); w += NT)
+                reinterpret_cast<unsigned long long*>(&s_box)[w] = reinterpret_cast<const unsigned long long*>(src)[w];
+            q -= box_start[s_b];
+        }
+        __syncthreads();
+        const int W = 2 * A.D + 1;
+        const int4 root = A.geo[0];
         int64_t s;
         int64_t out;
-        if (a.targets) {
-            const int32_t k = a.targets[q];
-            if (k < 0 || k >= a.nleaves) {
-                if (tid == 0) atomicOr(a.err, kErrTarget);
+        if (A.targets) {
+            const int32_t k = A.targets[q];
+            if (k < 0 || k >= A.nleaves) {
+                if (tid == 0) atomicOr(A.err, kErrTarget);
                 __syncthreads();
                 continue;
             }
-            s = a.inv_perm[k];
+            s = A.inv_perm[k];
             out = q;
         } else {
             s = q;
-            out = a.perm[s];
+            out = A.perm[s];
         }
-        const int tnode = a.leaf_node[s];
-        const int4 tg = a.geo[tnode];
+        const int tnode = A.leaf_node[s];
+        const int4 tg = A.geo[tnode];
         const int tx = tg.x, ty = tg.y, tz = tg.z & 0xffffff;
         const int tl = tg.z >> 24;
-        const int64_t* thr = a.bin_thr + (int64_t)tl * nb;
-        const float* R2 = a.R2 + (int64_t)tl * nb;
-        const float2 lp = __ldg(a.lvlp + tl);
+        const int64_t* thr = A.bin_thr + (int64_t)tl * nb;
+        const float* R2 = A.R2 + (int64_t)tl * nb;
+        const float2 lp = __ldg(A.lvlp + tl);
 
         for (int i = tid; i < nq * cells; i += NT) tL[i] = 0.0f;
         if (THICK)
@@ -283,16 +316,16 @@ __global__ void __launch_bounds__(WPT * 32) k_evaluate(EvalArgs a) {
             int ox = 0, oy = 0, oz = 0, lvl = 0;
             int64_t d2 = 0;
             if (valid) {
-                gg = __ldg(a.geo + node);
+                gg = __ldg(A.geo + node);
                 lvl = gg.z >> 24;
                 ox = gg.x - tx;
                 oy = gg.y - ty;
                 oz = (gg.z & 0xffffff) - tz;
                 d2 = (int64_t)ox * ox + (int64_t)oy * oy + (int64_t)oz * oz;
                 if (gg.w >= 0) {
-                    const int E = 2 << (a.lmax - lvl);
+                    const int E = 2 << (A.lmax - lvl);
                     const bool inside = 2 * abs(ox) < E && 2 * abs(oy) < E && 2 * abs(oz) < E;
-                    open = inside || d2 <= __ldg(a.open_max + lvl);
+                    open = inside || d2 <= __ldg(A.open_max + lvl);
                 }
                 acc = !open && d2 != 0;  // the own cell is deposited after the walk
             }
@@ -303,7 +336,7 @@ __global__ void __launch_bounds__(WPT * 32) k_evaluate(EvalArgs a) {
                 pos0 = __shfl_sync(full, pos0, 0);
                 if (open) {
                     const int pos = pos0 + __popc(om & lt_mask);
-                    if (pos < a.stack_cap) stack[pos] = gg.w;
+                    if (pos < A.stack_cap) stack[pos] = gg.w;
                     else s_overflow = 1;
                 }
             }
@@ -315,35 +348,35 @@ __global__ void __launch_bounds__(WPT * 32) k_evaluate(EvalArgs a) {
             float bL = 0.0f, bA = 0.0f;
             if (acc) {
                 const int i = fixup(guess_bin((float)d2, lp), d2, thr, nb);
-                const float4 v0 = __ldg(a.thin + node);
-                const float4 v1 = __ldg(a.thick + node);
+                const float4 v0 = __ldg(A.thin + node);
+                const float4 v1 = __ldg(A.thick + node);
                 const float rx = (float)ox + v0.z, ry = (float)oy + v0.w, rz = (float)oz + v1.x;
                 const float beta = __ldg(R2 + i) / (rx * rx + ry * ry + rz * rz);
-                const int elog = a.lmax - lvl + 1;
+                const int elog = A.lmax - lvl + 1;
                 const int Kx = alpha_key(ox, elog), Ky = alpha_key(oy, elog), Kz = alpha_key(oz, elog);
-                if (abs(Kx) > a.D || abs(Ky) > a.D || abs(Kz) > a.D) {
-                    atomicOr(a.err, kErrAlphaKey);
+                if (abs(Kx) > A.D || abs(Ky) > A.D || abs(Kz) > A.D) {
+                    atomicOr(A.err, kErrAlphaKey);
                 } else {
-                    const int idx = ((Kz + a.D) * W + (Ky + a.D)) * W + (Kx + a.D);
-                    const int e0 = __ldg(a.aoff + idx), e1 = __ldg(a.aoff + idx + 1);
-                    if (e1 == e0) atomicOr(a.err, kErrAlphaKey);
+                    const int idx = ((Kz + A.D) * W + (Ky + A.D)) * W + (Kx + A.D);
+                    const int e0 = __ldg(A.aoff + idx), e1 = __ldg(A.aoff + idx + 1);
+                    if (e1 == e0) atomicOr(A.err, kErrAlphaKey);
                     ne = e1 - e0;
                     ebase = e0;
                     cbase = i * NPIX;
                     bL = beta * v0.x * inv_s3;
                     bA = beta * v0.y * inv_s3;
                     if (THICK && v1.w > 0.0f) {
-                        const int64_t* lo = a.str_lo + ((int64_t)tl * (a.lmax + 1) + lvl) * nb;
-                        const int64_t* hi = a.str_hi + ((int64_t)tl * (a.lmax + 1) + lvl) * nb;
+                        const int64_t* lo = A.str_lo + ((int64_t)tl * (A.lmax + 1) + lvl) * nb;
+                        const int64_t* hi = A.str_hi + ((int64_t)tl * (A.lmax + 1) + lvl) * nb;
                         const float d = sqrtf((float)d2);
-                        const float sd = 0.8660254f * (float)(2 << (a.lmax - lvl));
+                        const float sd = 0.8660254f * (float)(2 << (A.lmax - lvl));
                         const float dl = fmaxf(d - sd, 0.0f), dh = d + sd;
                         const int ilo = fixup(guess_bin(dl * dl, lp), d2, lo, nb);
                         const int ihi = fixup(guess_bin(dh * dh, lp), d2, hi, nb);
                         unsigned long long fmask = 0ull;
                         for (int j = ilo; j < ihi; ++j) fmask |= 1ull << j;
                         for (int e = e0; e < e1; ++e) {
-                            const uint32_t ent = __ldg(a.aent + e);
+                            const uint32_t ent = __ldg(A.aent + e);
                             const int h = (int)(ent & 0xffffu);
                             const int cidx = i * NPIX + h;
                             const float wn = (float)(ent >> 16) * inv_s3;
@@ -373,7 +406,7 @@ __global__ void __launch_bounds__(WPT * 32) k_evaluate(EvalArgs a) {
                     __syncwarp();
                     for (int r = lane; r < tw; r += 32) {
                         const int4 nd = nodebuf[owner[r]];
-                        const uint32_t ent = __ldg(a.aent + nd.y + r);
+                        const uint32_t ent = __ldg(A.aent + nd.y + r);
                         const int c = nd.x + (int)(ent & 0xffffu);
                         const float w = (float)(ent >> 16);
                         atomicAdd(tL + c, w * __int_as_float(nd.z));
@@ -382,7 +415,7 @@ __global__ void __launch_bounds__(WPT * 32) k_evaluate(EvalArgs a) {
                     __syncwarp();
                 } else {
                     for (int e = ebase; e < ebase + ne; ++e) {
-                        const uint32_t ent = __ldg(a.aent + e);
+                        const uint32_t ent = __ldg(A.aent + e);
                         const int c = cbase + (int)(ent & 0xffffu);
                         const float w = (float)(ent >> 16);
                         atomicAdd(tL + c, w * bL);
@@ -393,17 +426,17 @@ __global__ void __launch_bounds__(WPT * 32) k_evaluate(EvalArgs a) {
             __syncthreads();
         }
         if (s_overflow) {
-            if (tid == 0) atomicOr(a.err, kErrStack);
+            if (tid == 0) atomicOr(A.err, kErrStack);
             __syncthreads();
             continue;
         }
         // ---- own cell: segment 0 of every ray, alpha = 1/N_pix, beta = 1
         {
-            const float4 v0 = __ldg(a.thin + tnode);
-            const float4 v1 = __ldg(a.thick + tnode);
+            const float4 v0 = __ldg(A.thin + tnode);
+            const float4 v1 = __ldg(A.thick + tnode);
             unsigned long long fmask = 0ull;
             if (THICK && v1.w > 0.0f) {
-                const int64_t* hi = a.str_hi + ((int64_t)tl * (a.lmax + 1) + tl) * nb;
+                const int64_t* hi = A.str_hi + ((int64_t)tl * (A.lmax + 1) + tl) * nb;
                 int ihi = 0;
                 for (int j = 1; j < nb; ++j) ihi += 0 >= __ldg(hi + j);
                 for (int j = 0; j < ihi; ++j) fmask |= 1ull << j;
@@ -483,9 +516,9 @@ __global__ void __launch_bounds__(WPT * 32) k_evaluate(EvalArgs a) {
                 if (THICK && f > 0.0f) ek *= (1.0f - f) + f * expf(-tk);
             }
             Js += (double)Fh;
-            Fx -= (double)Fh * (double)__ldg(a.nhat + 3 * h);
-            Fy -= (double)Fh * (double)__ldg(a.nhat + 3 * h + 1);
-            Fz -= (double)Fh * (double)__ldg(a.nhat + 3 * h + 2);
+            Fx -= (double)Fh * (double)__ldg(A.nhat + 3 * h);
+            Fy -= (double)Fh * (double)__ldg(A.nhat + 3 * h + 1);
+            Fz -= (double)Fh * (double)__ldg(A.nhat + 3 * h + 2);
         }
         // ---- team reduction in FP64 (only warps that hold rays contribute)
         if (warp * 32 < NPIX) {
@@ -507,12 +540,12 @@ __global__ void __launch_bounds__(WPT * 32) k_evaluate(EvalArgs a) {
             double r[4] = {0.0, 0.0, 0.0, 0.0};
             for (int w = 0; w < WPT && w * 32 < NPIX; ++w)
                 for (int c = 0; c < 4; ++c) r[c] += s_red[c][w];
-            const double Fu = a.scal[0] / (a.u * a.u);  // internal flux unit in erg/s/cm^2
-            const int64_t k = a.perm[s];
-            a.J[out] = (float)(r[0] / (4.0 * kPi) * Fu + a.jsrc[k]);
-            a.F[3 * out] = r[1] * Fu;
-            a.F[3 * out + 1] = r[2] * Fu;
-            a.F[3 * out + 2] = r[3] * Fu;
+            const double Fu = A.scal[0] / (A.u * A.u);  // internal flux unit in erg/s/cm^2
+            const int64_t k = A.perm[s];
+            A.J[out] = (float)(r[0] / (4.0 * kPi) * Fu + A.jsrc[k]);
+            A.F[3 * out] = r[1] * Fu;
+            A.F[3 * out + 1] = r[2] * Fu;
+            A.F[3 * out + 2] = r[3] * Fu;
         }
         __syncthreads();
     }
@@ -549,19 +582,19 @@ treeray_status launch_persistent(treeray_ctx* c, K kern, size_t per_warp, int ma
     return TREERAY_OK;
 }
 
-template <int NPIX, bool THICK>
-treeray_status launch_t(treeray_ctx* c, const EvalArgs& a, cudaStream_t s) {
-    constexpr int WPT = 4;  // warps per target team
+template <int NPIX, bool THICK, int WPT>
+treeray_status launch_team(treeray_ctx* c, const EvalArgs& a, const EvalArgs* boxes,
+                           const int64_t* box_start, int nbox, int layout_lmax, cudaStream_t s) {
     constexpr int nq = THICK ? 6 : 2;
     EvalArgs b = a;
     // the team stack holds at most one batch of pushes (32 WPT groups) per level
-    b.stack_cap = 32 * WPT * (c->lmax + 1) + 64;
+    b.stack_cap = 32 * WPT * (layout_lmax + 1) + 64;
     const size_t smem = (size_t)nq * a.nbins * NPIX * 4 + (THICK ? NPIX * 8 : 0) + (size_t)b.stack_cap * 4 +
                         (size_t)WPT * (32 * 16 + kOwnerCap);
     int smem_optin = 0, sms = 0;
     TR_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
     TR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
-    if (smem + 1024 > (size_t)smem_optin) {
+    if (smem + 2048 > (size_t)smem_optin) {
         set_error("evaluate: the per-target ray tile (npix x nbins) exceeds shared memory");
         return TREERAY_EINVAL;
     }
@@ -576,21 +609,41 @@ treeray_status launch_t(treeray_ctx* c, const EvalArgs& a, cudaStream_t s) {
     int64_t blocks = (int64_t)per_sm * sms;
     if (blocks > a.n) blocks = a.n;
     TR_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), s));
-    kern<<<(int)blocks, WPT * 32, smem, s>>>(b);
+    kern<<<(int)blocks, WPT * 32, smem, s>>>(b, boxes, box_start, nbox);
     c->launches += 1;
     TR_CUDA(cudaGetLastError());
     return TREERAY_OK;
 }
 
-treeray_status dispatch_eval(treeray_ctx* c, const EvalArgs& a, cudaStream_t s) {
-    const bool thick = c->has_thick || c->force_thick;
+template <int NPIX, bool THICK>
+treeray_status launch_wpt(treeray_ctx* c, int wpt, const EvalArgs& a, const EvalArgs* boxes,
+                          const int64_t* box_start, int nbox, int layout_lmax, cudaStream_t s) {
+    switch (wpt) {
+        case 2: return launch_team<NPIX, THICK, 2>(c, a, boxes, box_start, nbox, layout_lmax, s);
+        case 8: return launch_team<NPIX, THICK, 8>(c, a, boxes, box_start, nbox, layout_lmax, s);
+        default: return launch_team<NPIX, THICK, 4>(c, a, boxes, box_start, nbox, layout_lmax, s);
+    }
+}
+
+treeray_status dispatch_team(treeray_ctx* c, bool thick, int wpt, const EvalArgs& a, const EvalArgs* boxes,
+                             const int64_t* box_start, int nbox, int layout_lmax, cudaStream_t s) {
     switch (c->p.npix) {
-        case 12: return thick ? launch_t<12, true>(c, a, s) : launch_t<12, false>(c, a, s);
-        case 48: return thick ? launch_t<48, true>(c, a, s) : launch_t<48, false>(c, a, s);
-        case 192: return thick ? launch_t<192, true>(c, a, s) : launch_t<192, false>(c, a, s);
+        case 12:
+            return thick ? launch_wpt<12, true>(c, wpt, a, boxes, box_start, nbox, layout_lmax, s)
+                         : launch_wpt<12, false>(c, wpt, a, boxes, box_start, nbox, layout_lmax, s);
+        case 48:
+            return thick ? launch_wpt<48, true>(c, wpt, a, boxes, box_start, nbox, layout_lmax, s)
+                         : launch_wpt<48, false>(c, wpt, a, boxes, box_start, nbox, layout_lmax, s);
+        case 192:
+            return thick ? launch_wpt<192, true>(c, wpt, a, boxes, box_start, nbox, layout_lmax, s)
+                         : launch_wpt<192, false>(c, wpt, a, boxes, box_start, nbox, layout_lmax, s);
     }
     set_error("evaluate: npix must be 12, 48 or 192");
     return TREERAY_EINVAL;
+}
+
+treeray_status dispatch_eval(treeray_ctx* c, const EvalArgs& a, cudaStream_t s) {
+    return dispatch_team(c, c->has_thick || c->force_thick, c->wpt, a, nullptr, nullptr, 1, c->lmax, s);
 }
 
 treeray_status dispatch_list(treeray_ctx* c, const EvalArgs& a, cudaStream_t s) {
@@ -666,4 +719,249 @@ treeray_status launch_walk_stats(treeray_ctx* c, const int32_t* targets, int64_t
     return dispatch_list(c, a, s);
 }
 
+
+namespace {
+__global__ void k_sample_targets(int32_t* t, int64_t n, int64_t N, int64_t step) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) t[i] = (int32_t)((i * step) % N);
+}
+int64_t gcd64(int64_t a, int64_t b) {
+    while (b) {
+        const int64_t t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+}  // namespace
+
+treeray_status autotune(treeray_ctx* c, int64_t n_sample, int* best, float* ms, cudaStream_t s) {
+    const int64_t N = c->nleaves;
+    const int64_t n = std::max<int64_t>(1, std::min(n_sample, N));
+    int64_t step = 1000003;
+    while (gcd64(step, N) != 1) step += 2;
+    int32_t* t = nullptr;
+    float* J = nullptr;
+    double* F = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    struct Free {
+        int32_t*& t;
+        float*& J;
+        double*& F;
+        cudaEvent_t& e0;
+        cudaEvent_t& e1;
+        ~Free() {
+            if (t) cudaFree(t);
+            if (J) cudaFree(J);
+            if (F) cudaFree(F);
+            if (e0) cudaEventDestroy(e0);
+            if (e1) cudaEventDestroy(e1);
+        }
+    } guard{t, J, F, e0, e1};
+    TR_CUDA(cudaMalloc(&t, sizeof(int32_t) * n));
+    TR_CUDA(cudaMalloc(&J, sizeof(float) * n));
+    TR_CUDA(cudaMalloc(&F, sizeof(double) * 3 * n));
+    TR_CUDA(cudaEventCreate(&e0));
+    TR_CUDA(cudaEventCreate(&e1));
+    k_sample_targets<<<(int)((n + 255) / 256), 256, 0, s>>>(t, n, N, step);
+    ++c->launches;
+    const int cand[3] = {2, 4, 8};
+    float bestt = 0.0f;
+    int bw = c->wpt;
+    for (int k = 0; k < 3; ++k) {
+        EvalArgs a = make_args(c, t, n);
+        a.J = J;
+        a.F = F;
+        treeray_status rc;
+        for (int rep = 0; rep < 2; ++rep) {  // the second launch is timed
+            if (rep == 1) TR_CUDA(cudaEventRecord(e0, s));
+            rc = dispatch_team(c, c->has_thick || c->force_thick, cand[k], a, nullptr, nullptr, 1, c->lmax, s);
+            if (rc != TREERAY_OK) return rc;
+        }
+        TR_CUDA(cudaEventRecord(e1, s));
+        TR_CUDA(cudaEventSynchronize(e1));
+        float t_ms = 0.0f;
+        TR_CUDA(cudaEventElapsedTime(&t_ms, e0, e1));
+        if (ms) ms[k] = t_ms;
+        if (k == 0 || t_ms < bestt) {
+            bestt = t_ms;
+            bw = cand[k];
+        }
+    }
+    c->wpt = bw;
+    if (best) *best = bw;
+    return TREERAY_OK;
+}
+
 }  // namespace tr
+
+// ----------------------------------------------------------------------- batches
+struct treeray_batch {
+    std::vector<treeray_t> ctx;
+    std::vector<tr::EvalArgs> desc;
+    std::vector<int64_t> start;
+    tr::EvalArgs* d_desc = nullptr;
+    int64_t* d_start = nullptr;
+    unsigned long long* d_queue = nullptr;
+    int max_lmax = 0;
+    bool thick = false;
+    bool uploaded = false;
+    cudaGraphExec_t graph = nullptr;
+    cudaStream_t gstream = nullptr;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+};
+
+using namespace tr;
+
+extern "C" {
+
+treeray_status treeray_batch_create(const treeray_t* ctxs, int n_boxes, treeray_batch_t* out) {
+    if (!ctxs || !out || n_boxes < 1) {
+        set_error("batch_create: contexts and n_boxes >= 1 required");
+        return TREERAY_EINVAL;
+    }
+    *out = nullptr;
+    const treeray_t c0 = ctxs[0];
+    for (int k = 0; k < n_boxes; ++k) {
+        const treeray_t c = ctxs[k];
+        if (!c || !c->built) {
+            set_error("batch_create: every context must hold a built tree");
+            return TREERAY_ENOTBUILT;
+        }
+        if (c->p.npix != c0->p.npix || c->p.nbins != c0->p.nbins || c->device != c0->device) {
+            set_error("batch_create: all boxes need the same npix, nbins and device");
+            return TREERAY_EINVAL;
+        }
+    }
+    treeray_batch* b = new (std::nothrow) treeray_batch();
+    if (!b) {
+        set_error("out of host memory");
+        return TREERAY_ENOMEM;
+    }
+    b->ctx.assign(ctxs, ctxs + n_boxes);
+    b->start.assign(n_boxes + 1, 0);
+    for (int k = 0; k < n_boxes; ++k) {
+        treeray_t c = ctxs[k];
+        EvalArgs a = make_args(c, nullptr, c->nleaves);
+        a.stack_cap = 32 * 4 * (c->lmax + 1) + 64;  // 4-warp teams
+        b->desc.push_back(a);
+        b->start[k + 1] = b->start[k] + c->nleaves;
+        b->max_lmax = std::max(b->max_lmax, c->lmax);
+        b->thick = b->thick || c->has_thick;
+    }
+    auto fail = [&](treeray_status rc) {
+        treeray_batch_destroy(b);
+        return rc;
+    };
+    if (cudaMalloc(&b->d_desc, sizeof(EvalArgs) * n_boxes) != cudaSuccess ||
+        cudaMalloc(&b->d_start, sizeof(int64_t) * (n_boxes + 1)) != cudaSuccess ||
+        cudaMalloc(&b->d_queue, sizeof(unsigned long long)) != cudaSuccess) {
+        set_error("batch_create: device allocation failed");
+        return fail(TREERAY_ENOMEM);
+    }
+    if (cudaMemcpy(b->d_start, b->start.data(), sizeof(int64_t) * (n_boxes + 1), cudaMemcpyHostToDevice) !=
+        cudaSuccess) {
+        set_error("batch_create: upload failed");
+        return fail(TREERAY_ECUDA);
+    }
+    *out = b;
+    return TREERAY_OK;
+}
+
+treeray_status treeray_batch_destroy(treeray_batch_t b) {
+    if (!b) return TREERAY_OK;
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->gstream) cudaStreamDestroy(b->gstream);
+    for (cudaEvent_t e : b->ev)
+        if (e) cudaEventDestroy(e);
+    if (b->d_desc) cudaFree(b->d_desc);
+    if (b->d_start) cudaFree(b->d_start);
+    if (b->d_queue) cudaFree(b->d_queue);
+    delete b;
+    return TREERAY_OK;
+}
+
+treeray_status treeray_batch_evaluate(treeray_batch_t b, float* const* J, double* const* F, int use_graph,
+                                      treeray_stream_t stream) {
+    if (!b || !J || !F) {
+        set_error("batch_evaluate: batch, J and F required");
+        return TREERAY_EINVAL;
+    }
+    const int nb = (int)b->ctx.size();
+    bool changed = !b->uploaded;
+    for (int k = 0; k < nb; ++k) {
+        if (!J[k] || !F[k]) {
+            set_error("batch_evaluate: every box needs J and F");
+            return TREERAY_EINVAL;
+        }
+        changed = changed || b->desc[k].J != J[k] || b->desc[k].F != F[k];
+        b->desc[k].J = J[k];
+        b->desc[k].F = F[k];
+    }
+    cudaStream_t us = (cudaStream_t)stream;
+    if (changed) {
+        if (b->graph) {
+            cudaGraphExecDestroy(b->graph);
+            b->graph = nullptr;
+        }
+        TR_CUDA(cudaMemcpyAsync(b->d_desc, b->desc.data(), sizeof(EvalArgs) * nb, cudaMemcpyHostToDevice, us));
+        TR_CUDA(cudaStreamSynchronize(us));  // the host descriptors may change on the next call
+        b->uploaded = true;
+    }
+    treeray_t c0 = b->ctx[0];
+    EvalArgs a = b->desc[0];
+    a.n = b->start[nb];
+    a.queue = b->d_queue;
+    a.targets = nullptr;
+    a.skip = nullptr;
+    if (!use_graph)
+        return dispatch_team(c0, b->thick, 4, a, b->d_desc, b->d_start, nb, b->max_lmax, us);
+    if (!b->gstream) TR_CUDA(cudaStreamCreateWithFlags(&b->gstream, cudaStreamNonBlocking));
+    for (cudaEvent_t& e : b->ev)
+        if (!e) TR_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    if (!b->graph) {
+        cudaGraph_t g = nullptr;
+        TR_CUDA(cudaStreamBeginCapture(b->gstream, cudaStreamCaptureModeThreadLocal));
+        treeray_status rc = dispatch_team(c0, b->thick, 4, a, b->d_desc, b->d_start, nb, b->max_lmax, b->gstream);
+        cudaError_t ce = cudaStreamEndCapture(b->gstream, &g);
+        if (rc != TREERAY_OK) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        TR_CUDA(ce);
+        ce = cudaGraphInstantiate(&b->graph, g, 0);
+        cudaGraphDestroy(g);
+        TR_CUDA(ce);
+    }
+    TR_CUDA(cudaEventRecord(b->ev[0], us));
+    TR_CUDA(cudaStreamWaitEvent(b->gstream, b->ev[0], 0));
+    TR_CUDA(cudaGraphLaunch(b->graph, b->gstream));
+    c0->launches += 1;
+    TR_CUDA(cudaEventRecord(b->ev[1], b->gstream));
+    TR_CUDA(cudaStreamWaitEvent(us, b->ev[1], 0));
+    return TREERAY_OK;
+}
+
+treeray_status treeray_set_warps_per_target(treeray_t c, int wpt) {
+    if (!c || (wpt != 2 && wpt != 4 && wpt != 8)) {
+        set_error("set_warps_per_target: wpt must be 2, 4 or 8");
+        return TREERAY_EINVAL;
+    }
+    c->wpt = wpt;
+    return TREERAY_OK;
+}
+
+treeray_status treeray_autotune(treeray_t c, int64_t n_sample, int* best_wpt, float* ms,
+                                treeray_stream_t stream) {
+    if (!c || !c->built) {
+        set_error("autotune: no tree");
+        return c ? TREERAY_ENOTBUILT : TREERAY_EINVAL;
+    }
+    if (n_sample < 1) {
+        set_error("autotune: n_sample >= 1");
+        return TREERAY_EINVAL;
+    }
+    return autotune(c, n_sample, best_wpt, ms, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -125,6 +125,7 @@ struct treeray_ctx {
     cudaStream_t fp_stream = nullptr;
     cudaEvent_t fp_ev[2] = {nullptr, nullptr};
     int64_t launches = 0;  // kernels launched by this context
+    int wpt = 4;           // warps per target team of the evaluate kernel (autotuned)
     // table cache key
     int tab_lmax = -1;
     bool tab_amr = false;
