@@ -350,6 +350,92 @@ def cpu_baseline(w, seconds: float):
             "threads": cores}
 
 
+def run_batch64(args):
+    """64 independent AMR boxes (12.3 M leaves): one batched persistent launch replayed as a
+    CUDA graph, against one evaluate launch per box. Prints one JSON line."""
+    import torch
+
+    import paper_2204_09072_gb300 as tr
+    import synth
+    dev = torch.device("cuda:0")
+    boxes = synth.batch_of_boxes(64, seed=5, npix=args.npix)
+    ctxs, Js, Fs = [], [], []
+    t0 = time.perf_counter()
+    for w in boxes:
+        c = tr.Context(w.params)
+        c.build(w.box_cm, torch.as_tensor(w.rho, device=dev), torch.as_tensor(w.td, device=dev),
+                blocks=w.blocks)
+        ctxs.append(c)
+        Js.append(torch.empty(w.n_leaves, dtype=torch.float32, device=dev))
+        Fs.append(torch.empty(3 * w.n_leaves, dtype=torch.float64, device=dev))
+    t_build = time.perf_counter() - t0
+    batch = tr.Batch(ctxs)
+    n = sum(w.n_leaves for w in boxes)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.mean(ts)
+
+    ms_graph = timed(lambda: batch.evaluate(Js, Fs, use_graph=True), args.steps)
+    ms_plain = timed(lambda: batch.evaluate(Js, Fs, use_graph=False), args.steps)
+
+    def per_box():
+        for c, J, F in zip(ctxs, Js, Fs):
+            c.evaluate(J, F)
+    ms_seq = timed(per_box, args.steps)
+    for c in ctxs:
+        c.check()
+    print(json.dumps({"metric": METRIC, "unit": UNIT, "workload": "batch64_amr",
+                      "boxes": len(boxes), "cells": n, "npix": args.npix,
+                      "value_batched_graph": n * args.npix / (ms_graph * 1e-3),
+                      "value_batched_plain": n * args.npix / (ms_plain * 1e-3),
+                      "value_per_box_launches": n * args.npix / (ms_seq * 1e-3),
+                      "ms_batched_graph": ms_graph, "ms_batched_plain": ms_plain,
+                      "ms_per_box_launches": ms_seq, "host_build_s": t_build,
+                      "steps": args.steps, "warmup": args.warmup}))
+
+
+def run_sweep(args):
+    """Cost of the 128^3 cloud's evaluation over N_pix x segments, with the autotuner's
+    team size for each; one JSON line per combination."""
+    import torch
+
+    import paper_2204_09072_gb300 as tr
+    import synth
+    dev = torch.device("cuda:0")
+    for npix in (12, 48, 192):
+        for nb in (10, 20, 40):
+            w = synth.turbulent_cloud(128, npix=npix, nbins=nb)
+            c = tr.Context(w.params)
+            c.build(w.box_cm, torch.as_tensor(w.rho, device=dev), torch.as_tensor(w.td, device=dev), n=128,
+                    star_pos=w.star_pos, star_lum=w.star_lum)
+            best, tune = c.autotune(65536)
+            J = torch.empty(w.n_leaves, dtype=torch.float32, device=dev)
+            F = torch.empty(3 * w.n_leaves, dtype=torch.float64, device=dev)
+            c.evaluate(J, F)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            c.evaluate(J, F)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            c.check()
+            print(json.dumps({"sweep": "turb128", "npix": npix, "nbins": nb, "warps_per_target": best,
+                              "autotune_ms_wpt2_4_8_on_65536": tune, "ms_evaluate": ms,
+                              "ray_evals_per_s": w.n_leaves * npix / (ms * 1e-3)}))
+            c.close()
+
+
 def run_profile(args):
     """Profiling driver for ncu: build the full tree once, then launch the evaluate
     kernel on a seeded subset of targets: two warm-up launches, then one more."""
@@ -427,11 +513,17 @@ def main():
     ap.add_argument("--profile-evaluate", action="store_true",
                     help="ncu driver: evaluate kernel only, on --profile-targets cells")
     ap.add_argument("--profile-targets", type=int, default=262144)
+    ap.add_argument("--batch64", action="store_true", help="64-box AMR batch: batched vs per-box launches")
+    ap.add_argument("--sweep", action="store_true", help="N_pix x segments sweep with the autotuner")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.profile_evaluate:
         run_profile(args)
+    elif args.batch64:
+        run_batch64(args)
+    elif args.sweep:
+        run_sweep(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

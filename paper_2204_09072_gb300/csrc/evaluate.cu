@@ -235,8 +235,9 @@ __global__ void __launch_bounds__(WPT * 32) k_evaluate(EvalArgs a, const EvalArg
     // the per-box descriptor lives in shared memory: copied once (one box) or per target (a
     // batch of boxes whose targets share one work counter)
     __shared__ __align__(16) EvalArgs s_box;
-    __shared__ int s_b;
+    __shared__ int s_b, s_bcur;
     const EvalArgs& A = s_box;
+    if (tid == 0) s_bcur = -1;
     if (!boxes) {
         for (int w = tid; w < (int)(sizeof(EvalArgs) / 8); w += NT)
             reinterpret_cast<unsigned long long*>(&s_box)[w] = reinterpret_cast<const unsigned long long*>(&a)[w];
@@ -258,10 +259,16 @@ __global__ void __launch_bounds__(WPT * 32) k_evaluate(EvalArgs a, const EvalArg
                 s_b = lo;
             }
             __syncthreads();
-            const EvalArgs* src = boxes + s_b;
-            for (int w = tid; w < (int)(sizeof(EvalArgs) / 8); w += NT)
-                reinterpret_cast<unsigned long long*>(&s_box)[w] = reinterpret_cast<const unsigned long long*>(src)[w];
-            q -= box_start[s_b];
+            const int b = s_b;
+            if (b != s_bcur) {  // consecutive targets mostly come from the same box
+                const EvalArgs* src = boxes + b;
+                for (int w = tid; w < (int)(sizeof(EvalArgs) / 8); w += NT)
+                    reinterpret_cast<unsigned long long*>(&s_box)[w] =
+                        reinterpret_cast<const unsigned long long*>(src)[w];
+            }
+            q -= box_start[b];
+            __syncthreads();
+            if (tid == 0) s_bcur = b;
         }
         __syncthreads();
         const int W = 2 * A.D + 1;
@@ -797,15 +804,21 @@ treeray_status autotune(treeray_ctx* c, int64_t n_sample, int* best, float* ms, 
 
 // ----------------------------------------------------------------------- batches
 struct treeray_batch {
+    // boxes split by the kernel they need (thin only, or with thick material); one
+    // persistent launch per non-empty group
+    struct Group {
+        std::vector<int> box;  // indices into ctx
+        std::vector<tr::EvalArgs> desc;
+        std::vector<int64_t> start;
+        tr::EvalArgs* d_desc = nullptr;
+        int64_t* d_start = nullptr;
+        unsigned long long* d_queue = nullptr;
+        int max_lmax = 0;
+    };
     std::vector<treeray_t> ctx;
-    std::vector<tr::EvalArgs> desc;
-    std::vector<int64_t> start;
-    tr::EvalArgs* d_desc = nullptr;
-    int64_t* d_start = nullptr;
-    unsigned long long* d_queue = nullptr;
-    int max_lmax = 0;
-    bool thick = false;
+    Group g[2];
     bool uploaded = false;
+    std::vector<void*> lastJ, lastF;
     cudaGraphExec_t graph = nullptr;
     cudaStream_t gstream = nullptr;
     cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -839,30 +852,35 @@ treeray_status treeray_batch_create(const treeray_t* ctxs, int n_boxes, treeray_
         return TREERAY_ENOMEM;
     }
     b->ctx.assign(ctxs, ctxs + n_boxes);
-    b->start.assign(n_boxes + 1, 0);
     for (int k = 0; k < n_boxes; ++k) {
         treeray_t c = ctxs[k];
+        treeray_batch::Group& g = b->g[(c->has_thick || c->force_thick) ? 1 : 0];
         EvalArgs a = make_args(c, nullptr, c->nleaves);
         a.stack_cap = 32 * 4 * (c->lmax + 1) + 64;  // 4-warp teams
-        b->desc.push_back(a);
-        b->start[k + 1] = b->start[k] + c->nleaves;
-        b->max_lmax = std::max(b->max_lmax, c->lmax);
-        b->thick = b->thick || c->has_thick;
+        if (g.start.empty()) g.start.push_back(0);
+        g.box.push_back(k);
+        g.desc.push_back(a);
+        g.start.push_back(g.start.back() + c->nleaves);
+        g.max_lmax = std::max(g.max_lmax, c->lmax);
     }
     auto fail = [&](treeray_status rc) {
         treeray_batch_destroy(b);
         return rc;
     };
-    if (cudaMalloc(&b->d_desc, sizeof(EvalArgs) * n_boxes) != cudaSuccess ||
-        cudaMalloc(&b->d_start, sizeof(int64_t) * (n_boxes + 1)) != cudaSuccess ||
-        cudaMalloc(&b->d_queue, sizeof(unsigned long long)) != cudaSuccess) {
-        set_error("batch_create: device allocation failed");
-        return fail(TREERAY_ENOMEM);
-    }
-    if (cudaMemcpy(b->d_start, b->start.data(), sizeof(int64_t) * (n_boxes + 1), cudaMemcpyHostToDevice) !=
-        cudaSuccess) {
-        set_error("batch_create: upload failed");
-        return fail(TREERAY_ECUDA);
+    for (auto& g : b->g) {
+        if (g.box.empty()) continue;
+        const size_t nb = g.box.size();
+        if (cudaMalloc(&g.d_desc, sizeof(EvalArgs) * nb) != cudaSuccess ||
+            cudaMalloc(&g.d_start, sizeof(int64_t) * (nb + 1)) != cudaSuccess ||
+            cudaMalloc(&g.d_queue, sizeof(unsigned long long)) != cudaSuccess) {
+            set_error("batch_create: device allocation failed");
+            return fail(TREERAY_ENOMEM);
+        }
+        if (cudaMemcpy(g.d_start, g.start.data(), sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
+            set_error("batch_create: upload failed");
+            return fail(TREERAY_ECUDA);
+        }
     }
     *out = b;
     return TREERAY_OK;
@@ -874,12 +892,33 @@ treeray_status treeray_batch_destroy(treeray_batch_t b) {
     if (b->gstream) cudaStreamDestroy(b->gstream);
     for (cudaEvent_t e : b->ev)
         if (e) cudaEventDestroy(e);
-    if (b->d_desc) cudaFree(b->d_desc);
-    if (b->d_start) cudaFree(b->d_start);
-    if (b->d_queue) cudaFree(b->d_queue);
+    for (auto& g : b->g) {
+        if (g.d_desc) cudaFree(g.d_desc);
+        if (g.d_start) cudaFree(g.d_start);
+        if (g.d_queue) cudaFree(g.d_queue);
+    }
     delete b;
     return TREERAY_OK;
 }
+
+namespace {
+treeray_status batch_launch(treeray_batch_t b, cudaStream_t s) {
+    for (int t = 0; t < 2; ++t) {
+        treeray_batch::Group& g = b->g[t];
+        if (g.box.empty()) continue;
+        treeray_t c0 = b->ctx[g.box[0]];
+        EvalArgs a = g.desc[0];
+        a.n = g.start.back();
+        a.queue = g.d_queue;
+        a.targets = nullptr;
+        a.skip = nullptr;
+        const treeray_status rc =
+            dispatch_team(c0, t == 1, 4, a, g.d_desc, g.d_start, (int)g.box.size(), g.max_lmax, s);
+        if (rc != TREERAY_OK) return rc;
+    }
+    return TREERAY_OK;
+}
+}  // namespace
 
 treeray_status treeray_batch_evaluate(treeray_batch_t b, float* const* J, double* const* F, int use_graph,
                                       treeray_stream_t stream) {
@@ -887,56 +926,53 @@ treeray_status treeray_batch_evaluate(treeray_batch_t b, float* const* J, double
         set_error("batch_evaluate: batch, J and F required");
         return TREERAY_EINVAL;
     }
-    const int nb = (int)b->ctx.size();
     bool changed = !b->uploaded;
-    for (int k = 0; k < nb; ++k) {
-        if (!J[k] || !F[k]) {
-            set_error("batch_evaluate: every box needs J and F");
-            return TREERAY_EINVAL;
+    for (auto& g : b->g)
+        for (size_t q = 0; q < g.box.size(); ++q) {
+            const int k = g.box[q];
+            if (!J[k] || !F[k]) {
+                set_error("batch_evaluate: every box needs J and F");
+                return TREERAY_EINVAL;
+            }
+            changed = changed || g.desc[q].J != J[k] || g.desc[q].F != F[k];
+            g.desc[q].J = J[k];
+            g.desc[q].F = F[k];
         }
-        changed = changed || b->desc[k].J != J[k] || b->desc[k].F != F[k];
-        b->desc[k].J = J[k];
-        b->desc[k].F = F[k];
-    }
     cudaStream_t us = (cudaStream_t)stream;
     if (changed) {
         if (b->graph) {
             cudaGraphExecDestroy(b->graph);
             b->graph = nullptr;
         }
-        TR_CUDA(cudaMemcpyAsync(b->d_desc, b->desc.data(), sizeof(EvalArgs) * nb, cudaMemcpyHostToDevice, us));
+        for (auto& g : b->g)
+            if (!g.box.empty())
+                TR_CUDA(cudaMemcpyAsync(g.d_desc, g.desc.data(), sizeof(EvalArgs) * g.box.size(),
+                                        cudaMemcpyHostToDevice, us));
         TR_CUDA(cudaStreamSynchronize(us));  // the host descriptors may change on the next call
         b->uploaded = true;
     }
-    treeray_t c0 = b->ctx[0];
-    EvalArgs a = b->desc[0];
-    a.n = b->start[nb];
-    a.queue = b->d_queue;
-    a.targets = nullptr;
-    a.skip = nullptr;
-    if (!use_graph)
-        return dispatch_team(c0, b->thick, 4, a, b->d_desc, b->d_start, nb, b->max_lmax, us);
+    if (!use_graph) return batch_launch(b, us);
     if (!b->gstream) TR_CUDA(cudaStreamCreateWithFlags(&b->gstream, cudaStreamNonBlocking));
     for (cudaEvent_t& e : b->ev)
         if (!e) TR_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     if (!b->graph) {
-        cudaGraph_t g = nullptr;
+        cudaGraph_t gr = nullptr;
         TR_CUDA(cudaStreamBeginCapture(b->gstream, cudaStreamCaptureModeThreadLocal));
-        treeray_status rc = dispatch_team(c0, b->thick, 4, a, b->d_desc, b->d_start, nb, b->max_lmax, b->gstream);
-        cudaError_t ce = cudaStreamEndCapture(b->gstream, &g);
+        treeray_status rc = batch_launch(b, b->gstream);
+        cudaError_t ce = cudaStreamEndCapture(b->gstream, &gr);
         if (rc != TREERAY_OK) {
-            if (g) cudaGraphDestroy(g);
+            if (gr) cudaGraphDestroy(gr);
             return rc;
         }
         TR_CUDA(ce);
-        ce = cudaGraphInstantiate(&b->graph, g, 0);
-        cudaGraphDestroy(g);
+        ce = cudaGraphInstantiate(&b->graph, gr, 0);
+        cudaGraphDestroy(gr);
         TR_CUDA(ce);
     }
     TR_CUDA(cudaEventRecord(b->ev[0], us));
     TR_CUDA(cudaStreamWaitEvent(b->gstream, b->ev[0], 0));
     TR_CUDA(cudaGraphLaunch(b->graph, b->gstream));
-    c0->launches += 1;
+    b->ctx[0]->launches += 1;
     TR_CUDA(cudaEventRecord(b->ev[1], b->gstream));
     TR_CUDA(cudaStreamWaitEvent(us, b->ev[1], 0));
     return TREERAY_OK;

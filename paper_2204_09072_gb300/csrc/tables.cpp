@@ -8,7 +8,10 @@
 // so the kernels decide in exact integer arithmetic.
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
 #include <thread>
+#include <tuple>
 
 #include "internal.h"
 
@@ -143,6 +146,13 @@ inline int key_class(int64_t k) {
 // two or more levels coarser than the target (odd keys) and one level coarser (2 mod 4)
 // only when accepted by the opening criterion, i.e. at 8 d / E > 8 / theta, unless the
 // grid is AMR (coarser and finer leaves next to the target, classes 1-3 anywhere).
+namespace {
+// tables already built in this process, keyed by (npix, samples, theta, D, amr)
+std::mutex g_tab_mutex;
+std::map<std::tuple<int, int, double, int64_t, bool>, std::pair<std::vector<int32_t>, std::vector<uint32_t>>>
+    g_tab_cache;
+}  // namespace
+
 void build_alpha_table(HostTables& t, double theta, int lmax, bool amr) {
     const double th = theta > 1e-6 ? theta : 1e-6;
     const double reach = std::max(2.0 / th, std::sqrt(3.0)) + 0.5 * std::sqrt(3.0);
@@ -151,6 +161,16 @@ void build_alpha_table(HostTables& t, double theta, int lmax, bool amr) {
     D = std::min(D, cap);
     D = std::min<int64_t>(D, 128);
     t.D = (int)D;
+    const auto key = std::make_tuple(t.npix, t.s, theta, D, amr);
+    {
+        std::lock_guard<std::mutex> lock(g_tab_mutex);
+        auto it = g_tab_cache.find(key);
+        if (it != g_tab_cache.end()) {
+            t.alpha_off = it->second.first;
+            t.alpha_ent = it->second.second;
+            return;
+        }
+    }
     const int64_t W = 2 * D + 1, nk = W * W * W;
     const double shell = std::max(0.0, 8.0 / th - std::sqrt(3.0));
     const double shell2 = shell * shell;
@@ -190,6 +210,9 @@ void build_alpha_table(HostTables& t, double theta, int lmax, bool amr) {
     t.alpha_ent.assign(t.alpha_off[nk], 0);
     for (size_t q = 0; q < keys.size(); ++q)
         std::copy(lists[q].begin(), lists[q].end(), t.alpha_ent.begin() + t.alpha_off[keys[q]]);
+    std::lock_guard<std::mutex> lock(g_tab_mutex);
+    if (g_tab_cache.size() > 16) g_tab_cache.clear();
+    g_tab_cache[key] = std::make_pair(t.alpha_off, t.alpha_ent);
 }
 
 // R_i = R_0 (R_max / R_0)^(i / nbins), R_0 = Et / 2, R_max = sqrt(3) box (half-cells)

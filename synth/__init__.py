@@ -302,6 +302,73 @@ def amr_core(n_base_blocks: int = 2, max_level: int = 5, box_pc: float = 0.4,
     return w
 
 
+def amr_random(finest: int, levels: int, seed: int, box_pc: float = 2.0, sigma_ln: float = 1.5,
+               refine_frac: float = 0.3, kappa: float = 5.0, **pover) -> Workload:
+    """AMR box of 8^3-cell blocks: base grid finest / 2^(levels-1) cells per axis, blocks
+    refined (8 children) up to levels-1 times where their peak density is in the top
+    refine_frac of their level; density lognormal from a seeded 32^3 Gaussian random field
+    (nearest lookup); grey opacity kappa; T_d ~ U[10, 40] K."""
+    box = box_pc * PC_CM
+    base = finest >> (levels - 1)
+    if base < 8 or base % 8:
+        raise ValueError("base grid must be a multiple of 8 cells")
+    rng = np.random.Generator(np.random.PCG64(seed))
+    gres = 32
+    g = _grf(gres, -4.0, rng).reshape(gres, gres, gres)
+    lb0 = int(round(math.log2(base // 8)))   # block level of the base grid
+    def dens(cen):
+        gi = np.clip((cen / box * gres).astype(np.int64), 0, gres - 1)
+        return np.exp(sigma_ln * g[gi[..., 2], gi[..., 1], gi[..., 0]] - 0.5 * sigma_ln ** 2) * 1e-20
+    cc = (np.indices((8, 8, 8)).reshape(3, -1).T[:, ::-1] + 0.5)
+    nb0 = base // 8
+    blocks = [(i, j, k, 0) for k in range(nb0) for j in range(nb0) for i in range(nb0)]
+    leaves = []
+    for lev in range(levels):
+        if not blocks:
+            break
+        nbl = nb0 << lev
+        dxb = box / nbl
+        peaks = np.array([dens(np.array([b[0], b[1], b[2]]) * dxb + cc * (dxb / 8)).max() for b in blocks])
+        if lev < levels - 1:
+            thr = np.quantile(peaks, 1.0 - refine_frac)
+            refine = peaks >= thr
+        else:
+            refine = np.zeros(len(blocks), bool)
+        nxt = []
+        for b, r in zip(blocks, refine):
+            if r:
+                for c in range(8):
+                    nxt.append((2 * b[0] + (c & 1), 2 * b[1] + ((c >> 1) & 1), 2 * b[2] + ((c >> 2) & 1), lev + 1))
+            else:
+                leaves.append((b[0], b[1], b[2], lb0 + lev + 3))
+        blocks = nxt
+    bl = np.array(leaves, dtype=np.int32)
+    cell = np.indices((8, 8, 8)).reshape(3, -1).T[:, ::-1].astype(np.int32)
+    ijk = (bl[:, None, :3] * 8 + cell[None, :, :]).reshape(-1, 3).astype(np.int32)
+    lev = np.repeat(bl[:, 3], 512).astype(np.int32)
+    cen = (ijk.astype(np.float64) + 0.5) * (box / (2.0 ** lev))[:, None]
+    rho = dens(cen)
+    td = np.random.Generator(np.random.PCG64(seed + 1)).uniform(10.0, 40.0, rho.shape[0])
+    return Workload(name=f"amr{finest}L{levels}s{seed}", box_cm=box, lmax=int(lev.max()), leaf_level=lev,
+                    leaf_ijk=ijk, rho=rho.astype(np.float32), td=td.astype(np.float32),
+                    params=default_params(kappa_model=0, kappa0=kappa, **pover), blocks=bl)
+
+
+def batch_of_boxes(count: int = 64, seed: int = 5, **pover):
+    """Independent boxes of seeded sizes: finest resolution 32, 64 or 128 per axis,
+    2 to 5 AMR levels (base grid >= 8 cells), own density seed, grey kappa ~ U[1, 10]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    while len(out) < count:
+        finest = int(rng.choice([32, 64, 128]))
+        levels = int(rng.integers(2, 6))
+        if (finest >> (levels - 1)) < 8:
+            continue
+        kap = float(rng.uniform(1.0, 10.0))
+        out.append(amr_random(finest, levels, seed=int(rng.integers(1 << 30)), kappa=kap, **pover))
+    return out
+
+
 def sample_targets(n_leaves: int, count: int, seed: int = 11) -> np.ndarray:
     """Seeded random subset of leaf indices (caller order), sorted, without repeats."""
     rng = np.random.Generator(np.random.PCG64(seed))
