@@ -220,6 +220,63 @@ treeray_status treeray_batch_destroy(treeray_batch_t batch);
 treeray_status treeray_batch_evaluate(treeray_batch_t batch, float* const* J, double* const* F,
                                       int use_graph, treeray_stream_t stream);
 
+/*
+ * Learned warm start of the fixed point. The paper has no learned component; a small
+ * network predicts log10 T_d per cell from 6 features, and the fixed point still decides
+ * the result (treeray_fixed_point from the predicted temperatures).
+ *
+ * Features (treeray_features), per leaf, 6 floats, row-major X[N][6]:
+ *   log10 rho, log10 T_gas, log10(mean over rays of the ray optical depth + 1e-6),
+ *   log10(ionising photon flux + 1), log10(smallest ray optical depth + 1e-6),
+ *   log10(unattenuated stellar J + 1e-30), J_* = sum_s L_s / (16 pi^2 r_s^2).
+ * treeray_features runs one ray evaluation of the current tree (J, F as treeray_evaluate,
+ * plus tau_mean, tau_min: device float[N]) and then fills X (device float[6N]).
+ * phi: device float[N] ionising photon flux or NULL (zero).
+ */
+treeray_status treeray_features(treeray_t ctx, const float* Tgas, const float* phi, float* X, float* J,
+                                double* F, float* tau_mean, float* tau_min, treeray_stream_t stream);
+
+/*
+ * The network: 6 -> 64 -> 64 -> 1 with SiLU activations; FP32 master weights, BF16 weights
+ * and BF16-rounded layer inputs multiplied with FP32 accumulation. Parameters are a flat
+ * float[4673]: W1[64][6], b1[64], W2[64][64], b2[64], W3[64], b3[1]. The normalisation
+ * norm[14]: feature means [0..5], feature std [6..11], target mean [12], target std [13];
+ * the network maps normalised features to the normalised target log10 T_d.
+ */
+typedef struct treeray_mlp* treeray_mlp_t;
+/* Glorot-uniform weights from seed (host generator), zero biases, identity normalisation. */
+treeray_status treeray_mlp_create(uint64_t seed, treeray_mlp_t* out);
+treeray_status treeray_mlp_destroy(treeray_mlp_t mlp);
+/* Host float[4673] parameters and/or float[14] normalisation (either may be NULL); setting
+ * parameters resets the optimiser state. get copies them out. Synchronous. */
+treeray_status treeray_mlp_set_params(treeray_mlp_t mlp, const float* params, const float* norm);
+treeray_status treeray_mlp_get_params(treeray_mlp_t mlp, float* params, float* norm);
+/* Normalisation from data: column means and standard deviations of X (device float[6n])
+ * and y (device float[n], log10 T_d). */
+treeray_status treeray_mlp_fit_normalization(treeray_mlp_t mlp, const float* X, const float* y, int64_t n,
+                                             treeray_stream_t stream);
+/*
+ * Adam training (beta 0.9 / 0.999, eps 1e-8) on the mean-square error of the normalised
+ * target: `steps` minibatches of `batch` samples drawn with replacement by a counter-based
+ * hash of (seed, step, slot) (splitmix64); loss_history host float[steps] (mean batch loss
+ * before each update) or NULL. X device float[6n], y device float[n]. Synchronous when
+ * loss_history is given.
+ */
+treeray_status treeray_mlp_train(treeray_mlp_t mlp, const float* X, const float* y, int64_t n, int batch,
+                                 int steps, float lr, uint64_t seed, float* loss_history,
+                                 treeray_stream_t stream);
+/* Gradient of the mean loss over all n samples (in order) with respect to the 4673
+ * parameters, to host float[4673]; host *loss the mean loss. Synchronous. */
+treeray_status treeray_mlp_grad(treeray_mlp_t mlp, const float* X, const float* y, int64_t n, float* grad,
+                                float* loss, treeray_stream_t stream);
+/* Predicted log10 T_d for n feature rows (tensor cores, mma m16n8k16 BF16 -> FP32).
+ * X device float[6n], y device float[n]. */
+treeray_status treeray_mlp_infer(treeray_mlp_t mlp, const float* X, int64_t n, float* y,
+                                 treeray_stream_t stream);
+/* Td (device float[N]) = max(2.7 K, 10^prediction) for the leaves' features X (float[6N]). */
+treeray_status treeray_warm_start(treeray_t ctx, treeray_mlp_t mlp, const float* X, float* Td,
+                                  treeray_stream_t stream);
+
 /* Synchronize the stream and report errors recorded by kernels since the last check
  * (TREERAY_ETIMEOUT for a bounded loop that ran out, TREERAY_ECUDA for CUDA errors). */
 treeray_status treeray_check(treeray_t ctx, treeray_stream_t stream);

@@ -14,7 +14,7 @@ import os
 from .build_lib import OUT as LIB_PATH
 from .build_lib import build as build_library
 
-__all__ = ["Params", "Grid", "Context", "Batch", "TreeRayError", "lib", "alpha_counts_host",
+__all__ = ["Params", "Grid", "Context", "Batch", "MLP", "TreeRayError", "lib", "alpha_counts_host",
            "build_library", "LIB_PATH", "STATUS"]
 
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTBUILT", 5: "ETIMEOUT",
@@ -80,6 +80,16 @@ def lib():
     L.treeray_batch_create.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(vp)]
     L.treeray_batch_destroy.argtypes = [vp]
     L.treeray_batch_evaluate.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.c_int, vp]
+    L.treeray_features.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.treeray_mlp_create.argtypes = [C.c_uint64, C.POINTER(vp)]
+    L.treeray_mlp_destroy.argtypes = [vp]
+    L.treeray_mlp_set_params.argtypes = [vp, vp, vp]
+    L.treeray_mlp_get_params.argtypes = [vp, vp, vp]
+    L.treeray_mlp_fit_normalization.argtypes = [vp, vp, vp, i64, vp]
+    L.treeray_mlp_train.argtypes = [vp, vp, vp, i64, C.c_int, C.c_int, C.c_float, C.c_uint64, vp, vp]
+    L.treeray_mlp_grad.argtypes = [vp, vp, vp, i64, vp, C.POINTER(C.c_float), vp]
+    L.treeray_mlp_infer.argtypes = [vp, vp, i64, vp, vp]
+    L.treeray_warm_start.argtypes = [vp, vp, vp, vp, vp]
     L.treeray_morton_order_noalloc.argtypes = [C.POINTER(Grid), vp, vp, vp]
     L.treeray_kernel_launches.argtypes = [vp]
     L.treeray_kernel_launches.restype = i64
@@ -90,7 +100,10 @@ def lib():
               "treeray_alpha_counts_host", "treeray_walk_stats", "treeray_morton_order_noalloc",
               "treeray_refresh", "treeray_fixed_point", "treeray_autotune",
               "treeray_set_warps_per_target", "treeray_batch_create", "treeray_batch_destroy",
-              "treeray_batch_evaluate"):
+              "treeray_batch_evaluate", "treeray_features", "treeray_mlp_create",
+              "treeray_mlp_destroy", "treeray_mlp_set_params", "treeray_mlp_get_params",
+              "treeray_mlp_fit_normalization", "treeray_mlp_train", "treeray_mlp_grad",
+              "treeray_mlp_infer", "treeray_warm_start"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -251,6 +264,30 @@ class Context:
     def set_warps_per_target(self, wpt: int):
         _raise(lib().treeray_set_warps_per_target(self.h, int(wpt)))
 
+    # -- C: treeray_features
+    def features(self, Tgas, phi=None, stream=None):
+        """One evaluation with ray optical depths, then the 6 warm-start features per leaf.
+        Returns (X [N, 6], J [N], F [3N], tau_mean [N], tau_min [N]) as CUDA tensors."""
+        import torch
+        n = self.leaf_count
+        d = Tgas.device
+        X = torch.empty(n * 6, dtype=torch.float32, device=d)
+        J = torch.empty(n, dtype=torch.float32, device=d)
+        F = torch.empty(3 * n, dtype=torch.float64, device=d)
+        tm = torch.empty(n, dtype=torch.float32, device=d)
+        tn = torch.empty(n, dtype=torch.float32, device=d)
+        f32 = torch.float32
+        _raise(lib().treeray_features(self.h, _dev(Tgas, f32, "Tgas"), _dev(phi, f32, "phi", True),
+                                      _dev(X, f32, "X"), _dev(J, f32, "J"), _dev(F, torch.float64, "F"),
+                                      _dev(tm, f32, "tau_mean"), _dev(tn, f32, "tau_min"), _stream(stream)))
+        return X.view(n, 6), J, F, tm, tn
+
+    # -- C: treeray_warm_start
+    def warm_start(self, mlp, X, Td, stream=None):
+        import torch
+        _raise(lib().treeray_warm_start(self.h, mlp.h, _dev(X, torch.float32, "X"),
+                                        _dev(Td, torch.float32, "Td"), _stream(stream)))
+
     # -- C: treeray_check
     def check(self, stream=None):
         _raise(lib().treeray_check(self.h, _stream(stream)))
@@ -342,3 +379,72 @@ class Batch:
         jp = (C.c_void_p * n)(*[_dev(j, torch.float32, "J").value for j in Js])
         fp = (C.c_void_p * n)(*[_dev(f, torch.float64, "F").value for f in Fs])
         _raise(lib().treeray_batch_evaluate(self.h, jp, fp, int(bool(use_graph)), _stream(stream)))
+
+
+class MLP:
+    """C: treeray_mlp_t. The warm-start network (6 -> 64 -> 64 -> 1, SiLU, BF16/FP32)."""
+
+    N_PARAMS = 4673
+
+    def __init__(self, seed: int = 1):
+        h = C.c_void_p()
+        _raise(lib().treeray_mlp_create(C.c_uint64(seed), C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().treeray_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self):
+        import numpy as np
+        p = np.zeros(self.N_PARAMS, np.float32)
+        nrm = np.zeros(14, np.float32)
+        _raise(lib().treeray_mlp_get_params(self.h, C.c_void_p(p.ctypes.data), C.c_void_p(nrm.ctypes.data)))
+        return p, nrm
+
+    def set_params(self, params=None, norm=None):
+        import numpy as np
+        p = None if params is None else np.ascontiguousarray(params, np.float32)
+        nrm = None if norm is None else np.ascontiguousarray(norm, np.float32)
+        _raise(lib().treeray_mlp_set_params(self.h, None if p is None else C.c_void_p(p.ctypes.data),
+                                            None if nrm is None else C.c_void_p(nrm.ctypes.data)))
+
+    def fit_normalization(self, X, y, stream=None):
+        import torch
+        n = y.numel()
+        _raise(lib().treeray_mlp_fit_normalization(self.h, _dev(X, torch.float32, "X"),
+                                                   _dev(y, torch.float32, "y"), n, _stream(stream)))
+
+    def train(self, X, y, steps: int, batch: int = 4096, lr: float = 1e-3, seed: int = 1, stream=None):
+        import numpy as np
+        import torch
+        n = y.numel()
+        hist = np.zeros(max(steps, 1), np.float32)
+        _raise(lib().treeray_mlp_train(self.h, _dev(X, torch.float32, "X"), _dev(y, torch.float32, "y"), n,
+                                       int(batch), int(steps), C.c_float(lr), C.c_uint64(seed),
+                                       C.c_void_p(hist.ctypes.data), _stream(stream)))
+        return hist[:steps]
+
+    def grad(self, X, y, stream=None):
+        import numpy as np
+        import torch
+        g = np.zeros(self.N_PARAMS, np.float32)
+        loss = C.c_float(0.0)
+        _raise(lib().treeray_mlp_grad(self.h, _dev(X, torch.float32, "X"), _dev(y, torch.float32, "y"),
+                                      y.numel(), C.c_void_p(g.ctypes.data), C.byref(loss), _stream(stream)))
+        return g, loss.value
+
+    def infer(self, X, stream=None):
+        import torch
+        n = X.numel() // 6
+        y = torch.empty(n, dtype=torch.float32, device=X.device)
+        _raise(lib().treeray_mlp_infer(self.h, _dev(X, torch.float32, "X"), n, _dev(y, torch.float32, "y"),
+                                       _stream(stream)))
+        return y

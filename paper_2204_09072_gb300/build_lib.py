@@ -24,6 +24,7 @@ SOURCES = {
     "evaluate.cu": [],
     "post.cu": [],
     "noalloc.cu": [],
+    "mlp.cu": [],
     "tables.cpp": [],
 }
 

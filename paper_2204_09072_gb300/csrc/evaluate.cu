@@ -49,6 +49,8 @@ struct __align__(16) EvalArgs {
     unsigned long long* queue;
     float* J;
     double* F;
+    float* tau_mean;   // optional: mean over rays of the ray optical depth
+    float* tau_min;    // optional: smallest ray optical depth
     int32_t* acc_counts;   // accepted-list mode
     int32_t* acc_ids;
     unsigned long long* stats;  // accepted-list mode: totals of visits, accepted, entries
@@ -227,6 +229,7 @@ __global__ void __launch_bounds__(WPT * 32) k_evaluate(EvalArgs a, const EvalArg
     __shared__ int s_sp, s_overflow;
     __shared__ long long s_q;
     __shared__ double s_red[4][WPT];
+    __shared__ float s_tau[2][WPT];
     const unsigned full = 0xffffffffu;
     const unsigned lt_mask = (1u << lane) - 1u;
     const float omega = (float)(4.0 * kPi / NPIX);
@@ -464,6 +467,7 @@ __global__ void __launch_bounds__(WPT * 32) k_evaluate(EvalArgs a, const EvalArg
         __syncthreads();
         // ---- integrate each ray from the inside out (one thread per ray)
         double Js = 0.0, Fx = 0.0, Fy = 0.0, Fz = 0.0;
+        float tsum = 0.0f, tminv = 3.0e38f;
         for (int h = tid; h < NPIX; h += NT) {
             if (THICK) {
                 const unsigned long long fl = flags[h];
@@ -522,6 +526,11 @@ __global__ void __launch_bounds__(WPT * 32) k_evaluate(EvalArgs a, const EvalArg
                 }
                 if (THICK && f > 0.0f) ek *= (1.0f - f) + f * expf(-tk);
             }
+            if (A.tau_mean) {  // optical depth of the whole ray: thin prefix plus thick transmission
+                const float tr = (deep ? (float)tcum_d : tcum) + (THICK && ek < 1.0f ? -__logf(ek) : 0.0f);
+                tsum += tr;
+                tminv = fminf(tminv, tr);
+            }
             Js += (double)Fh;
             Fx -= (double)Fh * (double)__ldg(A.nhat + 3 * h);
             Fy -= (double)Fh * (double)__ldg(A.nhat + 3 * h + 1);
@@ -541,6 +550,16 @@ __global__ void __launch_bounds__(WPT * 32) k_evaluate(EvalArgs a, const EvalArg
                 s_red[2][warp] = Fy;
                 s_red[3][warp] = Fz;
             }
+            if (A.tau_mean) {
+                for (int off = 16; off > 0; off >>= 1) {
+                    tsum += __shfl_xor_sync(full, tsum, off);
+                    tminv = fminf(tminv, __shfl_xor_sync(full, tminv, off));
+                }
+                if (lane == 0) {
+                    s_tau[0][warp] = tsum;
+                    s_tau[1][warp] = tminv;
+                }
+            }
         }
         __syncthreads();
         if (tid == 0) {
@@ -553,6 +572,15 @@ __global__ void __launch_bounds__(WPT * 32) k_evaluate(EvalArgs a, const EvalArg
             A.F[3 * out] = r[1] * Fu;
             A.F[3 * out + 1] = r[2] * Fu;
             A.F[3 * out + 2] = r[3] * Fu;
+            if (A.tau_mean) {
+                float ts = 0.0f, tm = 3.0e38f;
+                for (int w = 0; w < WPT && w * 32 < NPIX; ++w) {
+                    ts += s_tau[0][w];
+                    tm = fminf(tm, s_tau[1][w]);
+                }
+                A.tau_mean[out] = ts / NPIX;
+                A.tau_min[out] = tm;
+            }
         }
         __syncthreads();
     }
@@ -698,6 +726,16 @@ treeray_status launch_evaluate(treeray_ctx* c, const int32_t* targets, int64_t n
     EvalArgs a = make_args(c, targets, n);
     a.J = J;
     a.F = F;
+    return dispatch_eval(c, a, s);
+}
+
+treeray_status launch_evaluate_tau(treeray_ctx* c, float* J, double* F, float* tau_mean, float* tau_min,
+                                   cudaStream_t s) {
+    EvalArgs a = make_args(c, nullptr, c->nleaves);
+    a.J = J;
+    a.F = F;
+    a.tau_mean = tau_mean;
+    a.tau_min = tau_min;
     return dispatch_eval(c, a, s);
 }
 
