@@ -31,6 +31,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -436,6 +438,106 @@ def run_sweep(args):
             c.close()
 
 
+def _cloud(n, seed, sigma, n_stars, npix, uv_heating=False):
+    """Turbulent cloud with stars and an ionising flux field. The flux is a network
+    feature; its UV dust heating is left out unless asked for: with it, dense cells near
+    the stars turn optically thick, and a thick cell's own segment (tau_thick,0 = 0) passes
+    all outside radiation, so their dust balance has no equilibrium."""
+    import synth
+    w = synth.turbulent_cloud(n, seed=seed, t_seed=seed + 1, sigma_ln=sigma, n_stars=n_stars, npix=npix)
+    w = synth.with_gas(w, seed=seed + 2, tgas_lo=10.0, tgas_hi=100.0)
+    w = synth.ionising_field(w)
+    if not uv_heating:
+        w.heat_extra = np.zeros_like(w.heat_extra)
+    return w
+
+
+def run_warmstart(args):
+    import numpy as np  # noqa: F401  (used by _cloud)
+    """Learned warm start of the dust-temperature fixed point.
+
+    Training: plain fixed points (tol 1e-4) of five seeded 128^3 clouds (sigma_lnrho 1.5
+    and 2, 1-4 stars with ionising fields), features taken at their initial T_d: ~1e7
+    samples. Test: a 256^3 cloud (sigma_lnrho 2, 4 stars, ionising field, seed 777), plain
+    fixed point from T_d ~ U[10, 40] K against features -> network -> fixed point."""
+    import torch
+
+    import paper_2204_09072_gb300 as tr
+    dev = torch.device("cuda:0")
+
+    def make(w):
+        c = tr.Context(w.params)
+        c.build(w.box_cm, torch.as_tensor(w.rho, device=dev), torch.as_tensor(w.td, device=dev), n=w.uniform_n,
+                star_pos=w.star_pos, star_lum=w.star_lum)
+        tg = torch.as_tensor(w.tgas, device=dev)
+        he = torch.as_tensor(w.heat_extra, device=dev)
+        ph = torch.as_tensor(w.phi, device=dev)
+        return c, tg, he, ph
+
+    t0 = time.perf_counter()
+    Xs, ys, its = [], [], []
+    for k, (seed, sig, ns) in enumerate([(101, 1.5, 1), (102, 2.0, 2), (103, 1.5, 4), (104, 2.0, 3), (105, 2.0, 4),
+                                         (106, 2.0, 4), (107, 1.5, 2)]):
+        w = _cloud(128, seed, sig, ns, args.npix)
+        c, tg, he, ph = make(w)
+        X = c.features(tg, phi=ph)[0].clone()
+        td = torch.as_tensor(w.td, device=dev).clone()
+        it = c.fixed_point(tg, td, heat_extra=he, tol=1e-4, max_iter=60, raise_on_noconv=False)
+        its.append(it)
+        if it > 0:  # solves that run away (thick emission over-counted) are left out
+            Xs.append(X)
+            ys.append(torch.log10(td))
+        c.close()
+    X = torch.cat(Xs).reshape(-1).contiguous()
+    y = torch.cat(ys).contiguous()
+    t_data = time.perf_counter() - t0
+    net = tr.MLP(seed=2)
+    net.fit_normalization(X, y)
+    t0 = time.perf_counter()
+    hist = net.train(X, y, steps=args.train_steps, batch=8192, lr=2e-3, seed=7)
+    hist2 = net.train(X, y, steps=args.train_steps // 2, batch=8192, lr=3e-4, seed=8)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+
+    w = _cloud(args.warm_n, 777, 2.0, 4, args.npix)
+    c, tg, he, ph = make(w)
+    td0 = torch.as_tensor(w.td, device=dev)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    td_plain = td0.clone()
+    torch.cuda.synchronize()
+    e[0].record()
+    it_plain = c.fixed_point(tg, td_plain, heat_extra=he, tol=1e-4, max_iter=60, raise_on_noconv=False)
+    e[1].record()
+    torch.cuda.synchronize()
+    c.refresh(td0)
+    td_warm = td0.clone()
+    torch.cuda.synchronize()
+    e[2].record()
+    Xw = c.features(tg, phi=ph)[0]
+    c.warm_start(net, Xw.reshape(-1).contiguous(), td_warm)
+    guess = td_warm.clone()
+    it_warm = c.fixed_point(tg, td_warm, heat_extra=he, tol=1e-4, max_iter=60, raise_on_noconv=False)
+    e[3].record()
+    torch.cuda.synchronize()
+    c.check()
+    ms_plain = e[0].elapsed_time(e[1])
+    ms_warm = e[2].elapsed_time(e[3])
+    gerr = (guess / td_plain - 1).abs()
+    ferr = (td_warm / td_plain - 1).abs()
+    print(json.dumps({
+        "workload": f"learned warm start, test cloud {args.warm_n}^3 sigma_lnrho 2, 4 stars, ionising flux "
+                    "as a feature (no UV dust heating)",
+        "train_samples": int(y.numel()), "train_solves_iterations": its, "train_steps": len(hist) + len(hist2),
+        "train_loss_first_last": [float(hist[:20].mean()), float(hist2[-50:].mean())],
+        "s_training_data": t_data, "s_training": t_train,
+        "iterations_plain": it_plain, "iterations_warm": it_warm, "warm_extra_evaluations": 1,
+        "iteration_ratio": it_plain / max(it_warm, 1),
+        "evaluation_ratio": it_plain / (it_warm + 1),
+        "ms_fixed_point_plain": ms_plain, "ms_warm_total": ms_warm, "speedup": ms_plain / ms_warm,
+        "guess_rel_err_max": float(gerr.max()), "guess_rel_err_median": float(gerr.median()),
+        "final_rel_diff_max": float(ferr.max())}))
+
+
 def run_profile(args):
     """Profiling driver for ncu: build the full tree once, then launch the evaluate
     kernel on a seeded subset of targets: two warm-up launches, then one more."""
@@ -515,6 +617,9 @@ def main():
     ap.add_argument("--profile-targets", type=int, default=262144)
     ap.add_argument("--batch64", action="store_true", help="64-box AMR batch: batched vs per-box launches")
     ap.add_argument("--sweep", action="store_true", help="N_pix x segments sweep with the autotuner")
+    ap.add_argument("--warmstart", action="store_true", help="learned warm start of the T_d fixed point")
+    ap.add_argument("--warm-n", type=int, default=256)
+    ap.add_argument("--train-steps", type=int, default=4000)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
@@ -524,6 +629,8 @@ def main():
         run_batch64(args)
     elif args.sweep:
         run_sweep(args)
+    elif args.warmstart:
+        run_warmstart(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -228,7 +228,7 @@ treeray_status treeray_batch_evaluate(treeray_batch_t batch, float* const* J, do
  * Features (treeray_features), per leaf, 6 floats, row-major X[N][6]:
  *   log10 rho, log10 T_gas, log10(mean over rays of the ray optical depth + 1e-6),
  *   log10(ionising photon flux + 1), log10(smallest ray optical depth + 1e-6),
- *   log10(unattenuated stellar J + 1e-30), J_* = sum_s L_s / (16 pi^2 r_s^2).
+ *   log10(J + 1e-30) with J the mean intensity of this same evaluation (stars included).
  * treeray_features runs one ray evaluation of the current tree (J, F as treeray_evaluate,
  * plus tau_mean, tau_min: device float[N]) and then fills X (device float[6N]).
  * phi: device float[N] ionising photon flux or NULL (zero).

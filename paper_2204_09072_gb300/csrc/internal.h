@@ -152,7 +152,7 @@ treeray_status refresh_tree(treeray_ctx* c, const float* Td, const int* skip, cu
 treeray_status launch_evaluate_tau(treeray_ctx* c, float* J, double* F, float* tau_mean, float* tau_min,
                                    cudaStream_t s);
 treeray_status launch_features(treeray_ctx* c, const float* Tgas, const float* phi, const float* tau_mean,
-                               const float* tau_min, float* X, cudaStream_t s);
+                               const float* tau_min, const float* J, float* X, cudaStream_t s);
 treeray_status launch_evaluate_skip(treeray_ctx* c, float* J, double* F, const int* skip, cudaStream_t s);
 treeray_status launch_dust_skip(treeray_ctx* c, const float* Tgas, const float* heat, const float* J,
                                 float* Td, const int* skip, cudaStream_t s);

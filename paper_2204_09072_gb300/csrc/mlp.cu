@@ -1,7 +1,7 @@
 // Learned warm start of the dust-temperature fixed point: a 6 -> 64 -> 64 -> 1 SiLU
 // multilayer perceptron predicting log10 T_d from per-cell features (log density, log gas
-// temperature, log mean and smallest ray optical depth, log ionising flux, log
-// unattenuated stellar J). The paper has no learned component; this network only sets
+// temperature, log mean and smallest ray optical depth, log ionising flux, log J of the
+// feature pass at the initial dust temperatures). The paper has no learned component; this network only sets
 // the starting point of the iteration, which still converges to the same fixed point.
 //
 // Numerics: FP32 master weights; BF16 copies of the weights and BF16-rounded layer
@@ -595,7 +595,7 @@ treeray_status treeray_features(treeray_t c, const float* Tgas, const float* phi
     cudaStream_t s = (cudaStream_t)stream;
     treeray_status rc = launch_evaluate_tau(c, J, F, tau_mean, tau_min, s);
     if (rc != TREERAY_OK) return rc;
-    return launch_features(c, Tgas, phi, tau_mean, tau_min, X, s);
+    return launch_features(c, Tgas, phi, tau_mean, tau_min, J, X, s);
 }
 
 treeray_status treeray_warm_start(treeray_t c, treeray_mlp_t m, const float* X, float* Td,

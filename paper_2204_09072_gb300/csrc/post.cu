@@ -145,21 +145,14 @@ treeray_status launch_dust_skip(treeray_ctx* c, const float* Tgas, const float* 
 namespace {
 // Warm-start features of every leaf (caller order), as 6 floats:
 //   log10 rho, log10 T_gas, log10(mean ray optical depth + 1e-6), log10(ionising flux + 1),
-//   log10(smallest ray optical depth + 1e-6), log10(unattenuated stellar J + 1e-30)
-// with J_* = sum_s L_s / (16 pi^2 r_s^2), r_s from the cell centre (at least half a cell).
+//   log10(smallest ray optical depth + 1e-6), log10(J of the same evaluation + 1e-30)
 struct FeatArgs {
     const float* rho;
     const float* tgas;
     const float* phi;
     const float* tau_mean;
     const float* tau_min;
-    const double* star;
-    int n_stars;
-    const int4* geo;
-    const int32_t* leaf_node;
-    const int32_t* inv_perm;
-    double u;
-    int lmax;
+    const float* J;
     int64_t n;
     float* X;
 };
@@ -167,22 +160,13 @@ struct FeatArgs {
 __global__ void k_features(FeatArgs f) {
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= f.n) return;
-    const int4 g = f.geo[f.leaf_node[f.inv_perm[k]]];
-    const double cx = g.x * f.u, cy = g.y * f.u, cz = (g.z & 0xffffff) * f.u;
-    const double half = (double)(1 << (f.lmax - (g.z >> 24))) * f.u;  // half the cell edge
-    double js = 0.0;
-    for (int q = 0; q < f.n_stars; ++q) {
-        const double dx = f.star[4 * q] - cx, dy = f.star[4 * q + 1] - cy, dz = f.star[4 * q + 2] - cz;
-        const double r2 = fmax(dx * dx + dy * dy + dz * dz, half * half);
-        js += f.star[4 * q + 3] / (16.0 * kPi * kPi * r2);
-    }
     float* x = f.X + 6 * k;
     x[0] = log10f(f.rho[k]);
     x[1] = log10f(f.tgas[k]);
     x[2] = log10f(f.tau_mean[k] + 1e-6f);
     x[3] = log10f((f.phi ? f.phi[k] : 0.0f) + 1.0f);
     x[4] = log10f(f.tau_min[k] + 1e-6f);
-    x[5] = (float)log10(js + 1e-30);
+    x[5] = log10f(f.J[k] + 1e-30f);
 }
 
 // Largest relative change max_k |T_new - T| / T of one fixed-point iteration (as the
@@ -213,9 +197,8 @@ __global__ void k_fp_check(int* flags, float tol, int max_iter) {
 }  // namespace
 
 treeray_status launch_features(treeray_ctx* c, const float* Tgas, const float* phi, const float* tau_mean,
-                               const float* tau_min, float* X, cudaStream_t s) {
-    FeatArgs f{c->tree.rho, Tgas, phi, tau_mean, tau_min, c->tree.stars, c->n_stars, c->tree.geo,
-               c->tree.leaf_node, c->tree.inv_perm, c->u, c->lmax, c->nleaves, X};
+                               const float* tau_min, const float* J, float* X, cudaStream_t s) {
+    FeatArgs f{c->tree.rho, Tgas, phi, tau_mean, tau_min, J, c->nleaves, X};
     k_features<<<(int)((c->nleaves + 255) / 256), 256, 0, s>>>(f);
     c->launches += 1;
     TR_CUDA(cudaGetLastError());

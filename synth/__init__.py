@@ -43,6 +43,7 @@ class Workload:
     star_pos: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros((0, 3)))
     star_lum: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros((0,)))
     tgas: np.ndarray | None = None   # float32[N], K
+    phi: np.ndarray | None = None    # float32[N], ionising photon flux (photons/s/cm^2)
     heat_extra: np.ndarray | None = None  # float32[N], erg/s/cm^3
     params: dict = dataclasses.field(default_factory=dict)
     uniform_n: int = 0               # n for an n^3 uniform grid, 0 for AMR
@@ -367,6 +368,28 @@ def batch_of_boxes(count: int = 64, seed: int = 5, **pover):
         kap = float(rng.uniform(1.0, 10.0))
         out.append(amr_random(finest, levels, seed=int(rng.integers(1 << 30)), kappa=kap, **pover))
     return out
+
+
+def ionising_field(w: Workload, q_per_lsun: float = 1e44, e_photon_ev: float = 18.0,
+                   sigma_d: float = 1.5e-21) -> Workload:
+    """Attach a synthetic ionising photon flux and the UV heating it implies.
+
+    phi = sum_s Q_s / (4 pi d_s^2) (unattenuated; the ionising transfer itself is a
+    separate module), Q_s = q_per_lsun x L_s / Lsun photons/s; the UV heating
+    n_H sigma_d E phi (sigma_d = 1.5e-21 cm^2 per H, mean photon energy 18 eV, n_H =
+    0.7 rho / m_H) enters the dust balance as heat_extra.
+    """
+    n = w.n_leaves
+    cen = (w.leaf_ijk.astype(np.float64) + 0.5) * (w.box_cm / (2.0 ** w.leaf_level))[:, None]
+    half = 0.5 * w.box_cm / (2.0 ** w.leaf_level)
+    phi = np.zeros(n)
+    for pos, lum in zip(w.star_pos, w.star_lum):
+        d2 = np.maximum(((cen - pos) ** 2).sum(1), half * half)
+        phi += q_per_lsun * lum / LSUN / (4 * math.pi * d2)
+    nH = 0.7 * w.rho.astype(np.float64) / 1.6726e-24
+    w.phi = phi.astype(np.float32)
+    w.heat_extra = (nH * sigma_d * e_photon_ev * 1.602e-12 * phi).astype(np.float32)
+    return w
 
 
 def sample_targets(n_leaves: int, count: int, seed: int = 11) -> np.ndarray:
