@@ -204,7 +204,7 @@ constexpr int kOwnerCap = 512;  // entries per warp and walk step spread one per
 //   rays:    one thread per ray integrates the segments inside out in FP32 (optical-depth
 //            prefix in FP64 once it passes 40), then the team reduces J and F in FP64.
 template <int NPIX, bool THICK, int WPT>
-__global__ void __launch_bounds__(WPT * 32) k_evaluate(EvalArgs a, const EvalArgs* __restrict__ boxes,
+__global__ void __launch_bounds__(WPT * 32, 48 / WPT) k_evaluate(EvalArgs a, const EvalArgs* __restrict__ boxes,
                                                        const int64_t* __restrict__ box_start, int nbox) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int NT = WPT * 32;
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(WPT * 32) k_evaluate(EvalArgs a, const EvalArg
         warp * kOwnerCap;
     __shared__ int s_sp, s_overflow;
     __shared__ long long s_q;
-    __shared__ double s_red[4][WPT];
+    __shared__ double s_red[4][WPT];  // [0] holds the FP32 J sum
     __shared__ float s_tau[2][WPT];
     const unsigned full = 0xffffffffu;
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -466,7 +466,10 @@ __global__ void __launch_bounds__(WPT * 32) k_evaluate(EvalArgs a, const EvalArg
         }
         __syncthreads();
         // ---- integrate each ray from the inside out (one thread per ray)
-        double Js = 0.0, Fx = 0.0, Fy = 0.0, Fz = 0.0;
+        // J sums positive terms (FP32 tree reduction); the flux vector cancels between
+        // opposite rays and is reduced in FP64 from FP32 products F^h n^h
+        float Js = 0.0f;
+        double Fx = 0.0, Fy = 0.0, Fz = 0.0;
         float tsum = 0.0f, tminv = 3.0e38f;
         for (int h = tid; h < NPIX; h += NT) {
             if (THICK) {
@@ -531,10 +534,10 @@ __global__ void __launch_bounds__(WPT * 32) k_evaluate(EvalArgs a, const EvalArg
                 tsum += tr;
                 tminv = fminf(tminv, tr);
             }
-            Js += (double)Fh;
-            Fx -= (double)Fh * (double)__ldg(A.nhat + 3 * h);
-            Fy -= (double)Fh * (double)__ldg(A.nhat + 3 * h + 1);
-            Fz -= (double)Fh * (double)__ldg(A.nhat + 3 * h + 2);
+            Js += Fh;
+            Fx -= (double)(Fh * __ldg(A.nhat + 3 * h));
+            Fy -= (double)(Fh * __ldg(A.nhat + 3 * h + 1));
+            Fz -= (double)(Fh * __ldg(A.nhat + 3 * h + 2));
         }
         // ---- team reduction in FP64 (only warps that hold rays contribute)
         if (warp * 32 < NPIX) {
@@ -545,7 +548,7 @@ __global__ void __launch_bounds__(WPT * 32) k_evaluate(EvalArgs a, const EvalArg
                 Fz += __shfl_xor_sync(full, Fz, off);
             }
             if (lane == 0) {
-                s_red[0][warp] = Js;
+                s_red[0][warp] = (double)Js;
                 s_red[1][warp] = Fx;
                 s_red[2][warp] = Fy;
                 s_red[3][warp] = Fz;
