@@ -208,6 +208,7 @@ treeray_status treeray_destroy(treeray_t c) {
     if (c->fp_J) cudaFree(c->fp_J);
     if (c->fp_F) cudaFree(c->fp_F);
     if (c->fp_flags) cudaFree(c->fp_flags);
+    if (c->stack_scr) cudaFree(c->stack_scr);
     if (c->fp_stream) cudaStreamDestroy(c->fp_stream);
     for (cudaEvent_t e : c->fp_ev)
         if (e) cudaEventDestroy(e);
@@ -226,7 +227,9 @@ treeray_status treeray_build(treeray_t c, const treeray_grid* g, const float* rh
         set_error("null grid");
         return TREERAY_EINVAL;
     }
-    return build_tree(c, g, rho, Td, kappa, n_stars, star_pos, star_lum, (cudaStream_t)stream);
+    rc = build_tree(c, g, rho, Td, kappa, n_stars, star_pos, star_lum, (cudaStream_t)stream);
+    if (rc != TREERAY_OK) return rc;
+    return reserve_eval_stacks(c, c->lmax, (cudaStream_t)stream);
 }
 
 treeray_status treeray_evaluate(treeray_t c, const int32_t* targets, int64_t n, float* J, double* F,

@@ -1,18 +1,18 @@
-// Ray evaluation (Secs. 4.2-4.4 of Klepitko et al. 2023): one warp per target.
+// Ray evaluation (Secs. 4.2-4.4 of Klepitko et al. 2023): a team of warps per target.
 //
-// Walk: a shared-memory stack of child groups (the 8 sub-nodes of an opened node are
-// contiguous). Each step pops up to 4 groups, so the 32 lanes test 32 nodes at once;
-// opened nodes push their child group through a ballot compaction, accepted nodes
-// are deposited by their own lane. Open/accept, the segment index, the angular-kernel
-// key and straddled segment boundaries are decided in exact integer arithmetic on the
-// squared centre distance (thresholds built on the host in FP64).
+// Walk: a stack of child groups (the 8 sub-nodes of an opened node are contiguous). Each
+// step the team pops up to 4 groups per warp, so every thread tests one node; opened
+// nodes push their child group through a ballot compaction. Open/accept, the segment
+// index, the angular-kernel key and straddled segment boundaries are decided in exact
+// integer arithmetic on the squared centre distance (thresholds built on the host in FP64).
 //
 // Deposit (Secs. 4.2.1-4.2.2): per (segment i, ray h) shared-memory accumulators
 //   thin:  L^ += a b L,  A^ += a b A~          (b = R_i^2 / r_COL^2, a = alpha_node(h))
 //   thick: L^ += a L_V,  A^ += A~,  V^ += a V,  Q^ += a b V, plus straddle flags.
-// Integration (Sec. 4.3): lane = ray, segments inside out, optical-depth prefix sum and
-// thick transmission product in FP64. Finalization (Sec. 4.4): FP64 warp reduction of
-// sum_h F^h and sum_h -F^h n^h.
+// Integration (Sec. 4.3): segments inside out per ray in FP32, with the optical-depth
+// prefix and the flux sums carried as float pairs (error-free transformations), so the
+// GB300's slow FP64 pipe is not on the path. Finalization (Sec. 4.4): J = sum_h F^h / 4 pi,
+// F = -sum_h F^h n^h, converted to CGS in FP64.
 //
 // Internal units: lengths in half-cells of the finest level (u cm), luminosities in
 // L_scale erg/s; fluxes come out in L_scale / u^2 and are converted to CGS at the end.
@@ -55,11 +55,13 @@ struct __align__(16) EvalArgs {
     int32_t* acc_ids;
     unsigned long long* stats;  // accepted-list mode: totals of visits, accepted, entries
     const int* skip;            // fixed-point mode: return at once when *skip != 0
+    int* stack;                 // team stacks: stack_cap ints per block of the launch
     int acc_cap;
     int64_t n;
     int64_t nleaves;
     int lmax, nbins, D, stack_cap, npix;
     double u;
+    double inv_u2;  // 1 / u^2: flux unit = L_scale / u^2 (L_scale a power of two)
 };
 
 namespace {
@@ -85,6 +87,36 @@ __device__ __forceinline__ int fixup(int g, int64_t d2, const int64_t* __restric
 // and geometric ratio g: 0.5 log2(x2 / R_0^2) / log2(g).
 __device__ __forceinline__ int guess_bin(float x2, float2 lp) {
     return x2 > 0.0f ? (int)(__log2f(x2 * lp.x) * lp.y) : 0;
+}
+
+// Exact integer -> float conversions on the FP32 and integer pipes: the integer is
+// placed in the mantissa of a float whose unit in the last place is 1.
+__device__ __forceinline__ float small_int_to_float(int v) {  // exact for |v| < 2^22
+    return __int_as_float(0x4B400000 + v) - 12582912.0f;
+}
+__device__ __forceinline__ float count_to_float(uint32_t v) {  // exact for v < 2^23
+    return __uint_as_float(0x4B000000u | v) - 8388608.0f;
+}
+
+// Error-free transformations (Knuth's TwoSum; the FMA residual of a product), written
+// with the _rn intrinsics so that the compiler never fuses them. An unevaluated pair
+// (hi, lo) then carries about 48 significant bits through FP32 arithmetic.
+__device__ __forceinline__ void two_sum_into(float& hi, float& lo, float b) {
+    const float s = __fadd_rn(hi, b);
+    const float bb = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    hi = s;
+    lo = __fadd_rn(lo, err);
+}
+__device__ __forceinline__ void add_product(float& hi, float& lo, float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float e = fmaf(a, b, -p);  // a b - p exactly
+    two_sum_into(hi, lo, p);
+    lo = __fadd_rn(lo, e);
+}
+__device__ __forceinline__ void add_pair(float& hi, float& lo, float bh, float bl) {
+    two_sum_into(hi, lo, bh);
+    lo = __fadd_rn(lo, bl);
 }
 
 // Accepted-list / walk-statistics mode: the walk alone, one warp per target.
@@ -192,28 +224,39 @@ __global__ void __launch_bounds__(256) k_walk_list(EvalArgs a) {
     }
 }
 
-constexpr int kOwnerCap = 512;  // entries per warp and walk step spread one per lane
+constexpr int kOwnerCap = 256;  // entries per warp and walk step spread one per lane
 
-// Evaluation kernel: a team of WPT warps per target shares one block-wide walk stack and
-// one (segment x ray) tile in shared memory; the block processes one target at a time
-// and takes the next from a global work counter (persistent grid).
+// Teams resident per SM that the register budget is cut for: thin tiles at N_pix <= 48 are
+// small enough for 64 warps per SM; larger tiles are limited by shared memory anyway.
+constexpr int min_warps_per_sm(int npix, bool thick) { return thick ? 24 : (npix <= 48 ? 64 : 48); }
+
+// Evaluation kernel: a team of WPT warps per target shares one walk stack (its block's
+// slice of a global scratch array, L1-resident) and one (segment x ray) tile in shared
+// memory; the block processes one target at a time and takes the next from a global
+// work counter (persistent grid).
 //   walk:    each step the team pops up to 4 WPT child groups (32 WPT nodes), tests them,
-//            appends the opened nodes' child groups to the shared stack (one shared-memory
-//            atomic per warp) and deposits the accepted ones (one node per thread, its
-//            angular-kernel entries in a loop, shared-memory atomics into the tile);
-//   rays:    one thread per ray integrates the segments inside out in FP32 (optical-depth
-//            prefix in FP64 once it passes 40), then the team reduces J and F in FP64.
+//            appends the opened nodes' child groups to the stack (one shared-memory
+//            atomic per warp) and maps the accepted ones (segment, beta, angular key);
+//   deposit: the warp's thin deposits are spread one angular-kernel entry per lane, in
+//            child-major node order so that sibling nodes, which often hit the same cell,
+//            fall into different rounds; shared-memory atomics into the tile; thick
+//            deposits stay with the node's thread;
+//   rays:    threads integrate the rays' segments inside out (thin tiles with spare
+//            threads cut each ray into consecutive parts joined by their transmission),
+//            then the team reduces J and F.
 template <int NPIX, bool THICK, int WPT>
-__global__ void __launch_bounds__(WPT * 32, 48 / WPT) k_evaluate(EvalArgs a, const EvalArgs* __restrict__ boxes,
-                                                       const int64_t* __restrict__ box_start, int nbox) {
+__global__ void __launch_bounds__(WPT * 32, min_warps_per_sm(NPIX, THICK) / WPT)
+    k_evaluate(EvalArgs a, const EvalArgs* __restrict__ boxes, const int64_t* __restrict__ box_start, int nbox) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int NT = WPT * 32;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nb = a.nbins;
     const int cells = nb * NPIX;
     constexpr int nq = THICK ? 6 : 2;
-    // layout: tile [nq][nb][NPIX] f32 | THICK: flags [NPIX] u64 | stack [cap] i32 |
+    // layout: tile [nq][nb][NPIX] f32 | THICK: flags [NPIX] u64 |
     //         per warp: node buffer int4[32], entry owners u8[kOwnerCap]
+    // The team's stack of child groups is this block's slice of a global scratch array:
+    // it stays in L1, and leaving it out of shared memory lets more teams share an SM.
     float* tL = reinterpret_cast<float*>(smem);
     float* tA = tL + cells;
     float* tLk = tA + cells;
@@ -221,14 +264,14 @@ __global__ void __launch_bounds__(WPT * 32, 48 / WPT) k_evaluate(EvalArgs a, con
     float* tVk = tAk + cells;
     float* tQk = tVk + cells;
     unsigned long long* flags = reinterpret_cast<unsigned long long*>(smem + (size_t)nq * cells * 4);
-    int* stack = reinterpret_cast<int*>(smem + (size_t)nq * cells * 4 + (THICK ? NPIX * 8 : 0));
-    int4* nodebuf = reinterpret_cast<int4*>(stack + a.stack_cap) + warp * 32;
-    unsigned char* owner =
-        reinterpret_cast<unsigned char*>(reinterpret_cast<int4*>(stack + a.stack_cap) + WPT * 32) +
-        warp * kOwnerCap;
+    int4* nodebufs = reinterpret_cast<int4*>(smem + (size_t)nq * cells * 4 + (THICK ? NPIX * 8 : 0));
+    int4* nodebuf = nodebufs + warp * 32;
+    unsigned char* owner = reinterpret_cast<unsigned char*>(nodebufs + WPT * 32) + warp * kOwnerCap;
+    const int stack_cap = a.stack_cap;
+    int* stack = a.stack + (size_t)blockIdx.x * stack_cap;
     __shared__ int s_sp, s_overflow;
     __shared__ long long s_q;
-    __shared__ double s_red[4][WPT];  // [0] holds the FP32 J sum
+    __shared__ float s_red[7][WPT];  // J, then (hi, lo) pairs of F_x, F_y, F_z
     __shared__ float s_tau[2][WPT];
     const unsigned full = 0xffffffffu;
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -346,7 +389,7 @@ __global__ void __launch_bounds__(WPT * 32, 48 / WPT) k_evaluate(EvalArgs a, con
                 pos0 = __shfl_sync(full, pos0, 0);
                 if (open) {
                     const int pos = pos0 + __popc(om & lt_mask);
-                    if (pos < A.stack_cap) stack[pos] = gg.w;
+                    if (pos < stack_cap) stack[pos] = gg.w;
                     else s_overflow = 1;
                 }
             }
@@ -357,10 +400,13 @@ __global__ void __launch_bounds__(WPT * 32, 48 / WPT) k_evaluate(EvalArgs a, con
             int ne = 0, ebase = 0, cbase = 0;
             float bL = 0.0f, bA = 0.0f;
             if (acc) {
-                const int i = fixup(guess_bin((float)d2, lp), d2, thr, nb);
+                // the float distance only guesses the segment; the integer d^2 decides it
+                const float fx = small_int_to_float(ox), fy = small_int_to_float(oy), fz = small_int_to_float(oz);
+                const float fd2 = fx * fx + fy * fy + fz * fz;
+                const int i = fixup(guess_bin(fd2, lp), d2, thr, nb);
                 const float4 v0 = __ldg(A.thin + node);
                 const float4 v1 = __ldg(A.thick + node);
-                const float rx = (float)ox + v0.z, ry = (float)oy + v0.w, rz = (float)oz + v1.x;
+                const float rx = fx + v0.z, ry = fy + v0.w, rz = fz + v1.x;
                 const float beta = __ldg(R2 + i) / (rx * rx + ry * ry + rz * rz);
                 const int elog = A.lmax - lvl + 1;
                 const int Kx = alpha_key(ox, elog), Ky = alpha_key(oy, elog), Kz = alpha_key(oz, elog);
@@ -378,7 +424,7 @@ __global__ void __launch_bounds__(WPT * 32, 48 / WPT) k_evaluate(EvalArgs a, con
                     if (THICK && v1.w > 0.0f) {
                         const int64_t* lo = A.str_lo + ((int64_t)tl * (A.lmax + 1) + lvl) * nb;
                         const int64_t* hi = A.str_hi + ((int64_t)tl * (A.lmax + 1) + lvl) * nb;
-                        const float d = sqrtf((float)d2);
+                        const float d = sqrtf(fd2);
                         const float sd = 0.8660254f * (float)(2 << (A.lmax - lvl));
                         const float dl = fmaxf(d - sd, 0.0f), dh = d + sd;
                         const int ilo = fixup(guess_bin(dl * dl, lp), d2, lo, nb);
@@ -389,7 +435,7 @@ __global__ void __launch_bounds__(WPT * 32, 48 / WPT) k_evaluate(EvalArgs a, con
                             const uint32_t ent = __ldg(A.aent + e);
                             const int h = (int)(ent & 0xffffu);
                             const int cidx = i * NPIX + h;
-                            const float wn = (float)(ent >> 16) * inv_s3;
+                            const float wn = count_to_float(ent >> 16) * inv_s3;
                             atomicAdd(tLk + cidx, wn * v1.y);
                             atomicAdd(tAk + cidx, v1.z);
                             atomicAdd(tVk + cidx, wn * v1.w);
@@ -399,15 +445,18 @@ __global__ void __launch_bounds__(WPT * 32, 48 / WPT) k_evaluate(EvalArgs a, con
                     }
                 }
             }
-            // warp-level exclusive scan of the entry counts
-            int inc = ne;
+            // warp-level exclusive scan of the entry counts,
+            // in child-major order (child c of the warp's groups 0..3, then child c + 1, ...):
+            // entries of sibling nodes, which often share a cell, fall into different rounds
+            const int nv = __shfl_sync(full, ne, ((lane & 3) << 3) | (lane >> 2));
+            int inc = nv;
             for (int off = 1; off < 32; off <<= 1) {
                 const int t = __shfl_up_sync(full, inc, off);
                 if (lane >= off) inc += t;
             }
             const int tw = __shfl_sync(full, inc, 31);
+            const int pre = __shfl_sync(full, inc - nv, ((lane & 7) << 2) | (lane >> 3));
             if (tw > 0) {
-                const int pre = inc - ne;
                 if (tw <= kOwnerCap) {
                     if (ne > 0) {
                         nodebuf[lane] = make_int4(cbase, ebase - pre, __float_as_int(bL), __float_as_int(bA));
@@ -418,7 +467,7 @@ __global__ void __launch_bounds__(WPT * 32, 48 / WPT) k_evaluate(EvalArgs a, con
                         const int4 nd = nodebuf[owner[r]];
                         const uint32_t ent = __ldg(A.aent + nd.y + r);
                         const int c = nd.x + (int)(ent & 0xffffu);
-                        const float w = (float)(ent >> 16);
+                        const float w = count_to_float(ent >> 16);
                         atomicAdd(tL + c, w * __int_as_float(nd.z));
                         atomicAdd(tA + c, w * __int_as_float(nd.w));
                     }
@@ -427,7 +476,7 @@ __global__ void __launch_bounds__(WPT * 32, 48 / WPT) k_evaluate(EvalArgs a, con
                     for (int e = ebase; e < ebase + ne; ++e) {
                         const uint32_t ent = __ldg(A.aent + e);
                         const int c = cbase + (int)(ent & 0xffffu);
-                        const float w = (float)(ent >> 16);
+                        const float w = count_to_float(ent >> 16);
                         atomicAdd(tL + c, w * bL);
                         atomicAdd(tA + c, w * bA);
                     }
@@ -465,33 +514,15 @@ __global__ void __launch_bounds__(WPT * 32, 48 / WPT) k_evaluate(EvalArgs a, con
             }
         }
         __syncthreads();
-        // ---- integrate each ray from the inside out (one thread per ray)
-        // J sums positive terms (FP32 tree reduction); the flux vector cancels between
-        // opposite rays and is reduced in FP64 from FP32 products F^h n^h
-        float Js = 0.0f;
-        double Fx = 0.0, Fy = 0.0, Fz = 0.0;
-        float tsum = 0.0f, tminv = 3.0e38f;
-        for (int h = tid; h < NPIX; h += NT) {
-            if (THICK) {
-                const unsigned long long fl = flags[h];
-                if (fl)
-                    for (int i = nb - 2; i >= 0; --i) {
-                        if (!((fl >> i) & 1ull)) continue;
-                        const int c0 = i * NPIX + h, c1 = (i + 1) * NPIX + h;
-                        const float T = __ldg(R2 + i) / __ldg(R2 + i + 1);
-                        tL[c0] += T * tL[c1];
-                        tA[c0] += T * tA[c1];
-                        tQk[c0] += T * tQk[c1];
-                        tLk[c0] += tLk[c1];
-                        tAk[c0] += tAk[c1];
-                        tVk[c0] += tVk[c1];
-                        tL[c1] = tA[c1] = tQk[c1] = tLk[c1] = tAk[c1] = tVk[c1] = 0.0f;
-                    }
-            }
-            float tcum = 0.0f, ek = 1.0f, Fh = 0.0f;
-            double tcum_d = 0.0;
-            bool deep = false;
-            for (int i = 0; i < nb; ++i) {
+        // ---- integrate each ray from the inside out
+        // J sums positive FP32 terms. The flux vector cancels between opposite rays, so each
+        // product F^h n^h is split exactly into a float pair and summed with error-free
+        // transformations; the optical-depth prefix is such a pair too. No FP64 on the way.
+        //
+        // Segments i0 <= i < i1 of ray h with a local prefix starting at zero:
+        //   Fp = sum_i eps_i F*_i,  (thi, tlo) = sum_i tau_thin,i,  ek = prod_i thick transmission.
+        auto segments = [&](int h, int i0, int i1, float& Fp, float& thi, float& tlo, float& ek) {
+            for (int i = i0; i < i1; ++i) {
                 const int ci = i * NPIX + h;
                 const float Lth = tL[ci], Ath = tA[ci];
                 const float Vk = THICK ? tVk[ci] : 0.0f;
@@ -515,43 +546,97 @@ __global__ void __launch_bounds__(WPT * 32, 48 / WPT) k_evaluate(EvalArgs a, con
                 const float Fth = g * Lth * inv_R2 * (float)(1.0 / (4.0 * kPi));
                 const float den = Ath + f * Akv;
                 const float Fs = den > 0.0f ? (Fth * Ath + Fk * f * Akv) / den : Fth + Fk;
-                const float eps = expf(deep ? -(float)tcum_d : -tcum) * ek;
-                Fh += eps * Fs;
-                // optical-depth prefix: FP32, promoted to FP64 once the ray passes tau = 40
-                if (!deep) {
-                    tcum += tth;
-                    if (tcum > 40.0f) {
-                        deep = true;
-                        tcum_d = (double)tcum;
-                    }
-                } else {
-                    tcum_d += (double)tth;
-                }
+                // exp(-(thi + tlo)) with |tlo| far below one unit of thi
+                const float eps = expf(-thi) * (1.0f - tlo) * ek;
+                Fp += eps * Fs;
+                two_sum_into(thi, tlo, tth);
                 if (THICK && f > 0.0f) ek *= (1.0f - f) + f * expf(-tk);
             }
-            if (A.tau_mean) {  // optical depth of the whole ray: thin prefix plus thick transmission
-                const float tr = (deep ? (float)tcum_d : tcum) + (THICK && ek < 1.0f ? -__logf(ek) : 0.0f);
+        };
+        float Js = 0.0f;
+        float Fxh = 0.0f, Fxl = 0.0f, Fyh = 0.0f, Fyl = 0.0f, Fzh = 0.0f, Fzl = 0.0f;
+        float tsum = 0.0f, tminv = 3.0e38f;
+        auto ray_done = [&](int h, float Fh, float tr) {
+            if (A.tau_mean) {
                 tsum += tr;
                 tminv = fminf(tminv, tr);
             }
             Js += Fh;
-            Fx -= (double)(Fh * __ldg(A.nhat + 3 * h));
-            Fy -= (double)(Fh * __ldg(A.nhat + 3 * h + 1));
-            Fz -= (double)(Fh * __ldg(A.nhat + 3 * h + 2));
+            add_product(Fxh, Fxl, -Fh, __ldg(A.nhat + 3 * h));
+            add_product(Fyh, Fyl, -Fh, __ldg(A.nhat + 3 * h + 1));
+            add_product(Fzh, Fzl, -Fh, __ldg(A.nhat + 3 * h + 2));
+        };
+        // thin tiles with spare threads: the segments of a ray are cut into P consecutive
+        // parts, one thread each; a part's result is carried outward by the transmission
+        // exp(-tau) of the parts inside it
+        constexpr int P = THICK ? 1 : (NT >= 4 * NPIX ? 4 : (NT >= 2 * NPIX ? 2 : 1));
+        if (P > 1 && nb >= 2 * P) {
+            if (tid < P * NPIX) {
+                const int h = tid % NPIX, p = tid / NPIX;
+                const int i0 = p * nb / P, i1 = (p + 1) * nb / P;
+                float Fp = 0.0f, thi = 0.0f, tlo = 0.0f, ek = 1.0f;
+                segments(h, i0, i1, Fp, thi, tlo, ek);
+                // every part has >= 2 segments: its first two cells of ray h, read only by
+                // this thread, now hold (Fp, thi) and tlo
+                tL[i0 * NPIX + h] = Fp;
+                tA[i0 * NPIX + h] = thi;
+                tL[(i0 + 1) * NPIX + h] = tlo;
+            }
+            __syncthreads();
+            if (tid < NPIX) {
+                const int h = tid;
+                float Fh = 0.0f, chi = 0.0f, clo = 0.0f;
+                for (int p = 0; p < P; ++p) {
+                    const int i0 = p * nb / P;
+                    const float eps = expf(-chi) * (1.0f - clo);
+                    Fh += eps * tL[i0 * NPIX + h];
+                    add_pair(chi, clo, tA[i0 * NPIX + h], tL[(i0 + 1) * NPIX + h]);
+                }
+                ray_done(h, Fh, chi + clo);
+            }
+        } else {
+            for (int h = tid; h < NPIX; h += NT) {
+                if (THICK) {
+                    const unsigned long long fl = flags[h];
+                    if (fl)
+                        for (int i = nb - 2; i >= 0; --i) {
+                            if (!((fl >> i) & 1ull)) continue;
+                            const int c0 = i * NPIX + h, c1 = (i + 1) * NPIX + h;
+                            const float T = __ldg(R2 + i) / __ldg(R2 + i + 1);
+                            tL[c0] += T * tL[c1];
+                            tA[c0] += T * tA[c1];
+                            tQk[c0] += T * tQk[c1];
+                            tLk[c0] += tLk[c1];
+                            tAk[c0] += tAk[c1];
+                            tVk[c0] += tVk[c1];
+                            tL[c1] = tA[c1] = tQk[c1] = tLk[c1] = tAk[c1] = tVk[c1] = 0.0f;
+                        }
+                }
+                float Fh = 0.0f, thi = 0.0f, tlo = 0.0f, ek = 1.0f;
+                segments(h, 0, nb, Fh, thi, tlo, ek);
+                // optical depth of the whole ray: thin prefix plus thick transmission
+                ray_done(h, Fh, (thi + tlo) + (THICK && ek < 1.0f ? -__logf(ek) : 0.0f));
+            }
         }
-        // ---- team reduction in FP64 (only warps that hold rays contribute)
+        // ---- team reduction (only warps that hold rays contribute)
         if (warp * 32 < NPIX) {
             for (int off = 16; off > 0; off >>= 1) {
                 Js += __shfl_xor_sync(full, Js, off);
-                Fx += __shfl_xor_sync(full, Fx, off);
-                Fy += __shfl_xor_sync(full, Fy, off);
-                Fz += __shfl_xor_sync(full, Fz, off);
+                const float xh = __shfl_xor_sync(full, Fxh, off), xl = __shfl_xor_sync(full, Fxl, off);
+                const float yh = __shfl_xor_sync(full, Fyh, off), yl = __shfl_xor_sync(full, Fyl, off);
+                const float zh = __shfl_xor_sync(full, Fzh, off), zl = __shfl_xor_sync(full, Fzl, off);
+                add_pair(Fxh, Fxl, xh, xl);
+                add_pair(Fyh, Fyl, yh, yl);
+                add_pair(Fzh, Fzl, zh, zl);
             }
             if (lane == 0) {
-                s_red[0][warp] = (double)Js;
-                s_red[1][warp] = Fx;
-                s_red[2][warp] = Fy;
-                s_red[3][warp] = Fz;
+                s_red[0][warp] = Js;
+                s_red[1][warp] = Fxh;
+                s_red[2][warp] = Fxl;
+                s_red[3][warp] = Fyh;
+                s_red[4][warp] = Fyl;
+                s_red[5][warp] = Fzh;
+                s_red[6][warp] = Fzl;
             }
             if (A.tau_mean) {
                 for (int off = 16; off > 0; off >>= 1) {
@@ -565,17 +650,20 @@ __global__ void __launch_bounds__(WPT * 32, 48 / WPT) k_evaluate(EvalArgs a, con
             }
         }
         __syncthreads();
-        if (tid == 0) {
-            double r[4] = {0.0, 0.0, 0.0, 0.0};
-            for (int w = 0; w < WPT && w * 32 < NPIX; ++w)
-                for (int c = 0; c < 4; ++c) r[c] += s_red[c][w];
-            const double Fu = A.scal[0] / (A.u * A.u);  // internal flux unit in erg/s/cm^2
-            const int64_t k = A.perm[s];
-            A.J[out] = (float)(r[0] / (4.0 * kPi) * Fu + A.jsrc[k]);
-            A.F[3 * out] = r[1] * Fu;
-            A.F[3 * out + 1] = r[2] * Fu;
-            A.F[3 * out + 2] = r[3] * Fu;
-            if (A.tau_mean) {
+        // four lanes of warp 0 write J and the three flux components in CGS
+        if (tid < 4) {
+            const double Fu = A.scal[0] * A.inv_u2;  // internal flux unit in erg/s/cm^2
+            if (tid == 0) {
+                float js = 0.0f;
+                for (int w = 0; w < WPT && w * 32 < NPIX; ++w) js += s_red[0][w];
+                const int64_t k = A.perm[s];
+                A.J[out] = (float)((double)js * (Fu * (1.0 / (4.0 * kPi))) + A.jsrc[k]);
+            } else {
+                float hi = 0.0f, lo = 0.0f;
+                for (int w = 0; w < WPT && w * 32 < NPIX; ++w) add_pair(hi, lo, s_red[2 * tid - 1][w], s_red[2 * tid][w]);
+                A.F[3 * out + tid - 1] = ((double)hi + (double)lo) * Fu;
+            }
+            if (tid == 0 && A.tau_mean) {
                 float ts = 0.0f, tm = 3.0e38f;
                 for (int w = 0; w < WPT && w * 32 < NPIX; ++w) {
                     ts += s_tau[0][w];
@@ -620,15 +708,18 @@ treeray_status launch_persistent(treeray_ctx* c, K kern, size_t per_warp, int ma
     return TREERAY_OK;
 }
 
+size_t stack_bytes_for(int wpt, int lmax, int blocks) {
+    // the team stack holds at most one batch of pushes (32 WPT groups) per level
+    return (size_t)blocks * (size_t)(32 * wpt * (lmax + 1) + 64) * sizeof(int);
+}
+
 template <int NPIX, bool THICK, int WPT>
 treeray_status launch_team(treeray_ctx* c, const EvalArgs& a, const EvalArgs* boxes,
                            const int64_t* box_start, int nbox, int layout_lmax, cudaStream_t s) {
     constexpr int nq = THICK ? 6 : 2;
     EvalArgs b = a;
-    // the team stack holds at most one batch of pushes (32 WPT groups) per level
-    b.stack_cap = 32 * WPT * (layout_lmax + 1) + 64;
-    const size_t smem = (size_t)nq * a.nbins * NPIX * 4 + (THICK ? NPIX * 8 : 0) + (size_t)b.stack_cap * 4 +
-                        (size_t)WPT * (32 * 16 + kOwnerCap);
+    b.stack_cap = (int)(stack_bytes_for(WPT, layout_lmax, 1) / sizeof(int));
+    const size_t smem = (size_t)nq * a.nbins * NPIX * 4 + (THICK ? NPIX * 8 : 0) + (size_t)WPT * (32 * 16 + kOwnerCap);
     int smem_optin = 0, sms = 0;
     TR_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
     TR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
@@ -646,6 +737,11 @@ treeray_status launch_team(treeray_ctx* c, const EvalArgs& a, const EvalArgs* bo
     }
     int64_t blocks = (int64_t)per_sm * sms;
     if (blocks > a.n) blocks = a.n;
+    if (c->stack_scr_bytes < stack_bytes_for(WPT, layout_lmax, (int)blocks)) {
+        const treeray_status rc = reserve_eval_stacks(c, layout_lmax, s);
+        if (rc != TREERAY_OK) return rc;
+    }
+    b.stack = c->stack_scr;
     TR_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), s));
     kern<<<(int)blocks, WPT * 32, smem, s>>>(b, boxes, box_start, nbox);
     c->launches += 1;
@@ -717,12 +813,40 @@ EvalArgs make_args(treeray_ctx* c, const int32_t* targets, int64_t n) {
     a.D = c->ht.D;
     a.npix = c->p.npix;
     a.u = c->u;
+    a.inv_u2 = 1.0 / (c->u * c->u);
     // the stack holds at most 28 leftover groups per level plus one batch of pushes
     a.stack_cap = 28 * (c->lmax + 1) + 40;
     return a;
 }
 
 }  // namespace
+
+treeray_status reserve_eval_stacks(treeray_ctx* c, int lmax, cudaStream_t s) {
+    int sms = 0;
+    TR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+    // at most 2048 threads, i.e. 64 / WPT teams, per SM
+    size_t need = 0;
+    for (int wpt : {2, 4, 8}) need = std::max(need, stack_bytes_for(wpt, lmax, sms * (64 / wpt)));
+    if (c->stack_scr_bytes >= need) return TREERAY_OK;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    TR_CUDA(cudaStreamIsCapturing(s, &cs));
+    if (cs != cudaStreamCaptureStatusNone) {
+        set_error("evaluate: team-stack scratch must be reserved before stream capture (build first)");
+        return TREERAY_EINVAL;
+    }
+    if (c->stack_scr) {
+        TR_CUDA(cudaFree(c->stack_scr));  // waits for launches that may still use it
+        c->stack_scr = nullptr;
+        c->stack_scr_bytes = 0;
+    }
+    if (cudaMalloc(&c->stack_scr, need) != cudaSuccess) {
+        c->stack_scr = nullptr;
+        set_error("evaluate: cannot allocate the team-stack scratch");
+        return TREERAY_ENOMEM;
+    }
+    c->stack_scr_bytes = need;
+    return TREERAY_OK;
+}
 
 treeray_status launch_evaluate(treeray_ctx* c, const int32_t* targets, int64_t n, float* J, double* F,
                                cudaStream_t s) {
@@ -897,7 +1021,6 @@ treeray_status treeray_batch_create(const treeray_t* ctxs, int n_boxes, treeray_
         treeray_t c = ctxs[k];
         treeray_batch::Group& g = b->g[(c->has_thick || c->force_thick) ? 1 : 0];
         EvalArgs a = make_args(c, nullptr, c->nleaves);
-        a.stack_cap = 32 * 4 * (c->lmax + 1) + 64;  // 4-warp teams
         if (g.start.empty()) g.start.push_back(0);
         g.box.push_back(k);
         g.desc.push_back(a);
@@ -910,6 +1033,10 @@ treeray_status treeray_batch_create(const treeray_t* ctxs, int n_boxes, treeray_
     };
     for (auto& g : b->g) {
         if (g.box.empty()) continue;
+        // the group's launches use its first context's team-stack scratch, for the
+        // deepest tree of the group
+        const treeray_status rs = reserve_eval_stacks(b->ctx[g.box[0]], g.max_lmax, nullptr);
+        if (rs != TREERAY_OK) return fail(rs);
         const size_t nb = g.box.size();
         if (cudaMalloc(&g.d_desc, sizeof(EvalArgs) * nb) != cudaSuccess ||
             cudaMalloc(&g.d_start, sizeof(int64_t) * (nb + 1)) != cudaSuccess ||

@@ -124,6 +124,8 @@ struct treeray_ctx {
     int64_t fp_cap = 0;
     cudaStream_t fp_stream = nullptr;
     cudaEvent_t fp_ev[2] = {nullptr, nullptr};
+    int* stack_scr = nullptr;    // evaluate: team stacks (global scratch, grow-only)
+    size_t stack_scr_bytes = 0;
     int64_t launches = 0;  // kernels launched by this context
     int wpt = 4;           // warps per target team of the evaluate kernel (autotuned)
     // table cache key
@@ -134,6 +136,9 @@ struct treeray_ctx {
 
 // kernels entry points (defined in the .cu files)
 namespace tr {
+// Team-stack scratch of the evaluate kernel large enough for any team size on a tree of
+// `lmax` levels below the root; never allocates while `s` is being captured.
+treeray_status reserve_eval_stacks(treeray_ctx* c, int lmax, cudaStream_t s);
 treeray_status build_tree(treeray_ctx* c, const treeray_grid* g, const float* rho, const float* Td,
                           const float* kappa, int n_stars, const double* star_pos,
                           const double* star_lum, cudaStream_t s);
