@@ -1,5 +1,6 @@
 // Per-leaf epilogues: radiation energy density and pressure (Sec. 4.5) and the
-// equilibrium dust temperature (Sec. 4.6, App. D). Plain elementwise kernels in FP64.
+// equilibrium dust temperature (Sec. 4.6, App. D). Elementwise kernels; the dust balance is
+// decided in FP64.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -33,12 +34,15 @@ __global__ void k_radpressure(RpArgs r) {
     const double dx = ldexp(r.box, -lvl);
     const double dV = (dx * dx) * dx;
     const double tau = r.tau[k];
-    const double g = tau < 1e-4 ? 1.0 : -expm1(-tau) / tau;
+    // g in FP32 (the outputs are FP32); 1/c as a constant factor: no FP64 divisions
+    const float tf = (float)tau;
+    const double g = tau < 1e-4 ? 1.0 : (double)(-expm1f(-tf) / tf);
     const double kap = r.kap[k];
     const double kr = kap * (double)r.rho[k];
-    if (r.u) r.u[k] = (float)(4.0 * kPi * (double)r.J[k] / kLightC);
+    constexpr double inv_c = 1.0 / kLightC;
+    if (r.u) r.u[k] = (float)((4.0 * kPi * inv_c) * (double)r.J[k]);
     for (int ax = 0; ax < 3; ++ax) {
-        const double Fc = r.F[3 * k + ax] / kLightC;
+        const double Fc = r.F[3 * k + ax] * inv_c;
         if (r.f) r.f[3 * k + ax] = (float)(Fc * kr * g * dV);
         if (r.a) r.a[3 * k + ax] = (float)(Fc * kap * g);
     }
@@ -83,7 +87,67 @@ __device__ inline double balance(const DustArgs& d, int64_t k, const Cell& c, do
     return gd + c.H + c.rho * kap * (4.0 * kPi * c.J - 4.0 * kSigmaSB * T4);
 }
 
-// root by bracketing from the 2.7 K floor and 60 bisections in ln T
+// The reference procedure: 60 bisections in ln T on [floor, hi]; the root to FP64
+// precision (used where the fast path below cannot vouch for its bracket).
+__device__ double bisect64(const DustArgs& d, int64_t k, const Cell& c, double lo, double hi) {
+    for (int it = 0; it < 60; ++it) {
+        const double mid = sqrt(lo * hi);
+        if (balance(d, k, c, mid) > 0.0) lo = mid;
+        else hi = mid;
+    }
+    return sqrt(lo * hi);
+}
+
+// The same root, found in two stages so that the GB300's slow FP64 pipe does little work:
+// bisection in ln T in FP32 on G scaled by 1/M (M bounds every term of G on [floor, hi]),
+// until the bracket is two adjacent floats; then FP64 checks that G changes sign across
+// it (stepping by single floats when the FP32 signs misled it) and picks the float nearest
+// the root from the sign of G at the bracket's midpoint, i.e. the root rounded to FP32.
+__device__ double root_two_stage(const DustArgs& d, int64_t k, const Cell& c, double hi64) {
+    const double b = c.c1 * c.c2 * c.nH2 * (d.xi / 0.01);  // G_dust-gas = b (T_gas - T)
+    const double M = fabs(c.H) + fabs(b) * (c.Tg + hi64) +
+                     c.rho * kappa_of(d, k, hi64) * (4.0 * kPi * c.J + 4.0 * kSigmaSB * ((hi64 * hi64) * (hi64 * hi64)));
+    if (!(M > 0.0) || !(M < 1e300)) return bisect64(d, k, c, kDustFloorK, hi64);
+    const double sc = 1.0 / M;
+    const float Hs = (float)(c.H * sc), bs = (float)(b * sc), rs = (float)(c.rho * sc), Tg = (float)c.Tg;
+    const float J4 = (float)(4.0 * kPi * c.J), s4 = (float)(4.0 * kSigmaSB);
+    const float kc = d.kin ? d.kin[k] : (float)d.kappa0;
+    float lo = (float)kDustFloorK, hi = (float)hi64;
+    for (int it = 0; it < 96; ++it) {
+        float mid = sqrtf(lo) * sqrtf(hi);
+        // a few units apart the rounded geometric mean can fall on an end point: the
+        // arithmetic mean of the two floats then still splits the bracket
+        if (!(mid > lo && mid < hi)) mid = 0.5f * (lo + hi);
+        if (!(mid > lo && mid < hi)) break;
+        const float Tc = fminf(mid, 150.0f);
+        const float kap = (d.kin || d.model == 0) ? kc : 1.0e-3f * (Tc * Tc);
+        const float T4 = (mid * mid) * (mid * mid);
+        const float g = Hs + bs * (Tg - mid) + rs * kap * (J4 - s4 * T4);
+        if (g > 0.0f) lo = mid;
+        else hi = mid;
+    }
+    bool ok = false;
+    for (int it = 0; it < 8; ++it) {
+        if (!(balance(d, k, c, (double)lo) > 0.0)) {  // root below lo
+            hi = lo;
+            lo = nextafterf(lo, 0.0f);
+            continue;
+        }
+        if (balance(d, k, c, (double)hi) > 0.0) {  // root above hi
+            lo = hi;
+            hi = nextafterf(hi, 3.0e38f);
+            continue;
+        }
+        ok = true;
+        break;
+    }
+    if (!ok || nextafterf(lo, 3.0e38f) != hi) return bisect64(d, k, c, kDustFloorK, hi64);
+    const double m = 0.5 * ((double)lo + (double)hi);
+    return balance(d, k, c, m) > 0.0 ? (double)hi : (double)lo;
+}
+
+// root by bracketing from the 2.7 K floor (as the reference procedure), then the two-stage
+// search for the FP32 result
 __global__ void k_dust(DustArgs d) {
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= d.n || (d.skip && *d.skip)) return;
@@ -104,13 +168,7 @@ __global__ void k_dust(DustArgs d) {
         double hi = c.Tg > TJ ? c.Tg : TJ;
         if (hi < kDustFloorK) hi = kDustFloorK;
         for (int it = 0; it < 64 && balance(d, k, c, hi) > 0.0; ++it) hi *= 2.0;
-        double lo = kDustFloorK;
-        for (int it = 0; it < 60; ++it) {
-            const double mid = sqrt(lo * hi);
-            if (balance(d, k, c, mid) > 0.0) lo = mid;
-            else hi = mid;
-        }
-        T = sqrt(lo * hi);
+        T = root_two_stage(d, k, c, hi);
     }
     d.Td[k] = (float)T;
 }
