@@ -538,6 +538,101 @@ def run_warmstart(args):
         "final_rel_diff_max": float(ferr.max())}))
 
 
+def run_amr_core(args):
+    """Collapsing-core AMR grid (~1.9 M leaves of 8^3 blocks on levels 5-9, 10 stars of
+    1e2-1e5 Lsun, optically thick centre): evaluation throughput with the step as in the
+    main bench, then the plain GPU fixed point of T_d and the IR field to 1e-4 from
+    T_d = 20 K; when it does not converge, the largest relative change per iteration."""
+    import numpy as np
+    import torch
+
+    import paper_2204_09072_gb300 as tr
+    import synth
+    dev = torch.device("cuda:0")
+    t0 = time.perf_counter()
+    w = synth.amr_core()
+    t_gen = time.perf_counter() - t0
+    n = w.n_leaves
+    npix = w.params["npix"]
+    ctx = tr.Context(w.params)
+    st = torch.cuda.Stream(device=dev)
+    rho = torch.as_tensor(w.rho, device=dev)
+    td0 = torch.as_tensor(w.td, device=dev)
+    tgas = torch.as_tensor(w.tgas, device=dev)
+    J = torch.empty(n, dtype=torch.float32, device=dev)
+    F = torch.empty(3 * n, dtype=torch.float64, device=dev)
+    u = torch.empty(n, device=dev)
+    a_rp = torch.empty(3 * n, device=dev)
+    force = torch.empty(3 * n, device=dev)
+    p_src = torch.empty(n, device=dev)
+    Td = torch.empty(n, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def build():
+        ctx.build(w.box_cm, rho, td0, blocks=w.blocks, star_pos=w.star_pos, star_lum=w.star_lum, stream=st)
+
+    with torch.cuda.stream(st):
+        build()
+        best, tune = ctx.autotune(65536, stream=st)
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps + args.warmup)]
+        for k in range(args.steps + args.warmup):
+            flush.zero_()
+            e = ev[k]
+            e[0].record(st)
+            build()
+            e[1].record(st)
+            ctx.evaluate(J, F, stream=st)
+            e[2].record(st)
+            ctx.radpressure(J, F, u, a_rp, force, p_src, stream=st)
+            ctx.dust_temperature(tgas, J, Td, stream=st)
+            e[3].record(st)
+        torch.cuda.synchronize()
+        ctx.check(st)
+        tot = ctx.walk_stats(stream=st).cpu().numpy().astype(np.int64)
+    ev = ev[args.warmup:]
+    ms_step = statistics.mean(e[0].elapsed_time(e[3]) for e in ev)
+    ms_eval = statistics.mean(e[1].elapsed_time(e[2]) for e in ev)
+    visits, acc, ent = (int(x) for x in tot)
+    alg = BYTES_VISIT * visits + BYTES_ACCEPT * (acc - n) + BYTES_ENTRY * ent + BYTES_TARGET * n
+    peak, kind = measured_peak()
+    # plain GPU fixed point (graph of unrolled iterations)
+    ctx.refresh(td0)
+    td = td0.clone()
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record()
+    it = ctx.fixed_point(tgas, td, tol=1e-4, max_iter=args.fp_max_iter, raise_on_noconv=False)
+    f1.record()
+    torch.cuda.synchronize()
+    ms_fp = f0.elapsed_time(f1)
+    out = {
+        "workload": f"amr_core: collapsing-core AMR, {n} leaves, levels {sorted(set(np.asarray(w.leaf_level).tolist()))}, "
+                    f"{len(w.star_lum)} stars, N_pix {npix}, {w.params['nbins']} segments",
+        "s_generate": t_gen, "warps_per_target": best, "autotune_ms_wpt2_4_8": tune,
+        "ms_per_step": ms_step, "ms_evaluate": ms_eval,
+        "ray_evals_per_s": n * npix / (ms_step * 1e-3), "ray_evals_per_s_evaluate": n * npix / (ms_eval * 1e-3),
+        "roofline": {"bound": "hbm", "achieved": alg / (ms_eval * 1e-3) / 1e9, "peak": peak, "peak_kind": kind,
+                     "frac": alg / (ms_eval * 1e-3) / 1e9 / peak, "algorithmic_bytes_per_launch": alg},
+        "walk": {"visits": visits, "accepted": acc, "alpha_entries": ent},
+        "fixed_point": {"tol": 1e-4, "iterations": it, "converged": it > 0, "ms": ms_fp,
+                        "Td_min": float(td.min()), "Td_max": float(td.max())},
+    }
+    if it <= 0:
+        # one iteration at a time: the largest relative change and where it sits
+        ctx.refresh(td0)
+        td = td0.clone()
+        hist = []
+        for _ in range(args.fp_diag_iter):
+            prev = td.clone()
+            ctx.fixed_point(tgas, td, tol=1e-30, max_iter=1, unroll=0, raise_on_noconv=False)
+            ch = (td / prev - 1).abs()
+            k = int(torch.argmax(ch))
+            hist.append([float(ch[k]), k, float(prev[k]), float(td[k]), float(rho[k])])
+        out["fixed_point"]["history_max_change_cell_T_before_after_rho"] = hist
+    ctx.close()
+    print(json.dumps(out))
+
+
 def run_profile(args):
     """Profiling driver for ncu: build the full tree once, then launch the evaluate
     kernel on a seeded subset of targets: two warm-up launches, then one more."""
@@ -620,6 +715,10 @@ def main():
     ap.add_argument("--warmstart", action="store_true", help="learned warm start of the T_d fixed point")
     ap.add_argument("--warm-n", type=int, default=256)
     ap.add_argument("--train-steps", type=int, default=4000)
+    ap.add_argument("--amr-core", action="store_true",
+                    help="collapsing-core AMR grid: throughput and the plain fixed point to 1e-4")
+    ap.add_argument("--fp-max-iter", type=int, default=100)
+    ap.add_argument("--fp-diag-iter", type=int, default=20)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
@@ -631,6 +730,8 @@ def main():
         run_sweep(args)
     elif args.warmstart:
         run_warmstart(args)
+    elif args.amr_core:
+        run_amr_core(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -33,3 +33,23 @@ def test_weak_coupling_cools_to_floor(orc):
     td, it, _ = orc.fixed_point(w, tgas, w.td, max_iter=50, tol=1e-5)
     assert it > 0
     assert np.allclose(td, 2.7, rtol=1e-6)
+
+
+def test_thick_cells_under_outside_heating_do_not_settle(orc):
+    """The own segment of a target has no optical depth (eqs. tauthin and opt thick at
+    i = 0), so a thick cell's own emission gives it J = sigma T^4 / pi (App. B) while all
+    outside radiation still arrives: its radiative cooling is cancelled and only the
+    weak gas coupling can balance the heating. The same box with thin dust settles in a
+    few iterations; with thick dust the iteration keeps heating."""
+    runs = {}
+    for kappa0 in (10.0, 0.1):  # tau_b ~ 3 and ~ 0.03 per cell
+        w = synth.point_source(8, box_pc=0.1, rho0=7.7e-18, kappa0=kappa0, lum_lsun=1e3)
+        w.params = dict(w.params, dust_emission=1)
+        tgas = np.full(w.n_leaves, 20.0, np.float32)
+        td0 = np.full(w.n_leaves, 20.0, np.float32)
+        runs[kappa0] = orc.fixed_point(w, tgas, td0, max_iter=40, tol=1e-4)
+    td, it, hist = runs[0.1]
+    assert 0 < it <= 10
+    td, it, hist = runs[10.0]
+    assert it < 0  # not converged after 40 iterations
+    assert min(hist[-10:]) > 1e-3
