@@ -456,10 +456,13 @@ def run_warmstart(args):
     import numpy as np  # noqa: F401  (used by _cloud)
     """Learned warm start of the dust-temperature fixed point.
 
-    Training: plain fixed points (tol 1e-4) of five seeded 128^3 clouds (sigma_lnrho 1.5
-    and 2, 1-4 stars with ionising fields), features taken at their initial T_d: ~1e7
-    samples. Test: a 256^3 cloud (sigma_lnrho 2, 4 stars, ionising field, seed 777), plain
-    fixed point from T_d ~ U[10, 40] K against features -> network -> fixed point."""
+    Training: plain fixed points (tol 1e-4) of seven seeded 128^3 clouds (sigma_lnrho 1.5
+    and 2, 1-4 stars with ionising fields) and --warm-train-big clouds at the test size
+    (sigma_lnrho 2, 4 stars, seeds 200, 201, ...); the features come from one evaluation
+    at a uniform reference T_d (--warm-feature-td), so that they depend on the cloud alone
+    and not on the random initial T_d; solves that do not converge are left out. Test: a --warm-n^3 cloud (sigma_lnrho 2, 4
+    stars, ionising field, seed 777), plain fixed point from T_d ~ U[10, 40] K against
+    features -> network -> fixed point."""
     import torch
 
     import paper_2204_09072_gb300 as tr
@@ -476,10 +479,13 @@ def run_warmstart(args):
 
     t0 = time.perf_counter()
     Xs, ys, its = [], [], []
-    for k, (seed, sig, ns) in enumerate([(101, 1.5, 1), (102, 2.0, 2), (103, 1.5, 4), (104, 2.0, 3), (105, 2.0, 4),
-                                         (106, 2.0, 4), (107, 1.5, 2)]):
-        w = _cloud(128, seed, sig, ns, args.npix)
+    solves = [(128, 101, 1.5, 1), (128, 102, 2.0, 2), (128, 103, 1.5, 4), (128, 104, 2.0, 3), (128, 105, 2.0, 4),
+              (128, 106, 2.0, 4), (128, 107, 1.5, 2)]
+    solves += [(args.warm_n, 200 + k, 2.0, 4) for k in range(args.warm_train_big)]
+    for k, (nn, seed, sig, ns) in enumerate(solves):
+        w = _cloud(nn, seed, sig, ns, args.npix)
         c, tg, he, ph = make(w)
+        c.refresh(torch.full((w.n_leaves,), args.warm_feature_td, device=dev))
         X = c.features(tg, phi=ph)[0].clone()
         td = torch.as_tensor(w.td, device=dev).clone()
         it = c.fixed_point(tg, td, heat_extra=he, tol=1e-4, max_iter=60, raise_on_noconv=False)
@@ -509,10 +515,10 @@ def run_warmstart(args):
     it_plain = c.fixed_point(tg, td_plain, heat_extra=he, tol=1e-4, max_iter=60, raise_on_noconv=False)
     e[1].record()
     torch.cuda.synchronize()
-    c.refresh(td0)
     td_warm = td0.clone()
     torch.cuda.synchronize()
     e[2].record()
+    c.refresh(torch.full_like(td0, args.warm_feature_td))
     Xw = c.features(tg, phi=ph)[0]
     c.warm_start(net, Xw.reshape(-1).contiguous(), td_warm)
     guess = td_warm.clone()
@@ -524,9 +530,11 @@ def run_warmstart(args):
     ms_warm = e[2].elapsed_time(e[3])
     gerr = (guess / td_plain - 1).abs()
     ferr = (td_warm / td_plain - 1).abs()
+    gq = torch.quantile(gerr[torch.randperm(gerr.numel(), device=gerr.device)[:1 << 22]],
+                        torch.tensor([0.5, 0.9, 0.99, 0.999], device=gerr.device)).tolist()
     print(json.dumps({
         "workload": f"learned warm start, test cloud {args.warm_n}^3 sigma_lnrho 2, 4 stars, ionising flux "
-                    "as a feature (no UV dust heating)",
+                    f"as a feature (no UV dust heating); features at uniform T_d = {args.warm_feature_td} K",
         "train_samples": int(y.numel()), "train_solves_iterations": its, "train_steps": len(hist) + len(hist2),
         "train_loss_first_last": [float(hist[:20].mean()), float(hist2[-50:].mean())],
         "s_training_data": t_data, "s_training": t_train,
@@ -535,6 +543,7 @@ def run_warmstart(args):
         "evaluation_ratio": it_plain / (it_warm + 1),
         "ms_fixed_point_plain": ms_plain, "ms_warm_total": ms_warm, "speedup": ms_plain / ms_warm,
         "guess_rel_err_max": float(gerr.max()), "guess_rel_err_median": float(gerr.median()),
+        "guess_rel_err_p50_p90_p99_p999": gq, "training_solves": [list(x) for x in solves],
         "final_rel_diff_max": float(ferr.max())}))
 
 
@@ -715,6 +724,10 @@ def main():
     ap.add_argument("--warmstart", action="store_true", help="learned warm start of the T_d fixed point")
     ap.add_argument("--warm-n", type=int, default=256)
     ap.add_argument("--train-steps", type=int, default=4000)
+    ap.add_argument("--warm-feature-td", type=float, default=20.0,
+                    help="uniform T_d of the feature pass (training and test)")
+    ap.add_argument("--warm-train-big", type=int, default=2,
+                    help="training solves at the test resolution (seeds 200, 201, ...)")
     ap.add_argument("--amr-core", action="store_true",
                     help="collapsing-core AMR grid: throughput and the plain fixed point to 1e-4")
     ap.add_argument("--fp-max-iter", type=int, default=100)
