@@ -69,6 +69,12 @@ typedef enum {
  *  kappa_ext_scale multiplies the extinction areas A~ (1 = the method; 0 = test switch).
  *  alpha_s         sub-cube samples per axis of the angular kernel, a multiple of 4
  *                  (8 is the default, 512 samples per node position).
+ *  periodic        bit a (x = 1, y = 2, z = 4) set: axis a is periodic. Every node then
+ *                  enters at its closest periodic copy (Sec. 4.2, periodic boundaries); a
+ *                  node exactly half a box away on such an axis has two closest copies and
+ *                  enters at both, each with weight 1/2. R_max becomes the largest
+ *                  closest-copy distance, sqrt of the sum over axes of (box/2)^2 on
+ *                  periodic and box^2 on isolated axes. 0 (all isolated) is the default.
  */
 typedef struct {
     int npix;
@@ -80,6 +86,7 @@ typedef struct {
     int dust_emission;
     double kappa_ext_scale;
     int alpha_s;
+    int periodic;
 } treeray_params;
 
 /*

@@ -68,6 +68,7 @@ typedef struct {
     int dust_emission;     /* 0 switches dust re-emission off (point-source benchmark) */
     double kappa_ext_scale;/* scales the extinction areas A~ (test switch) */
     int alpha_s;           /* sub-points per axis of the angular kernel's sampling */
+    int periodic;          /* bit a set: axis a is periodic (nearest copies, Sec. 4.2) */
 } or_params;
 
 /* ------------------------------------------------------------------ HEALPix
@@ -644,10 +645,38 @@ int or_build(const or_params* p, int lmax, double box_cm, int64_t nleaves,
  * Reading: R_0 = Et / 2 (half the target cell), R_i = R_0 (R_max / R_0)^(i / N) with
  * R_max = sqrt(3) x box edge (geometric spacing). Segment i is [R_i, R_(i+1)); segment
  * 0 also holds [0, R_0); nodes beyond R_(N-1) fall into the last segment. */
-static void or_radii(int nbins, int lmax, int64_t Et, double* R) {
+static void or_radii(int nbins, int lmax, int periodic, int64_t Et, double* R) {
     double R0 = 0.5 * (double)Et;
-    double Rmax = sqrt(3.0) * (double)((int64_t)2 << lmax);
+    double B = (double)((int64_t)2 << lmax);
+    double Rmax = sqrt(3.0) * B;
+    if (periodic) { /* largest nearest-copy distance: half the box on periodic axes */
+        double s = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            double e = ((periodic >> a) & 1) ? 0.5 * B : B;
+            s += e * e;
+        }
+        Rmax = sqrt(s);
+    }
     for (int i = 0; i <= nbins; ++i) R[i] = R0 * pow(Rmax / R0, (double)i / (double)nbins);
+}
+
+/* Offset from the target to the closest periodic copy of a node (Sec. 4.2: "only the
+ * closest ones are considered"): on a periodic axis the offset is brought into
+ * [-B/2, B/2], B the box edge in half-units. An offset of exactly B/2 has two closest
+ * copies, at +B/2 and -B/2; the returned mask marks those axes (reading: both copies
+ * count, each with weight 1/2 per such axis). */
+static int or_nearest(const or_tree* t, const or_node* nd, const or_node* tn, int64_t* o) {
+    int64_t B = (int64_t)2 << t->lmax, half = B / 2;
+    int ties = 0;
+    for (int a = 0; a < 3; ++a) {
+        o[a] = nd->c[a] - tn->c[a];
+        if ((t->p.periodic >> a) & 1) {
+            if (o[a] > half) o[a] -= B;
+            else if (o[a] < -half) o[a] += B;
+            if (o[a] == half || o[a] == -half) ties |= 1 << a;
+        }
+    }
+    return ties;
 }
 
 static int or_bin(int nbins, const double* R, double d2) {
@@ -674,9 +703,10 @@ typedef struct {
  *          V^ += alpha V,       Q^ += alpha beta V
  * Thick material whose radial extent [d - sqrt3/2 E, d + sqrt3/2 E] crosses
  * segment boundaries flags those boundaries for merging (Sec. 4.3).
+ * w: weight of this copy of the node (1, or 1/2 per axis with two closest copies).
  */
 static void or_map_node(const or_tree* t, or_alpha_table* at, const or_node* nd, const int64_t* o,
-                        int64_t d2, const double* R, or_rays* ry, int* err) {
+                        int64_t d2, const double* R, or_rays* ry, double w) {
     int nb = ry->nbins, np = ry->npix;
     double u = t->u;
     int i = or_bin(nb, R, (double)d2);
@@ -693,7 +723,6 @@ static void or_map_node(const or_tree* t, or_alpha_table* at, const or_node* nd,
     int64_t K[3] = {0, 0, 0};
     const int* lst = NULL;
     int owned = 0;
-    (void)err;
     if (!own) {
         or_key(o, nd->E, K);
         lst = or_alpha_get(at, K, &owned);
@@ -708,8 +737,9 @@ static void or_map_node(const or_tree* t, or_alpha_table* at, const or_node* nd,
             if (dn <= 0.0 || (double)d2 >= dn * dn) ihi = j;
         }
     }
-    /* values in CGS: luminosities erg/s, areas cm^2, volumes cm^3 */
-    double Lt = nd->Lt, At = nd->At, LVk = nd->LVk, Ak = nd->Ak, Vk = nd->Vk;
+    /* values in CGS: luminosities erg/s, areas cm^2, volumes cm^3; w < 1 for one of
+     * several closest periodic copies */
+    double Lt = w * nd->Lt, At = w * nd->At, LVk = w * nd->LVk, Ak = w * nd->Ak, Vk = w * nd->Vk;
     (void)u;
     int n = own ? np : 0;
     if (!own)
@@ -832,7 +862,7 @@ int or_evaluate(or_tree* t, int64_t ntargets, const int64_t* targets, double* J,
             const or_node* tn = &t->nodes[t->leaf_node[leaf]];
             memset(buf, 0, sizeof(double) * 6 * cells);
             memset(ry.flag, 0, sizeof(uint64_t) * np);
-            or_radii(nb, t->lmax, tn->E, R);
+            or_radii(nb, t->lmax, p->periodic, tn->E, R);
             for (int i = 0; i <= nb; ++i) Rcm[i] = R[i] * t->u;
             int sp = 0;
             stack[sp++] = 0;
@@ -842,8 +872,8 @@ int or_evaluate(or_tree* t, int64_t ntargets, const int64_t* targets, double* J,
                 int64_t o[3];
                 int64_t d2 = 0;
                 int inside = 1;
+                int ties = or_nearest(t, nd, tn, o);
                 for (int a = 0; a < 3; ++a) {
-                    o[a] = nd->c[a] - tn->c[a];
                     d2 += o[a] * o[a];
                     int64_t ao = o[a] < 0 ? -o[a] : o[a];
                     if (2 * ao >= nd->E) inside = 0;
@@ -855,8 +885,19 @@ int or_evaluate(or_tree* t, int64_t ntargets, const int64_t* targets, double* J,
                 }
                 if (open) {
                     for (int k = 7; k >= 0; --k) stack[sp++] = nd->child[k];
-                } else {
-                    or_map_node(t, &t->alpha, nd, o, d2, R, &ry, &myerr);
+                } else if (!ties) {
+                    or_map_node(t, &t->alpha, nd, o, d2, R, &ry, 1.0);
+                } else { /* every closest copy, 1/2 per tied axis */
+                    int nt = ((ties & 1) != 0) + ((ties & 2) != 0) + ((ties & 4) != 0);
+                    double w = 1.0 / (double)(1 << nt);
+                    int64_t half = (int64_t)1 << t->lmax;
+                    for (int m = 0; m < 8; ++m) {
+                        if (m & ~ties) continue;
+                        int64_t oi[3];
+                        for (int a = 0; a < 3; ++a)
+                            oi[a] = ((ties >> a) & 1) ? (((m >> a) & 1) ? half : -half) : o[a];
+                        or_map_node(t, &t->alpha, nd, oi, d2, R, &ry, w);
+                    }
                 }
             }
             /* integrate every ray in CGS */
@@ -1022,12 +1063,12 @@ int64_t or_accepted(const or_tree* t, int64_t leaf, int32_t* ids, int64_t cap) {
     while (sp > 0) {
         int id = stack[--sp];
         const or_node* nd = &t->nodes[id];
-        int64_t d2 = 0;
+        int64_t d2 = 0, o[3];
         int inside = 1;
+        or_nearest(t, nd, tn, o);
         for (int a = 0; a < 3; ++a) {
-            int64_t o = nd->c[a] - tn->c[a];
-            d2 += o * o;
-            if (2 * (o < 0 ? -o : o) >= nd->E) inside = 0;
+            d2 += o[a] * o[a];
+            if (2 * (o[a] < 0 ? -o[a] : o[a]) >= nd->E) inside = 0;
         }
         int open = nd->leaf < 0 && (inside || (double)(nd->E * nd->E) >= th2 * (double)d2);
         if (open) {
@@ -1056,8 +1097,8 @@ void or_walk_stats(or_tree* t, int64_t leaf, int64_t* out) {
         ++visits;
         int64_t o[3], d2 = 0;
         int inside = 1;
+        int ties = or_nearest(t, nd, tn, o);
         for (int a = 0; a < 3; ++a) {
-            o[a] = nd->c[a] - tn->c[a];
             d2 += o[a] * o[a];
             if (2 * (o[a] < 0 ? -o[a] : o[a]) >= nd->E) inside = 0;
         }
@@ -1067,14 +1108,20 @@ void or_walk_stats(or_tree* t, int64_t leaf, int64_t* out) {
         } else {
             ++acc;
             if (d2 != 0) {
-                int64_t K[3];
-                int owned = 0;
-                or_key(o, nd->E, K);
-                const int* l = or_alpha_get(&t->alpha, K, &owned);
-                int n = 0;
-                while (l[2 * n] >= 0) ++n;
-                ent += n;
-                if (owned) free((void*)l);
+                int64_t half = (int64_t)1 << t->lmax;
+                for (int m = 0; m < 8; ++m) { /* entries of every closest copy */
+                    if (m & ~ties) continue;
+                    int64_t oi[3], K[3];
+                    for (int a = 0; a < 3; ++a)
+                        oi[a] = ((ties >> a) & 1) ? (((m >> a) & 1) ? half : -half) : o[a];
+                    int owned = 0;
+                    or_key(oi, nd->E, K);
+                    const int* l = or_alpha_get(&t->alpha, K, &owned);
+                    int n = 0;
+                    while (l[2 * n] >= 0) ++n;
+                    ent += n;
+                    if (owned) free((void*)l);
+                }
             }
         }
     }
@@ -1085,7 +1132,7 @@ void or_walk_stats(or_tree* t, int64_t leaf, int64_t* out) {
 
 /* Evaluation radii R_i (half-units) for a target leaf. */
 void or_target_radii(const or_tree* t, int64_t leaf, double* R) {
-    or_radii(t->p.nbins, t->lmax, t->nodes[t->leaf_node[leaf]].E, R);
+    or_radii(t->p.nbins, t->lmax, t->p.periodic, t->nodes[t->leaf_node[leaf]].E, R);
 }
 
 /* alpha key for an offset o and node edge E. */

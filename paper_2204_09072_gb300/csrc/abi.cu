@@ -81,7 +81,7 @@ treeray_status upload_tables(treeray_ctx* c, cudaStream_t s) {
         omax[lv] = x;
     }
     for (int lt = 0; lt <= L; ++lt) {
-        radii(nb, L, (int64_t)2 << (L - lt), R.data());
+        radii(nb, L, c->p.periodic, (int64_t)2 << (L - lt), R.data());
         lvlp[lt] = make_float2((float)(1.0 / (R[0] * R[0])),
                                (float)(0.5 * nb / std::log2(R[nb] / R[0])));
         for (int i = 0; i < nb; ++i) {
@@ -161,6 +161,10 @@ treeray_status treeray_create(const treeray_params* p, treeray_t* out) {
     }
     if (p->alpha_s < 4 || p->alpha_s > 16 || p->alpha_s % 4 != 0) {
         set_error("alpha_s must be 4, 8, 12 or 16");
+        return TREERAY_EINVAL;
+    }
+    if (p->periodic < 0 || p->periodic > 7) {
+        set_error("periodic must be a mask of axes in 0..7");
         return TREERAY_EINVAL;
     }
     treeray_ctx* c = new (std::nothrow) treeray_ctx();

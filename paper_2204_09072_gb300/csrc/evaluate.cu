@@ -60,6 +60,8 @@ struct __align__(16) EvalArgs {
     int64_t n;
     int64_t nleaves;
     int lmax, nbins, D, stack_cap, npix;
+    int periodic;  // bit a: axis a periodic (closest copies)
+    float inv_s3;  // 1 / alpha_s^3: weight of one sub-cube sample of the angular kernel
     double u;
     double inv_u2;  // 1 / u^2: flux unit = L_scale / u^2 (L_scale a power of two)
 };
@@ -96,6 +98,19 @@ __device__ __forceinline__ float small_int_to_float(int v) {  // exact for |v| <
 }
 __device__ __forceinline__ float count_to_float(uint32_t v) {  // exact for v < 2^23
     return __uint_as_float(0x4B000000u | v) - 8388608.0f;
+}
+
+// Closest periodic copy on one axis (Sec. 4.2): the offset o (half-cells) is brought into
+// [-half, half], half = half the box; an offset of exactly +-half has two closest copies
+// and sets `bit` in `ties`.
+__device__ __forceinline__ int closest_copy(int o, int half, int bit, int& ties) {
+    if (o > half) o -= 2 * half;
+    else if (o < -half) o += 2 * half;
+    if (o == half || o == -half) ties |= bit;
+    return o;
+}
+__device__ __forceinline__ int copy_offset(int o, int ties, int bit, int m, int half) {
+    return (ties & bit) ? ((m & bit) ? half : -half) : o;
 }
 
 // Error-free transformations (Knuth's TwoSum; the FMA residual of a product), written
@@ -166,12 +181,19 @@ __global__ void __launch_bounds__(256) k_walk_list(EvalArgs a) {
             int4 gg = make_int4(0, 0, 0, 0);
             int ox = 0, oy = 0, oz = 0, lvl = 0;
             int64_t d2 = 0;
+            int ties = 0;
             if (valid) {
                 gg = __ldg(a.geo + node);
                 lvl = gg.z >> 24;
                 ox = gg.x - tx;
                 oy = gg.y - ty;
                 oz = (gg.z & 0xffffff) - tz;
+                if (a.periodic) {
+                    const int half = 1 << a.lmax;
+                    if (a.periodic & 1) ox = closest_copy(ox, half, 1, ties);
+                    if (a.periodic & 2) oy = closest_copy(oy, half, 2, ties);
+                    if (a.periodic & 4) oz = closest_copy(oz, half, 4, ties);
+                }
                 d2 = (int64_t)ox * ox + (int64_t)oy * oy + (int64_t)oz * oz;
                 if (gg.w >= 0) {
                     const int E = 2 << (a.lmax - lvl);
@@ -199,10 +221,16 @@ __global__ void __launch_bounds__(256) k_walk_list(EvalArgs a) {
             nvis += __popc(__ballot_sync(full, valid));
             if (a.stats && acc && d2 != 0) {
                 const int elog = a.lmax - lvl + 1;
-                const int Kx = alpha_key(ox, elog), Ky = alpha_key(oy, elog), Kz = alpha_key(oz, elog);
-                if (abs(Kx) <= a.D && abs(Ky) <= a.D && abs(Kz) <= a.D) {
-                    const int idx = ((Kz + a.D) * W + (Ky + a.D)) * W + (Kx + a.D);
-                    nent += __ldg(a.aoff + idx + 1) - __ldg(a.aoff + idx);
+                const int half = 1 << a.lmax;
+                for (int m = 0; m < 8; ++m) {  // entries of every closest copy
+                    if (m & ~ties) continue;
+                    const int qx = copy_offset(ox, ties, 1, m, half), qy = copy_offset(oy, ties, 2, m, half),
+                              qz = copy_offset(oz, ties, 4, m, half);
+                    const int Kx = alpha_key(qx, elog), Ky = alpha_key(qy, elog), Kz = alpha_key(qz, elog);
+                    if (abs(Kx) <= a.D && abs(Ky) <= a.D && abs(Kz) <= a.D) {
+                        const int idx = ((Kz + a.D) * W + (Ky + a.D)) * W + (Kx + a.D);
+                        nent += __ldg(a.aoff + idx + 1) - __ldg(a.aoff + idx);
+                    }
                 }
             }
         }
@@ -230,6 +258,74 @@ constexpr int kOwnerCap = 256;  // entries per warp and walk step spread one per
 // small enough for 64 warps per SM; larger tiles are limited by shared memory anyway.
 constexpr int min_warps_per_sm(int npix, bool thick) { return thick ? 24 : (npix <= 48 ? 64 : 48); }
 
+// Deposit of an accepted node whose closest periodic copies are tied (it lies exactly half
+// a box away on a periodic axis): every closest copy, with weight 1/2 per tied axis, by the
+// node's own thread with shared-memory atomics. The copies share |offset| per axis, hence
+// d^2, the segment and the straddled boundaries; alpha and beta differ. Such nodes lie on
+// the planes half a box from the target, so this path is rare.
+template <int NPIX, bool THICK>
+__device__ __noinline__ void deposit_tied_copies(const EvalArgs& A, float* tL, float* tA, float* tLk, float* tAk,
+                                                 float* tVk, float* tQk, unsigned long long* flags, int node,
+                                                 int ox, int oy, int oz, int ties, int lvl, int64_t d2, int tl,
+                                                 float2 lp) {
+    const int nb = A.nbins;
+    const int64_t* thr = A.bin_thr + (int64_t)tl * nb;
+    const float* R2 = A.R2 + (int64_t)tl * nb;
+    const int W = 2 * A.D + 1;
+    const int half = 1 << A.lmax;
+    const float inv_s3 = A.inv_s3;
+    const float wt = 1.0f / (float)(1 << __popc(ties));
+    const float4 v0 = __ldg(A.thin + node);
+    const float4 v1 = __ldg(A.thick + node);
+    const float fd2 = (float)d2;
+    const int i = fixup(guess_bin(fd2, lp), d2, thr, nb);
+    unsigned long long fmask = 0ull;
+    if (THICK && v1.w > 0.0f) {
+        const int64_t* lo = A.str_lo + ((int64_t)tl * (A.lmax + 1) + lvl) * nb;
+        const int64_t* hi = A.str_hi + ((int64_t)tl * (A.lmax + 1) + lvl) * nb;
+        const float d = sqrtf(fd2);
+        const float sd = 0.8660254f * (float)(2 << (A.lmax - lvl));
+        const float dl = fmaxf(d - sd, 0.0f), dh = d + sd;
+        const int ilo = fixup(guess_bin(dl * dl, lp), d2, lo, nb);
+        const int ihi = fixup(guess_bin(dh * dh, lp), d2, hi, nb);
+        for (int j = ilo; j < ihi; ++j) fmask |= 1ull << j;
+    }
+    const int elog = A.lmax - lvl + 1;
+    for (int m = 0; m < 8; ++m) {
+        if (m & ~ties) continue;
+        const int qx = copy_offset(ox, ties, 1, m, half), qy = copy_offset(oy, ties, 2, m, half),
+                  qz = copy_offset(oz, ties, 4, m, half);
+        const float rx = small_int_to_float(qx) + v0.z, ry = small_int_to_float(qy) + v0.w,
+                    rz = small_int_to_float(qz) + v1.x;
+        const float beta = __ldg(R2 + i) / (rx * rx + ry * ry + rz * rz);
+        const int Kx = alpha_key(qx, elog), Ky = alpha_key(qy, elog), Kz = alpha_key(qz, elog);
+        if (abs(Kx) > A.D || abs(Ky) > A.D || abs(Kz) > A.D) {
+            atomicOr(A.err, kErrAlphaKey);
+            continue;
+        }
+        const int idx = ((Kz + A.D) * W + (Ky + A.D)) * W + (Kx + A.D);
+        const int e0 = __ldg(A.aoff + idx), e1 = __ldg(A.aoff + idx + 1);
+        if (e1 == e0) atomicOr(A.err, kErrAlphaKey);
+        const float bL = beta * v0.x * inv_s3 * wt, bA = beta * v0.y * inv_s3 * wt;
+        for (int e = e0; e < e1; ++e) {
+            const uint32_t ent = __ldg(A.aent + e);
+            const int h = (int)(ent & 0xffffu);
+            const int c = i * NPIX + h;
+            const float w = count_to_float(ent >> 16);
+            atomicAdd(tL + c, w * bL);
+            atomicAdd(tA + c, w * bA);
+            if (THICK && v1.w > 0.0f) {
+                const float wn = w * inv_s3;
+                atomicAdd(tLk + c, wn * v1.y * wt);
+                atomicAdd(tAk + c, v1.z * wt);
+                atomicAdd(tVk + c, wn * v1.w * wt);
+                atomicAdd(tQk + c, wn * beta * v1.w * wt);
+                if (fmask) atomicOr(flags + h, fmask);
+            }
+        }
+    }
+}
+
 // Evaluation kernel: a team of WPT warps per target shares one walk stack (its block's
 // slice of a global scratch array, L1-resident) and one (segment x ray) tile in shared
 // memory; the block processes one target at a time and takes the next from a global
@@ -244,7 +340,7 @@ constexpr int min_warps_per_sm(int npix, bool thick) { return thick ? 24 : (npix
 //   rays:    threads integrate the rays' segments inside out (thin tiles with spare
 //            threads cut each ray into consecutive parts joined by their transmission),
 //            then the team reduces J and F.
-template <int NPIX, bool THICK, int WPT>
+template <int NPIX, bool THICK, int WPT, bool PERIODIC>
 __global__ void __launch_bounds__(WPT * 32, min_warps_per_sm(NPIX, THICK) / WPT)
     k_evaluate(EvalArgs a, const EvalArgs* __restrict__ boxes, const int64_t* __restrict__ box_start, int nbox) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -276,7 +372,6 @@ __global__ void __launch_bounds__(WPT * 32, min_warps_per_sm(NPIX, THICK) / WPT)
     const unsigned full = 0xffffffffu;
     const unsigned lt_mask = (1u << lane) - 1u;
     const float omega = (float)(4.0 * kPi / NPIX);
-    const float inv_s3 = 1.0f / 512.0f;
     if (a.skip && *a.skip) return;
     // the per-box descriptor lives in shared memory: copied once (one box) or per target (a
     // batch of boxes whose targets share one work counter)
@@ -368,12 +463,19 @@ __global__ void __launch_bounds__(WPT * 32, min_warps_per_sm(NPIX, THICK) / WPT)
             int4 gg = make_int4(0, 0, 0, 0);
             int ox = 0, oy = 0, oz = 0, lvl = 0;
             int64_t d2 = 0;
+            int ties = 0;
             if (valid) {
                 gg = __ldg(A.geo + node);
                 lvl = gg.z >> 24;
                 ox = gg.x - tx;
                 oy = gg.y - ty;
                 oz = (gg.z & 0xffffff) - tz;
+                if (PERIODIC && A.periodic) {
+                    const int half = 1 << A.lmax;
+                    if (A.periodic & 1) ox = closest_copy(ox, half, 1, ties);
+                    if (A.periodic & 2) oy = closest_copy(oy, half, 2, ties);
+                    if (A.periodic & 4) oz = closest_copy(oz, half, 4, ties);
+                }
                 d2 = (int64_t)ox * ox + (int64_t)oy * oy + (int64_t)oz * oz;
                 if (gg.w >= 0) {
                     const int E = 2 << (A.lmax - lvl);
@@ -399,7 +501,10 @@ __global__ void __launch_bounds__(WPT * 32, min_warps_per_sm(NPIX, THICK) / WPT)
             // of one segment); thick deposits stay with the node's thread.
             int ne = 0, ebase = 0, cbase = 0;
             float bL = 0.0f, bA = 0.0f;
-            if (acc) {
+            if (PERIODIC && acc && ties) {
+                deposit_tied_copies<NPIX, THICK>(A, tL, tA, tLk, tAk, tVk, tQk, flags, node, ox, oy, oz, ties, lvl,
+                                                 d2, tl, lp);
+            } else if (acc) {
                 // the float distance only guesses the segment; the integer d^2 decides it
                 const float fx = small_int_to_float(ox), fy = small_int_to_float(oy), fz = small_int_to_float(oz);
                 const float fd2 = fx * fx + fy * fy + fz * fz;
@@ -419,8 +524,8 @@ __global__ void __launch_bounds__(WPT * 32, min_warps_per_sm(NPIX, THICK) / WPT)
                     ne = e1 - e0;
                     ebase = e0;
                     cbase = i * NPIX;
-                    bL = beta * v0.x * inv_s3;
-                    bA = beta * v0.y * inv_s3;
+                    bL = beta * v0.x * A.inv_s3;
+                    bA = beta * v0.y * A.inv_s3;
                     if (THICK && v1.w > 0.0f) {
                         const int64_t* lo = A.str_lo + ((int64_t)tl * (A.lmax + 1) + lvl) * nb;
                         const int64_t* hi = A.str_hi + ((int64_t)tl * (A.lmax + 1) + lvl) * nb;
@@ -435,7 +540,7 @@ __global__ void __launch_bounds__(WPT * 32, min_warps_per_sm(NPIX, THICK) / WPT)
                             const uint32_t ent = __ldg(A.aent + e);
                             const int h = (int)(ent & 0xffffu);
                             const int cidx = i * NPIX + h;
-                            const float wn = count_to_float(ent >> 16) * inv_s3;
+                            const float wn = count_to_float(ent >> 16) * A.inv_s3;
                             atomicAdd(tLk + cidx, wn * v1.y);
                             atomicAdd(tAk + cidx, v1.z);
                             atomicAdd(tVk + cidx, wn * v1.w);
@@ -713,7 +818,7 @@ size_t stack_bytes_for(int wpt, int lmax, int blocks) {
     return (size_t)blocks * (size_t)(32 * wpt * (lmax + 1) + 64) * sizeof(int);
 }
 
-template <int NPIX, bool THICK, int WPT>
+template <int NPIX, bool THICK, int WPT, bool PERIODIC>
 treeray_status launch_team(treeray_ctx* c, const EvalArgs& a, const EvalArgs* boxes,
                            const int64_t* box_start, int nbox, int layout_lmax, cudaStream_t s) {
     constexpr int nq = THICK ? 6 : 2;
@@ -727,7 +832,7 @@ treeray_status launch_team(treeray_ctx* c, const EvalArgs& a, const EvalArgs* bo
         set_error("evaluate: the per-target ray tile (npix x nbins) exceeds shared memory");
         return TREERAY_EINVAL;
     }
-    auto kern = k_evaluate<NPIX, THICK, WPT>;
+    auto kern = k_evaluate<NPIX, THICK, WPT, PERIODIC>;
     TR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     TR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WPT * 32, smem));
@@ -749,35 +854,43 @@ treeray_status launch_team(treeray_ctx* c, const EvalArgs& a, const EvalArgs* bo
     return TREERAY_OK;
 }
 
-template <int NPIX, bool THICK>
+template <int NPIX, bool THICK, bool PERIODIC>
 treeray_status launch_wpt(treeray_ctx* c, int wpt, const EvalArgs& a, const EvalArgs* boxes,
                           const int64_t* box_start, int nbox, int layout_lmax, cudaStream_t s) {
     switch (wpt) {
-        case 2: return launch_team<NPIX, THICK, 2>(c, a, boxes, box_start, nbox, layout_lmax, s);
-        case 8: return launch_team<NPIX, THICK, 8>(c, a, boxes, box_start, nbox, layout_lmax, s);
-        default: return launch_team<NPIX, THICK, 4>(c, a, boxes, box_start, nbox, layout_lmax, s);
+        case 2: return launch_team<NPIX, THICK, 2, PERIODIC>(c, a, boxes, box_start, nbox, layout_lmax, s);
+        case 8: return launch_team<NPIX, THICK, 8, PERIODIC>(c, a, boxes, box_start, nbox, layout_lmax, s);
+        default: return launch_team<NPIX, THICK, 4, PERIODIC>(c, a, boxes, box_start, nbox, layout_lmax, s);
     }
 }
 
-treeray_status dispatch_team(treeray_ctx* c, bool thick, int wpt, const EvalArgs& a, const EvalArgs* boxes,
-                             const int64_t* box_start, int nbox, int layout_lmax, cudaStream_t s) {
+template <int NPIX>
+treeray_status launch_kind(treeray_ctx* c, bool thick, bool periodic, int wpt, const EvalArgs& a,
+                           const EvalArgs* boxes, const int64_t* box_start, int nbox, int layout_lmax,
+                           cudaStream_t s) {
+    // the periodic instantiations carry the closest-copy code; isolated grids run without it
+    if (periodic)
+        return thick ? launch_wpt<NPIX, true, true>(c, wpt, a, boxes, box_start, nbox, layout_lmax, s)
+                     : launch_wpt<NPIX, false, true>(c, wpt, a, boxes, box_start, nbox, layout_lmax, s);
+    return thick ? launch_wpt<NPIX, true, false>(c, wpt, a, boxes, box_start, nbox, layout_lmax, s)
+                 : launch_wpt<NPIX, false, false>(c, wpt, a, boxes, box_start, nbox, layout_lmax, s);
+}
+
+treeray_status dispatch_team(treeray_ctx* c, bool thick, bool periodic, int wpt, const EvalArgs& a,
+                             const EvalArgs* boxes, const int64_t* box_start, int nbox, int layout_lmax,
+                             cudaStream_t s) {
     switch (c->p.npix) {
-        case 12:
-            return thick ? launch_wpt<12, true>(c, wpt, a, boxes, box_start, nbox, layout_lmax, s)
-                         : launch_wpt<12, false>(c, wpt, a, boxes, box_start, nbox, layout_lmax, s);
-        case 48:
-            return thick ? launch_wpt<48, true>(c, wpt, a, boxes, box_start, nbox, layout_lmax, s)
-                         : launch_wpt<48, false>(c, wpt, a, boxes, box_start, nbox, layout_lmax, s);
-        case 192:
-            return thick ? launch_wpt<192, true>(c, wpt, a, boxes, box_start, nbox, layout_lmax, s)
-                         : launch_wpt<192, false>(c, wpt, a, boxes, box_start, nbox, layout_lmax, s);
+        case 12: return launch_kind<12>(c, thick, periodic, wpt, a, boxes, box_start, nbox, layout_lmax, s);
+        case 48: return launch_kind<48>(c, thick, periodic, wpt, a, boxes, box_start, nbox, layout_lmax, s);
+        case 192: return launch_kind<192>(c, thick, periodic, wpt, a, boxes, box_start, nbox, layout_lmax, s);
     }
     set_error("evaluate: npix must be 12, 48 or 192");
     return TREERAY_EINVAL;
 }
 
 treeray_status dispatch_eval(treeray_ctx* c, const EvalArgs& a, cudaStream_t s) {
-    return dispatch_team(c, c->has_thick || c->force_thick, c->wpt, a, nullptr, nullptr, 1, c->lmax, s);
+    return dispatch_team(c, c->has_thick || c->force_thick, c->p.periodic != 0, c->wpt, a, nullptr, nullptr, 1,
+                         c->lmax, s);
 }
 
 treeray_status dispatch_list(treeray_ctx* c, const EvalArgs& a, cudaStream_t s) {
@@ -812,6 +925,8 @@ EvalArgs make_args(treeray_ctx* c, const int32_t* targets, int64_t n) {
     a.nbins = c->p.nbins;
     a.D = c->ht.D;
     a.npix = c->p.npix;
+    a.periodic = c->p.periodic;
+    a.inv_s3 = 1.0f / (float)(c->ht.s * c->ht.s * c->ht.s);
     a.u = c->u;
     a.inv_u2 = 1.0 / (c->u * c->u);
     // the stack holds at most 28 leftover groups per level plus one batch of pushes
@@ -947,7 +1062,8 @@ treeray_status autotune(treeray_ctx* c, int64_t n_sample, int* best, float* ms, 
         treeray_status rc;
         for (int rep = 0; rep < 2; ++rep) {  // the second launch is timed
             if (rep == 1) TR_CUDA(cudaEventRecord(e0, s));
-            rc = dispatch_team(c, c->has_thick || c->force_thick, cand[k], a, nullptr, nullptr, 1, c->lmax, s);
+            rc = dispatch_team(c, c->has_thick || c->force_thick, c->p.periodic != 0, cand[k], a, nullptr, nullptr,
+                               1, c->lmax, s);
             if (rc != TREERAY_OK) return rc;
         }
         TR_CUDA(cudaEventRecord(e1, s));
@@ -979,6 +1095,7 @@ struct treeray_batch {
         int64_t* d_start = nullptr;
         unsigned long long* d_queue = nullptr;
         int max_lmax = 0;
+        bool periodic = false;  // some box of the group has periodic axes
     };
     std::vector<treeray_t> ctx;
     Group g[2];
@@ -1026,6 +1143,7 @@ treeray_status treeray_batch_create(const treeray_t* ctxs, int n_boxes, treeray_
         g.desc.push_back(a);
         g.start.push_back(g.start.back() + c->nleaves);
         g.max_lmax = std::max(g.max_lmax, c->lmax);
+        g.periodic = g.periodic || c->p.periodic != 0;
     }
     auto fail = [&](treeray_status rc) {
         treeray_batch_destroy(b);
@@ -1081,7 +1199,7 @@ treeray_status batch_launch(treeray_batch_t b, cudaStream_t s) {
         a.targets = nullptr;
         a.skip = nullptr;
         const treeray_status rc =
-            dispatch_team(c0, t == 1, 4, a, g.d_desc, g.d_start, (int)g.box.size(), g.max_lmax, s);
+            dispatch_team(c0, t == 1, g.periodic, 4, a, g.d_desc, g.d_start, (int)g.box.size(), g.max_lmax, s);
         if (rc != TREERAY_OK) return rc;
     }
     return TREERAY_OK;

@@ -215,10 +215,20 @@ void build_alpha_table(HostTables& t, double theta, int lmax, bool amr) {
     g_tab_cache[key] = std::make_pair(t.alpha_off, t.alpha_ent);
 }
 
-// R_i = R_0 (R_max / R_0)^(i / nbins), R_0 = Et / 2, R_max = sqrt(3) box (half-cells)
-void radii(int nbins, int lmax, int64_t Et, double* R) {
+// R_i = R_0 (R_max / R_0)^(i / nbins), R_0 = Et / 2, R_max = sqrt(3) box (half-cells); with
+// periodic axes R_max is the largest closest-copy distance (half the box on those axes)
+void radii(int nbins, int lmax, int periodic, int64_t Et, double* R) {
     const double R0 = 0.5 * (double)Et;
-    const double Rmax = std::sqrt(3.0) * (double)((int64_t)2 << lmax);
+    const double B = (double)((int64_t)2 << lmax);
+    double Rmax = std::sqrt(3.0) * B;
+    if (periodic) {
+        double s = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            const double e = ((periodic >> a) & 1) ? 0.5 * B : B;
+            s += e * e;
+        }
+        Rmax = std::sqrt(s);
+    }
     for (int i = 0; i <= nbins; ++i) R[i] = R0 * std::pow(Rmax / R0, (double)i / (double)nbins);
 }
 

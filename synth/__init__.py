@@ -56,7 +56,7 @@ class Workload:
 
 def default_params(**over) -> dict:
     p = dict(npix=48, nbins=20, theta=0.5, kappa_model=0, kappa0=5.0,
-             dust_to_gas=0.01, dust_emission=1, kappa_ext_scale=1.0, alpha_s=8)
+             dust_to_gas=0.01, dust_emission=1, kappa_ext_scale=1.0, alpha_s=8, periodic=0)
     p.update(over)
     return p
 

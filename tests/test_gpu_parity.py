@@ -27,6 +27,12 @@ CASES = {
     "rand16_thick": lambda: synth.random_uniform(16, seed=5, thick_frac=0.15, n_stars=3),
     "point16": lambda: synth.point_source(16, kappa0=1.0),
     "blob16": lambda: synth.thick_blob(16),
+    # periodic axes (closest copies; ties half a box away split in two), and an angular
+    # kernel of 4^3 samples instead of 8^3
+    "rand16_periodic": lambda: synth.random_uniform(16, seed=6, thick_frac=0.15, n_stars=3, periodic=7),
+    "amr_periodic_x": lambda: synth.amr_core(n_base_blocks=2, max_level=2, target_leaves=24 * 512, n_stars=3,
+                                             periodic=1),
+    "clump16_s4": lambda: synth.gaussian_clump(16, alpha_s=4),
 }
 
 
@@ -56,7 +62,7 @@ def test_leaf_quantities(orc, name):
         assert np.allclose(g[k], o[k], rtol=1e-14, atol=0), k
 
 
-@pytest.mark.parametrize("name", ["clump16", "rand16_thick"])
+@pytest.mark.parametrize("name", ["clump16", "rand16_thick", "rand16_periodic", "amr_periodic_x"])
 def test_accepted_lists_bit_exact(orc, name):
     import torch
     w = CASES[name]()
@@ -140,6 +146,17 @@ def test_evaluate_turbulent128_sampled(orc, npix):
     assert ej.max() <= J_TOL and ef.max() <= F_TOL
 
 
+def test_isotropic_periodic_box_gpu(orc):
+    """Homogeneous isothermal box periodic on every axis, theta = 0.5: the GPU matches
+    the oracle cell by cell, and |F| stays at the tree-error level (<= 0.1 x 4 pi J)."""
+    w = synth.homogeneous(16, 1.0, 1e-21, td=20.0, kappa0=5.0, periodic=7)
+    ej, ef = _parity(orc, w)
+    assert ej.max() <= J_TOL and ef.max() <= F_TOL
+    ctx, _ = build_ctx(w)
+    J, F = evaluate(ctx)
+    assert (np.linalg.norm(F, axis=1) <= 0.1 * 4 * np.pi * J).all()
+
+
 def test_radpressure_and_dust(orc):
     import torch
     w = synth.with_gas(synth.random_uniform(16, seed=2, thick_frac=0.1), heat_scale=1e-25)
@@ -193,7 +210,7 @@ def test_errors_are_reported():
                    blocks=np.array([[0, 0, 0, 4]]))
 
 
-@pytest.mark.parametrize("name", ["clump16", "rand16_thick"])
+@pytest.mark.parametrize("name", ["clump16", "rand16_thick", "rand16_periodic", "amr_periodic_x", "clump16_s4"])
 def test_walk_stats_exact(orc, name):
     """Visited/accepted/angular-entry totals of the GPU walk equal the oracle's."""
     import torch

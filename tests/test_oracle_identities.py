@@ -184,3 +184,70 @@ def test_uniform_slab_closed_form(orc, tau_cell, ncell):
     assert F[1, 2] > 0  # radiation leaves the slab upward above it
     assert 0.75 < J[1] / Jinf < 1.25
     assert 0.85 < F[1, 2] / Finf < 1.05
+
+
+@pytest.mark.parametrize("periodic", [7, 1, 6])
+def test_no_extinction_periodic_nearest_copies(orc, periodic):
+    """The identity above with periodic axes (Sec. 4.2: only the closest periodic copies
+    of a node are considered): every source enters at its nearest copy; a source exactly
+    half a box away on a periodic axis has two closest copies, each counted with weight 1/2
+    (the reading), so it adds to J but its flux along that axis cancels."""
+    n = 8
+    w = synth.random_uniform(n, seed=3, thick_frac=0.0, kappa_ext_scale=0.0, theta=1e-9, periodic=periodic)
+    t = orc.Tree(w)
+    L, _ = _leaf_L(t)
+    dx = w.box_cm / n
+    cen = synth.cell_centres(n, w.box_cm)
+    nhat = np.array([orc.pix2vec(2, h) for h in range(48)])
+    targets = np.array([0, 73, 300, 511])
+    J, F = t.evaluate(targets)
+    for q, tk in enumerate(targets):
+        o = np.round((cen - cen[tk]) / dx * 2).astype(np.int64)  # half-cells
+        Jb, Fb = t.leaves()["jsrc"][tk], np.zeros(3)
+        for k in range(n ** 3):
+            if k == tk:
+                Jb += L[k] / (16 * math.pi ** 2 * (0.5 * dx) ** 2)
+                continue
+            copies = [(o[k].copy(), 1.0)]
+            for a in range(3):
+                if not (periodic >> a) & 1:
+                    continue
+                nxt = []
+                for oc, wt in copies:
+                    v = (oc[a] + n) % (2 * n) - n  # into [-n, n) half-cells
+                    if v == -n:  # exactly half a box: both copies
+                        for s in (-n, n):
+                            c2 = oc.copy()
+                            c2[a] = s
+                            nxt.append((c2, 0.5 * wt))
+                    else:
+                        oc = oc.copy()
+                        oc[a] = v
+                        nxt.append((oc, wt))
+                copies = nxt
+            for oc, wt in copies:
+                r2 = ((oc * 0.5 * dx) ** 2).sum()
+                Jb += wt * L[k] / (16 * math.pi ** 2 * r2)
+                c = orc.alpha_counts(48, orc.alpha_key(oc, 2)) / 512.0
+                Fb -= wt * L[k] / (4 * math.pi * r2) * (c[:, None] * nhat).sum(0)
+        assert math.isclose(J[q], Jb, rel_tol=1e-12)
+        assert np.allclose(F[q], Fb, rtol=1e-11, atol=1e-12 * np.abs(Fb).max())
+
+
+def test_isotropic_periodic_box_has_no_net_flux(orc):
+    """Homogeneous isothermal box, periodic on every axis: with every leaf accepted
+    (theta -> 0) each cell sees a point-symmetric set of nearest copies (ties split in
+    half), the ray set is antipodally symmetric, so F = 0 to rounding and J is the same in
+    every cell. At theta = 0.5 the octree's fixed node boundaries break the symmetry at the
+    level of the tree error (measured |F| <= 0.075 x 4 pi J on 16^3); the isolated box
+    has cells at its edges that see one side only (|F| up to 0.72 x 4 pi J)."""
+    w = synth.homogeneous(8, 1.0, 1e-21, td=20.0, kappa0=5.0, periodic=7, theta=1e-6)
+    J, F = orc.Tree(w).evaluate()
+    assert np.abs(J / J[0] - 1).max() < 1e-12
+    assert (np.linalg.norm(F, axis=1) <= 1e-12 * 4 * math.pi * J).all()
+    w = synth.homogeneous(16, 1.0, 1e-21, td=20.0, kappa0=5.0, periodic=7)
+    J, F = orc.Tree(w).evaluate()
+    assert (np.linalg.norm(F, axis=1) <= 0.1 * 4 * math.pi * J).all()
+    w = synth.homogeneous(16, 1.0, 1e-21, td=20.0, kappa0=5.0)
+    J, F = orc.Tree(w).evaluate()
+    assert (np.linalg.norm(F, axis=1) / (4 * math.pi * J)).max() > 0.5
