@@ -254,9 +254,10 @@ __global__ void __launch_bounds__(256) k_walk_list(EvalArgs a) {
 
 constexpr int kOwnerCap = 256;  // entries per warp and walk step spread one per lane
 
-// Teams resident per SM that the register budget is cut for: thin tiles at N_pix <= 48 are
-// small enough for 64 warps per SM; larger tiles are limited by shared memory anyway.
-constexpr int min_warps_per_sm(int npix, bool thick) { return thick ? 24 : (npix <= 48 ? 64 : 48); }
+// Warps resident per SM that the register budget is cut for: thin tiles at N_pix <= 48 are
+// small enough for 64 warps per SM; larger thin tiles are limited by shared memory anyway;
+// thick kernels (six-quantity tiles) fit 32 warps without spilling.
+constexpr int min_warps_per_sm(int npix, bool thick) { return thick ? 32 : (npix <= 48 ? 64 : 48); }
 
 // Deposit of an accepted node whose closest periodic copies are tied (it lies exactly half
 // a box away on a periodic axis): every closest copy, with weight 1/2 per tied axis, by the
@@ -568,13 +569,23 @@ __global__ void __launch_bounds__(WPT * 32, min_warps_per_sm(NPIX, THICK) / WPT)
                         for (int k = 0; k < ne; ++k) owner[pre + k] = (unsigned char)lane;
                     }
                     __syncwarp();
-                    for (int r = lane; r < tw; r += 32) {
+                    // two entries per lane per pass: their loads and atomics overlap
+                    for (int r = lane; r < tw; r += 64) {
+                        const int r2 = r + 32;
                         const int4 nd = nodebuf[owner[r]];
+                        const int4 nd2 = r2 < tw ? nodebuf[owner[r2]] : nd;
                         const uint32_t ent = __ldg(A.aent + nd.y + r);
+                        const uint32_t ent2 = r2 < tw ? __ldg(A.aent + nd2.y + r2) : 0u;
                         const int c = nd.x + (int)(ent & 0xffffu);
                         const float w = count_to_float(ent >> 16);
                         atomicAdd(tL + c, w * __int_as_float(nd.z));
                         atomicAdd(tA + c, w * __int_as_float(nd.w));
+                        if (r2 < tw) {
+                            const int c2 = nd2.x + (int)(ent2 & 0xffffu);
+                            const float w2 = count_to_float(ent2 >> 16);
+                            atomicAdd(tL + c2, w2 * __int_as_float(nd2.z));
+                            atomicAdd(tA + c2, w2 * __int_as_float(nd2.w));
+                        }
                     }
                     __syncwarp();
                 } else {
