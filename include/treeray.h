@@ -59,7 +59,9 @@ typedef enum {
  *                  also holds [0, R_0) (Sec. 4.2, Fig. "ray bin").
  *  theta           opening angle theta_lim: a node of edge E at distance d from the
  *                  target (centre to centre) is opened iff E^2 >= theta^2 d^2, or if
- *                  it contains the target; leaves are always accepted (Sec. 4).
+ *                  it contains the target; leaves are always accepted (Sec. 4). In
+ *                  (0, 2]; a negative value selects the angle matched to the ray size,
+ *                  sqrt(4 pi / npix) (Sec. 6: more rays open nodes further).
  *  kappa_model     0: grey kappa0 per gram of gas; 1: Planck mean
  *                  0.1 cm^2/g (T/10 K)^2 capped at 150 K (Sec. 2).
  *  kappa0          grey opacity, cm^2/g (kappa_model 0).
@@ -75,6 +77,9 @@ typedef enum {
  *                  enters at both, each with weight 1/2. R_max becomes the largest
  *                  closest-copy distance, sqrt of the sum over axes of (box/2)^2 on
  *                  periodic and box^2 on isolated axes. 0 (all isolated) is the default.
+ *  bin_spacing     0: geometric radii as above (the default); 1: radii growing
+ *                  quadratically, R_i = R_0 + (R_max - R_0) (i / nbins)^2 (Sec. 4.2, "grows
+ *                  quadratically").
  */
 typedef struct {
     int npix;
@@ -87,6 +92,7 @@ typedef struct {
     double kappa_ext_scale;
     int alpha_s;
     int periodic;
+    int bin_spacing;
 } treeray_params;
 
 /*

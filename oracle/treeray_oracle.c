@@ -61,7 +61,7 @@
 typedef struct {
     int npix;              /* 12 * nside^2 HEALPix rays */
     int nbins;             /* radial evaluation points per ray */
-    double theta;          /* opening angle theta_lim */
+    double theta;          /* opening angle theta_lim; < 0: sqrt(4 pi / npix), ray-matched */
     int kappa_model;       /* 0: grey kappa0, 1: Planck mean 0.1 (T/10K)^2, capped at 150 K */
     double kappa0;         /* grey opacity per gram of gas */
     double dust_to_gas;    /* xi; enters only the gas-dust coupling */
@@ -69,6 +69,7 @@ typedef struct {
     double kappa_ext_scale;/* scales the extinction areas A~ (test switch) */
     int alpha_s;           /* sub-points per axis of the angular kernel's sampling */
     int periodic;          /* bit a set: axis a is periodic (nearest copies, Sec. 4.2) */
+    int bin_spacing;       /* 0: geometric radii, 1: quadratically growing radii (Sec. 4.2) */
 } or_params;
 
 /* ------------------------------------------------------------------ HEALPix
@@ -437,6 +438,9 @@ int or_build(const or_params* p, int lmax, double box_cm, int64_t nleaves,
         return 1;
     or_tree* t = (or_tree*)calloc(1, sizeof(or_tree));
     t->p = *p;
+    /* theta < 0: the opening angle matched to the ray size, sqrt(4 pi / N_pix)
+     * (Sec. 6: more rays open nodes further, toward the ray's angular size) */
+    if (t->p.theta < 0.0) t->p.theta = sqrt(4.0 * OR_PI / (double)p->npix);
     t->lmax = lmax;
     t->box = box_cm;
     t->u = ldexp(box_cm, -(lmax + 1));
@@ -645,7 +649,7 @@ int or_build(const or_params* p, int lmax, double box_cm, int64_t nleaves,
  * Reading: R_0 = Et / 2 (half the target cell), R_i = R_0 (R_max / R_0)^(i / N) with
  * R_max = sqrt(3) x box edge (geometric spacing). Segment i is [R_i, R_(i+1)); segment
  * 0 also holds [0, R_0); nodes beyond R_(N-1) fall into the last segment. */
-static void or_radii(int nbins, int lmax, int periodic, int64_t Et, double* R) {
+static void or_radii(int nbins, int lmax, int periodic, int spacing, int64_t Et, double* R) {
     double R0 = 0.5 * (double)Et;
     double B = (double)((int64_t)2 << lmax);
     double Rmax = sqrt(3.0) * B;
@@ -656,6 +660,13 @@ static void or_radii(int nbins, int lmax, int periodic, int64_t Et, double* R) {
             s += e * e;
         }
         Rmax = sqrt(s);
+    }
+    if (spacing == 1) { /* radii growing quadratically from R_0 to R_max */
+        for (int i = 0; i <= nbins; ++i) {
+            double q = (double)i / (double)nbins;
+            R[i] = R0 + (Rmax - R0) * (q * q);
+        }
+        return;
     }
     for (int i = 0; i <= nbins; ++i) R[i] = R0 * pow(Rmax / R0, (double)i / (double)nbins);
 }
@@ -862,7 +873,7 @@ int or_evaluate(or_tree* t, int64_t ntargets, const int64_t* targets, double* J,
             const or_node* tn = &t->nodes[t->leaf_node[leaf]];
             memset(buf, 0, sizeof(double) * 6 * cells);
             memset(ry.flag, 0, sizeof(uint64_t) * np);
-            or_radii(nb, t->lmax, p->periodic, tn->E, R);
+            or_radii(nb, t->lmax, p->periodic, p->bin_spacing, tn->E, R);
             for (int i = 0; i <= nb; ++i) Rcm[i] = R[i] * t->u;
             int sp = 0;
             stack[sp++] = 0;
@@ -1132,7 +1143,7 @@ void or_walk_stats(or_tree* t, int64_t leaf, int64_t* out) {
 
 /* Evaluation radii R_i (half-units) for a target leaf. */
 void or_target_radii(const or_tree* t, int64_t leaf, double* R) {
-    or_radii(t->p.nbins, t->lmax, t->p.periodic, t->nodes[t->leaf_node[leaf]].E, R);
+    or_radii(t->p.nbins, t->lmax, t->p.periodic, t->p.bin_spacing, t->nodes[t->leaf_node[leaf]].E, R);
 }
 
 /* alpha key for an offset o and node edge E. */

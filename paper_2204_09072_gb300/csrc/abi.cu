@@ -81,9 +81,14 @@ treeray_status upload_tables(treeray_ctx* c, cudaStream_t s) {
         omax[lv] = x;
     }
     for (int lt = 0; lt <= L; ++lt) {
-        radii(nb, L, c->p.periodic, (int64_t)2 << (L - lt), R.data());
-        lvlp[lt] = make_float2((float)(1.0 / (R[0] * R[0])),
-                               (float)(0.5 * nb / std::log2(R[nb] / R[0])));
+        radii(nb, L, c->p.periodic, c->p.bin_spacing, (int64_t)2 << (L - lt), R.data());
+        // segment guess parameters (the integer thresholds decide): geometric radii
+        // i ~ log2(d^2 / R_0^2) nb / (2 log2(R_max / R_0)); quadratic radii
+        // i ~ sqrt((d - R_0) nb^2 / (R_max - R_0))
+        // (the quadratic pair carries -R_0, so the kernel tells the two apart by its sign)
+        lvlp[lt] = c->p.bin_spacing == 1
+                       ? make_float2((float)-R[0], (float)((double)nb * nb / (R[nb] - R[0])))
+                       : make_float2((float)(1.0 / (R[0] * R[0])), (float)(0.5 * nb / std::log2(R[nb] / R[0])));
         for (int i = 0; i < nb; ++i) {
             thr[(size_t)lt * nb + i] = (int64_t)std::ceil(R[i] * R[i]);
             R2[(size_t)lt * nb + i] = (float)(R[i] * R[i]);
@@ -151,8 +156,12 @@ treeray_status treeray_create(const treeray_params* p, treeray_t* out) {
         set_error("nbins must lie in 1..64");
         return TREERAY_EINVAL;
     }
-    if (!(p->theta > 0.0) || p->theta > 2.0) {
-        set_error("theta must lie in (0, 2]");
+    if (!(p->theta > 0.0 || p->theta < 0.0) || p->theta > 2.0) {
+        set_error("theta must lie in (0, 2], or be negative for the ray-matched angle");
+        return TREERAY_EINVAL;
+    }
+    if (p->bin_spacing != 0 && p->bin_spacing != 1) {
+        set_error("bin_spacing must be 0 (geometric) or 1 (quadratic)");
         return TREERAY_EINVAL;
     }
     if (p->kappa_model != 0 && p->kappa_model != 1) {
@@ -173,6 +182,8 @@ treeray_status treeray_create(const treeray_params* p, treeray_t* out) {
         return TREERAY_ENOMEM;
     }
     c->p = *p;
+    // negative theta: the opening angle matched to the ray size (Sec. 6)
+    if (c->p.theta < 0.0) c->p.theta = std::sqrt(4.0 * kPi / (double)p->npix);
     cudaGetDevice(&c->device);
     c->ht.npix = p->npix;
     c->ht.nside = healpix_nside(p->npix);

@@ -43,7 +43,7 @@ struct __align__(16) EvalArgs {
     const int64_t* __restrict__ open_max;
     const int64_t* __restrict__ str_lo;
     const int64_t* __restrict__ str_hi;
-    const float2* __restrict__ lvlp;    // per target level: 1 / R_0^2, 0.5 / log2(g)
+    const float2* __restrict__ lvlp;    // per target level: segment-guess parameters
     const double* __restrict__ scal;
     unsigned* err;
     unsigned long long* queue;
@@ -85,10 +85,14 @@ __device__ __forceinline__ int fixup(int g, int64_t d2, const int64_t* __restric
     return g;
 }
 
-// Guess of the segment holding squared distance x2 for a target level with R_0^2 = 1/inv_r02
-// and geometric ratio g: 0.5 log2(x2 / R_0^2) / log2(g).
+// Guess of the segment holding squared distance x2 for a target level (the integer
+// thresholds then decide): geometric radii, lp = (1 / R_0^2, 0.5 / log2 g), gives
+// 0.5 log2(x2 / R_0^2) / log2(g); quadratic radii, lp = (-R_0, nb^2 / (R_max - R_0)),
+// give sqrt((d - R_0) nb^2 / (R_max - R_0)).
 __device__ __forceinline__ int guess_bin(float x2, float2 lp) {
-    return x2 > 0.0f ? (int)(__log2f(x2 * lp.x) * lp.y) : 0;
+    if (lp.x < 0.0f)  // quadratic radii: lp = (-R_0, nb^2 / (R_max - R_0))
+        return x2 > 0.0f ? (int)sqrtf(fmaxf(sqrtf(x2) + lp.x, 0.0f) * lp.y) : 0;
+    return x2 > 0.0f ? (int)(__log2f(x2 * lp.x) * lp.y) : 0;  // geometric radii
 }
 
 // Exact integer -> float conversions on the FP32 and integer pipes: the integer is

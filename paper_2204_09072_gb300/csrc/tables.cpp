@@ -217,7 +217,8 @@ void build_alpha_table(HostTables& t, double theta, int lmax, bool amr) {
 
 // R_i = R_0 (R_max / R_0)^(i / nbins), R_0 = Et / 2, R_max = sqrt(3) box (half-cells); with
 // periodic axes R_max is the largest closest-copy distance (half the box on those axes)
-void radii(int nbins, int lmax, int periodic, int64_t Et, double* R) {
+// (spacing 1: R_i = R_0 + (R_max - R_0) (i / nbins)^2, radii growing quadratically)
+void radii(int nbins, int lmax, int periodic, int spacing, int64_t Et, double* R) {
     const double R0 = 0.5 * (double)Et;
     const double B = (double)((int64_t)2 << lmax);
     double Rmax = std::sqrt(3.0) * B;
@@ -228,6 +229,13 @@ void radii(int nbins, int lmax, int periodic, int64_t Et, double* R) {
             s += e * e;
         }
         Rmax = std::sqrt(s);
+    }
+    if (spacing == 1) {
+        for (int i = 0; i <= nbins; ++i) {
+            const double q = (double)i / (double)nbins;
+            R[i] = R0 + (Rmax - R0) * (q * q);
+        }
+        return;
     }
     for (int i = 0; i <= nbins; ++i) R[i] = R0 * std::pow(Rmax / R0, (double)i / (double)nbins);
 }

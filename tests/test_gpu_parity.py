@@ -33,6 +33,9 @@ CASES = {
     "amr_periodic_x": lambda: synth.amr_core(n_base_blocks=2, max_level=2, target_leaves=24 * 512, n_stars=3,
                                              periodic=1),
     "clump16_s4": lambda: synth.gaussian_clump(16, alpha_s=4),
+    # radii growing quadratically, and the opening angle matched to the ray size
+    "rand16_quadratic": lambda: synth.random_uniform(16, seed=7, thick_frac=0.1, n_stars=2, bin_spacing=1),
+    "clump16_raytheta": lambda: synth.gaussian_clump(16, theta=-1.0),
 }
 
 
@@ -210,7 +213,8 @@ def test_errors_are_reported():
                    blocks=np.array([[0, 0, 0, 4]]))
 
 
-@pytest.mark.parametrize("name", ["clump16", "rand16_thick", "rand16_periodic", "amr_periodic_x", "clump16_s4"])
+@pytest.mark.parametrize("name", ["clump16", "rand16_thick", "rand16_periodic", "amr_periodic_x", "clump16_s4",
+                                  "rand16_quadratic", "clump16_raytheta"])
 def test_walk_stats_exact(orc, name):
     """Visited/accepted/angular-entry totals of the GPU walk equal the oracle's."""
     import torch

@@ -251,3 +251,24 @@ def test_isotropic_periodic_box_has_no_net_flux(orc):
     w = synth.homogeneous(16, 1.0, 1e-21, td=20.0, kappa0=5.0)
     J, F = orc.Tree(w).evaluate()
     assert (np.linalg.norm(F, axis=1) / (4 * math.pi * J)).max() > 0.5
+
+
+def test_quadratic_radii_and_ray_matched_theta(orc):
+    """Quadratic radii run from R_0 (half the target cell) to R_max with second differences
+    constant; the emission-only identity J = sum over accepted nodes of L / (16 pi^2 r^2)
+    holds for any radii (beta cancels R_i^2); a negative theta opens nodes down to the
+    ray size sqrt(4 pi / N_pix)."""
+    w = synth.gaussian_clump(16, kappa_ext_scale=0.0, bin_spacing=1)
+    t = orc.Tree(w)
+    R = t.radii(0)
+    n = len(R) - 1
+    assert math.isclose(R[0], 1.0) and math.isclose(R[-1], math.sqrt(3.0) * 32, rel_tol=1e-12)
+    d2 = np.diff(R, 2)
+    assert np.allclose(d2, d2[0], rtol=1e-9) and d2[0] > 0
+    assert np.allclose(R, 1.0 + (R[-1] - 1.0) * (np.arange(n + 1) / n) ** 2, rtol=1e-13)
+    Jq, _ = t.evaluate([0, 2080, 4095])
+    Jg, _ = orc.Tree(synth.gaussian_clump(16, kappa_ext_scale=0.0)).evaluate([0, 2080, 4095])
+    assert np.allclose(Jq, Jg, rtol=1e-12)
+    wt = synth.gaussian_clump(16, theta=-1.0)
+    w5 = synth.gaussian_clump(16, theta=math.sqrt(4 * math.pi / 48))
+    assert np.array_equal(orc.Tree(wt).accepted(2080), orc.Tree(w5).accepted(2080))
