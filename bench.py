@@ -409,33 +409,40 @@ def run_batch64(args):
 
 def run_sweep(args):
     """Cost of the 128^3 cloud's evaluation over N_pix x segments, with the autotuner's
-    team size for each; one JSON line per combination."""
+    team size for each; then 48 and 192 rays with the opening angle matched to the ray
+    size (theta = sqrt(4 pi / N_pix)) and quadratic radii, the setting in which the paper
+    quotes its cost ratio; one JSON line per combination."""
     import torch
 
     import paper_2204_09072_gb300 as tr
     import synth
     dev = torch.device("cuda:0")
-    for npix in (12, 48, 192):
-        for nb in (10, 20, 40):
-            w = synth.turbulent_cloud(128, npix=npix, nbins=nb)
-            c = tr.Context(w.params)
-            c.build(w.box_cm, torch.as_tensor(w.rho, device=dev), torch.as_tensor(w.td, device=dev), n=128,
-                    star_pos=w.star_pos, star_lum=w.star_lum)
-            best, tune = c.autotune(65536)
-            J = torch.empty(w.n_leaves, dtype=torch.float32, device=dev)
-            F = torch.empty(3 * w.n_leaves, dtype=torch.float64, device=dev)
-            c.evaluate(J, F)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            c.evaluate(J, F)
-            e1.record()
-            torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1)
-            c.check()
-            print(json.dumps({"sweep": "turb128", "npix": npix, "nbins": nb, "warps_per_target": best,
-                              "autotune_ms_wpt2_4_8_on_65536": tune, "ms_evaluate": ms,
-                              "ray_evals_per_s": w.n_leaves * npix / (ms * 1e-3)}))
-            c.close()
+    combos = [(npix, nb, {}) for npix in (12, 48, 192) for nb in (10, 20, 40)]
+    combos += [(npix, 20, {"theta": -1.0, "bin_spacing": sp}) for sp in (0, 1) for npix in (48, 192)]
+    for npix, nb, extra in combos:
+        w = synth.turbulent_cloud(128, npix=npix, nbins=nb, **extra)
+        c = tr.Context(w.params)
+        c.build(w.box_cm, torch.as_tensor(w.rho, device=dev), torch.as_tensor(w.td, device=dev), n=128,
+                star_pos=w.star_pos, star_lum=w.star_lum)
+        best, tune = c.autotune(65536)
+        J = torch.empty(w.n_leaves, dtype=torch.float32, device=dev)
+        F = torch.empty(3 * w.n_leaves, dtype=torch.float64, device=dev)
+        c.evaluate(J, F)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        c.evaluate(J, F)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        c.check()
+        st = c.walk_stats().cpu().numpy().tolist()
+        print(json.dumps({"sweep": "turb128", "npix": npix, "nbins": nb,
+                          "theta": "ray-matched" if extra.get("theta", 0.5) < 0 else 0.5,
+                          "bin_spacing": "quadratic" if extra.get("bin_spacing", 0) == 1 else "geometric",
+                          "warps_per_target": best, "autotune_ms_wpt2_4_8_on_65536": tune, "ms_evaluate": ms,
+                          "ray_evals_per_s": w.n_leaves * npix / (ms * 1e-3),
+                          "walk_visits_accepted_entries": st}))
+        c.close()
 
 
 def _cloud(n, seed, sigma, n_stars, npix, uv_heating=False):
