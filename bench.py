@@ -139,6 +139,24 @@ def ncu_traffic(workload_name: str):
     return None
 
 
+def job_times(ms_values, dist=None, device="cpu"):
+    """Step times of the whole job: each value reduced with MAX over the ranks (every rank
+    runs its own replica; the job is as slow as its slowest rank). Without a process group
+    the values pass through."""
+    if dist is None:
+        return [float(x) for x in ms_values]
+    import torch
+    t = torch.tensor([float(x) for x in ms_values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t]
+
+
+def job_value(cells: int, npix: int, world: int, ms: float) -> float:
+    """Whole-job ray evaluations per second: `world` replicas of `cells` cells x `npix` rays
+    each, in `ms` milliseconds (the slowest rank's step)."""
+    return cells * npix * world / (ms * 1e-3)
+
+
 # Algorithmic bytes of the evaluate kernel: per visited node its 16 B geometry record;
 # per accepted node (own cell aside) its two 16 B value records and the 8 B angular-kernel
 # offset pair; 4 B per angular-kernel entry; per target 16 B own geometry, 32 B own values,
@@ -225,11 +243,8 @@ def run_ours(args):
     post_ms = [e[2].elapsed_time(e[3]) for e in evs]
     ms = statistics.mean(step_ms)
     ms_eval = statistics.mean(eval_ms)
-    if dist:
-        t = torch.tensor([ms, ms_eval], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, ms_eval = float(t[0]), float(t[1])
-    value = n * npix * world / (ms * 1e-3)
+    ms, ms_eval = job_times([ms, ms_eval], dist, dev)
+    value = job_value(n, npix, world, ms)
 
     # ---- roofline of the evaluate kernel (algorithmic bytes / measured duration)
     with torch.cuda.stream(st):
@@ -276,11 +291,7 @@ def run_ours(args):
             e1.record(st)
             st.synchronize()
             e_ms.append(e0.elapsed_time(e1))
-    e2e_val = n * npix * world / (statistics.mean(e_ms) * 1e-3)
-    if dist:
-        t = torch.tensor([statistics.mean(e_ms)], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_val = n * npix * world / (float(t[0]) * 1e-3)
+    e2e_val = job_value(n, npix, world, job_times([statistics.mean(e_ms)], dist, dev)[0])
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
