@@ -164,6 +164,25 @@ treeray_status treeray_radpressure(treeray_t ctx, const float* J, const double* 
                                    treeray_stream_t stream);
 
 /*
+ * Radiation pressure of the ionising (UV) radiation on dust, neutral and ionised hydrogen
+ * (Sec. 4.5 and App. C), for every leaf (caller order), from a given ionising field (the
+ * transfer of ionising radiation itself is a separate module in the paper):
+ *  P_dot = (E/c) [sigma_d n N + sigma_H (1 - x) n N + alpha_B (x n)^2] u dV,
+ *  a_uv = P_dot / (rho dV), force_uv = P_dot,
+ * with n = 0.7 rho / m_H hydrogen nuclei per cm^3, E = 18 eV per photon, sigma_d =
+ * 1.5e-21 cm^2 per H, alpha_B = 2.5e-13 cm^3/s (the paper's values) and sigma_H =
+ * 6.3e-18 cm^2 (the Lyman-edge cross-section; the paper gives none).
+ *  nph     device float[N], ionising photons per s and cm^2 arriving at the cell.
+ *  uph     device float[3N], unit direction of that photon flux, xyz interleaved.
+ *  x_ion   device float[N], ionised fraction of hydrogen, or NULL (fully ionised).
+ *  a_uv, force_uv: device float[3N] outputs (cm/s^2, dyn); either may be NULL.
+ * Needs a built tree (density and cell sizes); TREERAY_EINVAL if nph or uph is NULL.
+ */
+treeray_status treeray_uv_radpressure(treeray_t ctx, const float* nph, const float* uph,
+                                      const float* x_ion, float* a_uv, float* force_uv,
+                                      treeray_stream_t stream);
+
+/*
  * Equilibrium dust temperature (Sec. 4.6, App. D) per leaf (caller order): the root of
  *  Gamma_dust-gas + heat_extra + rho kappa(T_d) (4 pi J - 4 sigma T_d^4) = 0,
  *  Gamma_dust-gas = 3.8e-33 sqrt(T) (T - T_d)(1 - 0.8 e^(-75/T)) n_H^2 (xi/0.01),

@@ -66,6 +66,8 @@ def lib():
             L.or_radpressure.argtypes = [C.c_void_p, C.c_int64, P(C.c_int64), P(C.c_double),
                                          P(C.c_double), P(C.c_double), P(C.c_double),
                                          P(C.c_double), P(C.c_double)]
+            L.or_uv_radpressure.argtypes = [C.c_void_p, C.c_int64, P(C.c_int64), P(C.c_double),
+                                            P(C.c_double), P(C.c_double), P(C.c_double), P(C.c_double)]
             L.or_dust_temperature.argtypes = [P(_Params), C.c_int64, P(C.c_float), P(C.c_float),
                                               P(C.c_float), P(C.c_double), P(C.c_float),
                                               P(C.c_double)]
@@ -206,6 +208,19 @@ class Tree:
                              _p(u, C.c_double), _p(a, C.c_double), _p(f, C.c_double),
                              _p(ps, C.c_double))
         return u, a.reshape(n, 3), f.reshape(n, 3), ps
+
+    def uv_radpressure(self, nph, uph, x_ion=None, targets=None):
+        """UV radiation pressure (App. C) per leaf: returns a_uv [n, 3], force [n, 3]."""
+        n = len(nph)
+        t = np.arange(n, dtype=np.int64) if targets is None else np.ascontiguousarray(targets, np.int64)
+        nph = np.ascontiguousarray(nph, np.float64)
+        uph = np.ascontiguousarray(uph, np.float64).reshape(-1)
+        x = None if x_ion is None else np.ascontiguousarray(x_ion, np.float64)
+        a = np.zeros(3 * n)
+        f = np.zeros(3 * n)
+        lib().or_uv_radpressure(self.h, n, _p(t, C.c_int64), _p(nph, C.c_double), _p(uph, C.c_double),
+                                _p(x, C.c_double), _p(a, C.c_double), _p(f, C.c_double))
+        return a.reshape(n, 3), f.reshape(n, 3)
 
     def export(self):
         nn = self.n_nodes

@@ -973,6 +973,45 @@ int or_radpressure(const or_tree* t, int64_t n, const int64_t* leaves, const dou
     return 0;
 }
 
+/*
+ * Radiation pressure of the ionising (UV) radiation on dust, neutral and ionised hydrogen
+ * (Sec. 4.5, App. C), per leaf, from a given ionising photon flux N_ph (photons/s/cm^2) in
+ * the unit direction u_ph and the ionised fraction x of hydrogen:
+ *   P_dust = sigma_d n   (E/c) N_ph u dV,  sigma_d = 1.5e-21 cm^2 per H nucleus (Sec. 4.5)
+ *   P_H    = sigma_H n_H (E/c) N_ph u dV,  n_H = (1 - x) n neutral hydrogen
+ *   P_H+   = alpha_B n_p^2 (E/c) u dV,     n_p = x n protons (App. C writes n^2 for an
+ *                                          ionised region)
+ * with n = X rho / m_H, E = 18 eV (the mean ionising photon energy of the appendix on
+ * HII-region interiors), alpha_B = 2.5e-13 cm^3/s (the Stroemgren radius of the HII-region
+ * test, eq. stroemgren). The paper
+ * gives no sigma_H; reading: 6.3e-18 cm^2, the hydrogen photoionisation cross-section at
+ * the Lyman edge. a_uv = (P_dust + P_H + P_H+) / (rho dV); force = the sum.
+ * x may be NULL (fully ionised).
+ */
+#define OR_SIGMA_D 1.5e-21
+#define OR_SIGMA_H 6.3e-18
+#define OR_ALPHA_B 2.5e-13
+#define OR_EPH (18.0 * 1.602176634e-12)
+int or_uv_radpressure(const or_tree* t, int64_t n, const int64_t* leaves, const double* nph,
+                      const double* uph, const double* x_ion, double* a_uv, double* force) {
+    for (int64_t q = 0; q < n; ++q) {
+        int64_t k = leaves[q];
+        double dx = ldexp(t->box, -t->leaf_level[k]);
+        double dV = (dx * dx) * dx;
+        double rho = t->rho[k];
+        double nh = OR_XH * rho / OR_MH;
+        double x = x_ion ? x_ion[q] : 1.0;
+        double n0 = (1.0 - x) * nh, np = x * nh;
+        double rate = OR_SIGMA_D * nh * nph[q] + OR_SIGMA_H * n0 * nph[q] + OR_ALPHA_B * np * np;
+        for (int a = 0; a < 3; ++a) {
+            double pd = (OR_EPH / OR_C) * rate * uph[3 * q + a] * dV;
+            force[3 * q + a] = pd;
+            a_uv[3 * q + a] = pd / (rho * dV);
+        }
+    }
+    return 0;
+}
+
 /* ------------------------------------------------------ dust temperature
  * Equilibrium dust temperature (Sec. 4.6, App. D): G(T_d) = 0 with
  *   G = Gamma_dust-gas + Gamma_extra + rho kappa(T_d) (4 pi J - 4 sigma T_d^4)

@@ -63,6 +63,7 @@ def lib():
     L.treeray_build.argtypes = [vp, C.POINTER(Grid), vp, vp, vp, C.c_int, vp, vp, vp]
     L.treeray_evaluate.argtypes = [vp, vp, i64, vp, vp, vp]
     L.treeray_radpressure.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+    L.treeray_uv_radpressure.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     L.treeray_dust_temperature.argtypes = [vp, vp, vp, vp, vp, vp]
     L.treeray_check.argtypes = [vp, vp]
     L.treeray_leaf_count.argtypes = [vp]
@@ -97,7 +98,7 @@ def lib():
     L.treeray_kernel_launches.restype = i64
     L.treeray_last_error.restype = C.c_char_p
     for f in ("treeray_create", "treeray_destroy", "treeray_build", "treeray_evaluate",
-              "treeray_radpressure", "treeray_dust_temperature", "treeray_check",
+              "treeray_radpressure", "treeray_uv_radpressure", "treeray_dust_temperature", "treeray_check",
               "treeray_tree_export", "treeray_leaf_export", "treeray_accepted",
               "treeray_alpha_counts_host", "treeray_walk_stats", "treeray_morton_order_noalloc",
               "treeray_refresh", "treeray_fixed_point", "treeray_autotune",
@@ -223,6 +224,14 @@ class Context:
                                          _dev(u, f32, "u", True), _dev(a_rp, f32, "a_rp", True),
                                          _dev(force, f32, "force", True),
                                          _dev(p_src, f32, "p_src", True), _stream(stream)))
+
+    # -- C: treeray_uv_radpressure
+    def uv_radpressure(self, nph, uph, a_uv=None, force_uv=None, x_ion=None, stream=None):
+        import torch
+        f32 = torch.float32
+        _raise(lib().treeray_uv_radpressure(self.h, _dev(nph, f32, "nph"), _dev(uph, f32, "uph"),
+                                            _dev(x_ion, f32, "x_ion", True), _dev(a_uv, f32, "a_uv", True),
+                                            _dev(force_uv, f32, "force_uv", True), _stream(stream)))
 
     # -- C: treeray_dust_temperature
     def dust_temperature(self, Tgas, J, Td, heat_extra=None, stream=None):

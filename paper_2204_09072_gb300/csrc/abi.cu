@@ -270,6 +270,17 @@ treeray_status treeray_radpressure(treeray_t c, const float* J, const double* F,
     return launch_radpressure(c, J, F, u, a_rp, force, p_src, (cudaStream_t)stream);
 }
 
+treeray_status treeray_uv_radpressure(treeray_t c, const float* nph, const float* uph, const float* x_ion,
+                                      float* a_uv, float* force_uv, treeray_stream_t stream) {
+    treeray_status rc = check_ctx(c, true);
+    if (rc != TREERAY_OK) return rc;
+    if (!nph || !uph) {
+        set_error("uv_radpressure: nph and uph required");
+        return TREERAY_EINVAL;
+    }
+    return launch_uv_radpressure(c, nph, uph, x_ion, a_uv, force_uv, (cudaStream_t)stream);
+}
+
 treeray_status treeray_dust_temperature(treeray_t c, const float* Tgas, const float* heat_extra,
                                         const float* J, float* Td, treeray_stream_t stream) {
     treeray_status rc = check_ctx(c, true);

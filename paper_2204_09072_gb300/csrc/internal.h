@@ -148,6 +148,8 @@ treeray_status launch_accepted(treeray_ctx* c, const int32_t* targets, int64_t n
                                int32_t* counts, int32_t* ids, cudaStream_t s);
 treeray_status launch_walk_stats(treeray_ctx* c, const int32_t* targets, int64_t n, int64_t* totals,
                                  cudaStream_t s);
+treeray_status launch_uv_radpressure(treeray_ctx* c, const float* nph, const float* uph, const float* xion,
+                                     float* a, float* f, cudaStream_t s);
 treeray_status launch_radpressure(treeray_ctx* c, const float* J, const double* F, float* u,
                                   float* a, float* f, float* p, cudaStream_t s);
 treeray_status launch_dust(treeray_ctx* c, const float* Tgas, const float* heat, const float* J,

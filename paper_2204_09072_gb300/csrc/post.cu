@@ -49,6 +49,46 @@ __global__ void k_radpressure(RpArgs r) {
     if (r.p) r.p[k] = (float)r.psrc[k];
 }
 
+// Radiation pressure of the ionising (UV) radiation (App. C) on dust, neutral and ionised
+// hydrogen, from a given photon flux N (photons/s/cm^2), its unit direction u and the
+// ionised fraction x (NULL: 1):
+//   P_dot = (E/c) [sigma_d n N + sigma_H (1 - x) n N + alpha_B (x n)^2] u dV, n = X rho / m_H,
+// E = 18 eV, sigma_d = 1.5e-21 cm^2 per H, alpha_B = 2.5e-13 cm^3/s, sigma_H = 6.3e-18 cm^2
+// (the Lyman-edge cross-section: the paper gives none); a_uv = P_dot / (rho dV).
+struct UvArgs {
+    const float* nph;
+    const float* uph;
+    const float* xion;
+    const float* rho;
+    const int4* geo;
+    const int32_t* leaf_node;
+    const int32_t* inv_perm;
+    float *a, *f;
+    int64_t n;
+    double box;
+};
+
+__global__ void k_uv_radpressure(UvArgs r) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= r.n) return;
+    constexpr double kSigmaD = 1.5e-21, kSigmaH = 6.3e-18, kAlphaB = 2.5e-13;
+    constexpr double kEoverC = 18.0 * 1.602176634e-12 / kLightC;
+    const int lvl = r.geo[r.leaf_node[r.inv_perm[k]]].z >> 24;
+    const double dx = ldexp(r.box, -lvl);
+    const double dV = (dx * dx) * dx;
+    const double rho = (double)r.rho[k];
+    const double nh = kHydrogenFraction * rho / kHydrogenMass;
+    const double x = r.xion ? (double)r.xion[k] : 1.0;
+    const double N = (double)r.nph[k];
+    const double n0 = (1.0 - x) * nh, np = x * nh;
+    const double rate = kSigmaD * nh * N + kSigmaH * n0 * N + kAlphaB * np * np;
+    for (int ax = 0; ax < 3; ++ax) {
+        const double pd = kEoverC * rate * (double)r.uph[3 * k + ax] * dV;
+        if (r.f) r.f[3 * k + ax] = (float)pd;
+        if (r.a) r.a[3 * k + ax] = (float)(pd / (rho * dV));
+    }
+}
+
 struct DustArgs {
     const int* skip;
     const float* rho;
@@ -180,6 +220,15 @@ treeray_status launch_radpressure(treeray_ctx* c, const float* J, const double* 
     RpArgs r{J, F, c->tree.kap, c->tree.tau, c->tree.psrc, c->tree.rho, c->tree.geo, c->tree.leaf_node,
              c->tree.inv_perm, u, a, f, p, c->nleaves, c->box};
     k_radpressure<<<(int)((c->nleaves + 255) / 256), 256, 0, s>>>(r);
+    c->launches += 1;
+    TR_CUDA(cudaGetLastError());
+    return TREERAY_OK;
+}
+
+treeray_status launch_uv_radpressure(treeray_ctx* c, const float* nph, const float* uph, const float* xion,
+                                     float* a, float* f, cudaStream_t s) {
+    UvArgs r{nph, uph, xion, c->tree.rho, c->tree.geo, c->tree.leaf_node, c->tree.inv_perm, a, f, c->nleaves, c->box};
+    k_uv_radpressure<<<(int)((c->nleaves + 255) / 256), 256, 0, s>>>(r);
     c->launches += 1;
     TR_CUDA(cudaGetLastError());
     return TREERAY_OK;

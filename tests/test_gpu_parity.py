@@ -187,6 +187,32 @@ def test_radpressure_and_dust(orc):
     assert np.allclose(Td.cpu().numpy(), Tr, rtol=2e-7, atol=0)
 
 
+@pytest.mark.parametrize("name", ["rand16_thick", "amr"])
+def test_uv_radpressure(orc, name):
+    """UV radiation pressure (App. C) from a given photon flux, direction and ionised
+    fraction against the FP64 oracle (FP32 outputs); a NULL fraction means fully ionised."""
+    import torch
+    w = CASES[name]()
+    t = _oracle(orc, w)
+    ctx, _ = build_ctx(w)
+    n = w.n_leaves
+    rng = np.random.default_rng(5)
+    nph = (10.0 ** rng.uniform(4, 12, n)).astype(np.float32)
+    u = rng.normal(size=(n, 3))
+    u = (u / np.linalg.norm(u, axis=1, keepdims=True)).astype(np.float32)
+    x = rng.uniform(0, 1, n).astype(np.float32)
+    dev = "cuda:0"
+    for xi in (x, None):
+        a = torch.empty(3 * n, dtype=torch.float32, device=dev)
+        f = torch.empty(3 * n, dtype=torch.float32, device=dev)
+        ctx.uv_radpressure(torch.as_tensor(nph, device=dev), torch.as_tensor(u.reshape(-1), device=dev), a, f,
+                           x_ion=None if xi is None else torch.as_tensor(xi, device=dev))
+        ctx.check()
+        ar, fr = t.uv_radpressure(nph, u, xi)
+        assert np.allclose(a.cpu().numpy().reshape(n, 3), ar, rtol=1e-6, atol=1e-6 * np.abs(ar).max())
+        assert np.allclose(f.cpu().numpy().reshape(n, 3), fr, rtol=1e-6, atol=1e-6 * np.abs(fr).max())
+
+
 def test_errors_are_reported():
     import torch
 

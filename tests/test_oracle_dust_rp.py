@@ -62,3 +62,36 @@ def test_radpressure_limits(orc):
     u2, a2, f2, _ = t2.radpressure(J2, F2)
     dx = w2.box_cm / 8
     assert np.allclose(f2, F2 * dx * dx / C, rtol=2e-3)
+
+
+def test_uv_radpressure_stroemgren_balance(orc):
+    """UV radiation pressure (App. C) tied to the Stroemgren sphere of the HII-region test
+    (eq. stroemgren, alpha_B = 2.5e-13 cm^3/s): inside a fully ionised uniform sphere of
+    radius R_s = (3 N / (4 pi alpha_B n^2))^(1/3) around a source of N ionising photons/s,
+    recombinations balance the source, so the recombination term summed over the sphere
+    carries the photon momentum N E / c (E = 18 eV) whatever the grid; the force points
+    along the photon direction, and a fully neutral cell feels only the absorption terms."""
+    import math
+    n = 32
+    w = synth.homogeneous(n, 1.0, 1e-21)  # n_H = 0.7 rho / m_H ~ 0.42 cm^-3
+    t = orc.Tree(w)
+    nh = 0.7 * float(w.rho[0]) / 1.6726e-24  # the FP32 density the tree holds
+    Rs = 0.35 * w.box_cm
+    N = 4 * math.pi / 3 * Rs ** 3 * 2.5e-13 * nh * nh
+    cen = synth.cell_centres(n, w.box_cm)
+    r = cen - 0.5 * w.box_cm
+    d = np.linalg.norm(r, axis=1)
+    u = r / d[:, None]
+    inside = d < Rs
+    x = np.where(inside, 1.0, 0.0)
+    a, f = t.uv_radpressure(np.zeros(n ** 3), u, x)  # no flux: recombination term only
+    p_tot = np.linalg.norm(f[inside], axis=1).sum()
+    E = 18.0 * 1.602176634e-12
+    assert abs(p_tot / (N * E / 2.99792458e10) - 1) < 0.02  # the sphere on a 32^3 grid
+    assert np.allclose(np.cross(f, u), 0.0, atol=1e-12 * np.abs(f).max())
+    assert np.allclose(a * (w.rho.astype(np.float64)[:, None] * (w.box_cm / n) ** 3), f, rtol=1e-12)
+    # a neutral cell under a photon flux: dust and neutral-H absorption, sigma_d + sigma_H
+    nph = np.full(n ** 3, 1e8)
+    a0, f0 = t.uv_radpressure(nph, u, np.zeros(n ** 3))
+    expect = (1.5e-21 + 6.3e-18) * nh * 1e8 * E / 2.99792458e10 * (w.box_cm / n) ** 3
+    assert np.allclose(np.linalg.norm(f0, axis=1), expect, rtol=1e-12)
