@@ -80,6 +80,12 @@ typedef enum {
  *  bin_spacing     0: geometric radii as above (the default); 1: radii growing
  *                  quadratically, R_i = R_0 + (R_max - R_0) (i / nbins)^2 (Sec. 4.2, "grows
  *                  quadratically").
+ *  col_mapping     0: accepted nodes are mapped at their geometric centre (the default);
+ *                  1: at their centre of luminosity (Sec. 6, nodes shifted towards their
+ *                  centre of emission): for a node whose COL is off centre, the segment,
+ *                  the straddled boundaries and the angular key come from the COL offset
+ *                  in FP32 (p = centre offset + COL offset, p^2 against the integer
+ *                  thresholds, key 2 floor(4 p / E) + 1 per axis).
  */
 typedef struct {
     int npix;
@@ -93,6 +99,7 @@ typedef struct {
     int alpha_s;
     int periodic;
     int bin_spacing;
+    int col_mapping;
 } treeray_params;
 
 /*

@@ -70,6 +70,7 @@ typedef struct {
     int alpha_s;           /* sub-points per axis of the angular kernel's sampling */
     int periodic;          /* bit a set: axis a is periodic (nearest copies, Sec. 4.2) */
     int bin_spacing;       /* 0: geometric radii, 1: quadratically growing radii (Sec. 4.2) */
+    int col_mapping;       /* 1: map accepted nodes at their centre of luminosity (Sec. 6) */
 } or_params;
 
 /* ------------------------------------------------------------------ HEALPix
@@ -720,8 +721,32 @@ static void or_map_node(const or_tree* t, or_alpha_table* at, const or_node* nd,
                         int64_t d2, const double* R, or_rays* ry, double w) {
     int nb = ry->nbins, np = ry->npix;
     double u = t->u;
-    int i = or_bin(nb, R, (double)d2);
     int own = (d2 == 0);
+    /* mapping at the centre of luminosity (Sec. 6: "we shift the nodes towards their
+     * center of emission during mapping to rays"), for nodes whose COL is off centre.
+     * Reading: the position p = o + c, c the COL offset rounded to FP32 (as a GPU node
+     * record holds it), is formed and squared in FP32; the segment and the straddled
+     * boundaries compare p^2 with the integer thresholds ceil(R_j^2), ceil((R_j +- s)^2)
+     * taken as FP32; the angular key is the odd grid point 2 floor(4 p / E) + 1 per axis.
+     * Every decision is then the same FP32 arithmetic on both implementations. */
+    float pf[3] = {0.0f, 0.0f, 0.0f}, pd2 = 0.0f;
+    int colmap = 0;
+    if (t->p.col_mapping && !own) {
+        for (int a = 0; a < 3; ++a) {
+            float c32 = (float)(nd->col[a] - (double)nd->c[a]);
+            if (c32 != 0.0f) colmap = 1;
+            pf[a] = (float)o[a] + c32;
+        }
+        pd2 = (pf[0] * pf[0] + pf[1] * pf[1]) + pf[2] * pf[2];
+    }
+    int i;
+    if (colmap) {
+        i = 0;
+        for (int j = 1; j < nb; ++j)
+            if (pd2 >= (float)ceil(R[j] * R[j])) i = j;
+    } else {
+        i = or_bin(nb, R, (double)d2);
+    }
     double beta = 1.0;
     if (!own) {
         double r2 = 0.0;
@@ -735,7 +760,11 @@ static void or_map_node(const or_tree* t, or_alpha_table* at, const or_node* nd,
     const int* lst = NULL;
     int owned = 0;
     if (!own) {
-        or_key(o, nd->E, K);
+        if (colmap) {
+            for (int a = 0; a < 3; ++a) K[a] = 2 * (int64_t)floorf(4.0f * pf[a] / (float)nd->E) + 1;
+        } else {
+            or_key(o, nd->E, K);
+        }
         lst = or_alpha_get(at, K, &owned);
     }
     int ilo = 0, ihi = 0;
@@ -743,9 +772,14 @@ static void or_map_node(const or_tree* t, or_alpha_table* at, const or_node* nd,
         double s = (sqrt(3.0) * 0.5) * (double)nd->E;
         for (int j = 1; j < nb; ++j) {
             double up = R[j] + s;
-            if ((double)d2 >= up * up) ilo = j;
             double dn = R[j] - s;
-            if (dn <= 0.0 || (double)d2 >= dn * dn) ihi = j;
+            if (colmap) {
+                if (pd2 >= (float)ceil(up * up)) ilo = j;
+                if (dn <= 0.0 || pd2 >= (float)ceil(dn * dn)) ihi = j;
+            } else {
+                if ((double)d2 >= up * up) ilo = j;
+                if (dn <= 0.0 || (double)d2 >= dn * dn) ihi = j;
+            }
         }
     }
     /* values in CGS: luminosities erg/s, areas cm^2, volumes cm^3; w < 1 for one of
@@ -1131,6 +1165,26 @@ int64_t or_accepted(const or_tree* t, int64_t leaf, int32_t* ids, int64_t cap) {
     return n;
 }
 
+/* Angular key of an accepted node at offset o: at its geometric centre (or_key), or with
+ * COL mapping, for a node whose COL is off centre, the odd grid point of its COL position
+ * in FP32 (as in or_map_node). */
+static void or_node_key(const or_tree* t, const or_node* nd, const int64_t* o, int64_t* K) {
+    if (t->p.col_mapping) {
+        float pf[3];
+        int shifted = 0;
+        for (int a = 0; a < 3; ++a) {
+            float c32 = (float)(nd->col[a] - (double)nd->c[a]);
+            if (c32 != 0.0f) shifted = 1;
+            pf[a] = (float)o[a] + c32;
+        }
+        if (shifted) {
+            for (int a = 0; a < 3; ++a) K[a] = 2 * (int64_t)floorf(4.0f * pf[a] / (float)nd->E) + 1;
+            return;
+        }
+    }
+    or_key(o, nd->E, K);
+}
+
 /* Walk statistics of one target: nodes visited (tested against the opening
  * criterion), nodes accepted (own cell included) and angular-kernel entries read by
  * the accepted nodes other than the own cell. out[3]. */
@@ -1165,7 +1219,7 @@ void or_walk_stats(or_tree* t, int64_t leaf, int64_t* out) {
                     for (int a = 0; a < 3; ++a)
                         oi[a] = ((ties >> a) & 1) ? (((m >> a) & 1) ? half : -half) : o[a];
                     int owned = 0;
-                    or_key(oi, nd->E, K);
+                    or_node_key(t, nd, oi, K);
                     const int* l = or_alpha_get(&t->alpha, K, &owned);
                     int n = 0;
                     while (l[2 * n] >= 0) ++n;

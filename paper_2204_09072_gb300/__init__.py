@@ -31,14 +31,14 @@ class Params(C.Structure):
     _fields_ = [("npix", C.c_int), ("nbins", C.c_int), ("theta", C.c_double),
                 ("kappa_model", C.c_int), ("kappa0", C.c_double), ("dust_to_gas", C.c_double),
                 ("dust_emission", C.c_int), ("kappa_ext_scale", C.c_double), ("alpha_s", C.c_int),
-                ("periodic", C.c_int), ("bin_spacing", C.c_int)]
+                ("periodic", C.c_int), ("bin_spacing", C.c_int), ("col_mapping", C.c_int)]
 
     @classmethod
     def from_dict(cls, d: dict) -> "Params":
         return cls(int(d["npix"]), int(d["nbins"]), float(d["theta"]), int(d["kappa_model"]),
                    float(d["kappa0"]), float(d["dust_to_gas"]), int(d["dust_emission"]),
                    float(d["kappa_ext_scale"]), int(d.get("alpha_s", 8)), int(d.get("periodic", 0)),
-                   int(d.get("bin_spacing", 0)))
+                   int(d.get("bin_spacing", 0)), int(d.get("col_mapping", 0)))
 
 
 class Grid(C.Structure):

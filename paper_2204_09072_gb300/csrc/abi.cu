@@ -54,7 +54,7 @@ treeray_status upload_tables(treeray_ctx* c, cudaStream_t s) {
         c->ht.npix = c->p.npix;
         c->ht.nside = healpix_nside(c->p.npix);
         c->ht.s = c->p.alpha_s;
-        build_alpha_table(c->ht, c->p.theta, L, c->amr);
+        build_alpha_table(c->ht, c->p.theta, L, c->amr, c->p.col_mapping != 0);
         treeray_status rc;
         if ((rc = upload(&c->dt.alpha_off, c->ht.alpha_off, s)) != TREERAY_OK) return rc;
         if ((rc = upload(&c->dt.alpha_ent, c->ht.alpha_ent, s)) != TREERAY_OK) return rc;
@@ -158,6 +158,10 @@ treeray_status treeray_create(const treeray_params* p, treeray_t* out) {
     }
     if (!(p->theta > 0.0 || p->theta < 0.0) || p->theta > 2.0) {
         set_error("theta must lie in (0, 2], or be negative for the ray-matched angle");
+        return TREERAY_EINVAL;
+    }
+    if (p->col_mapping != 0 && p->col_mapping != 1) {
+        set_error("col_mapping must be 0 or 1");
         return TREERAY_EINVAL;
     }
     if (p->bin_spacing != 0 && p->bin_spacing != 1) {

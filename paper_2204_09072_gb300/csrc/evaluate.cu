@@ -60,7 +60,8 @@ struct __align__(16) EvalArgs {
     int64_t n;
     int64_t nleaves;
     int lmax, nbins, D, stack_cap, npix;
-    int periodic;  // bit a: axis a periodic (closest copies)
+    int periodic;     // bit a: axis a periodic (closest copies)
+    int col_mapping;  // map accepted nodes at their centre of luminosity
     float inv_s3;  // 1 / alpha_s^3: weight of one sub-cube sample of the angular kernel
     double u;
     double inv_u2;  // 1 / u^2: flux unit = L_scale / u^2 (L_scale a power of two)
@@ -102,6 +103,24 @@ __device__ __forceinline__ float small_int_to_float(int v) {  // exact for |v| <
 }
 __device__ __forceinline__ float count_to_float(uint32_t v) {  // exact for v < 2^23
     return __uint_as_float(0x4B000000u | v) - 8388608.0f;
+}
+
+// Segment of a real squared distance x2 against the integer thresholds taken as FP32:
+// the largest j in [1, nb-1] with x2 >= (float)arr[j], else 0 (mapping at the COL).
+__device__ __forceinline__ int fixup_f(int g, float x2, const int64_t* __restrict__ arr, int nb) {
+    g = max(0, min(g, nb - 1));
+    while (g + 1 < nb && x2 >= (float)__ldg(arr + g + 1)) ++g;
+    while (g > 0 && x2 < (float)__ldg(arr + g)) --g;
+    return g;
+}
+// Angular key of a real offset p (half-cells) of a node of edge 2^elog: the odd grid point
+// 2 floor(4 p / E) + 1 (the scaling by a power of two is exact).
+__device__ __forceinline__ int odd_key(float p, int elog) {
+    return 2 * (int)floorf(p * ldexpf(1.0f, 2 - elog)) + 1;
+}
+// Squared length in FP32, evaluated in a fixed order and never fused, as the oracle does.
+__device__ __forceinline__ float sq3_rn(float x, float y, float z) {
+    return __fadd_rn(__fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y)), __fmul_rn(z, z));
 }
 
 // Closest periodic copy on one axis (Sec. 4.2): the offset o (half-cells) is brought into
@@ -226,11 +245,21 @@ __global__ void __launch_bounds__(256) k_walk_list(EvalArgs a) {
             if (a.stats && acc && d2 != 0) {
                 const int elog = a.lmax - lvl + 1;
                 const int half = 1 << a.lmax;
+                float cx = 0.0f, cy = 0.0f, cz = 0.0f;  // COL offset when nodes map at their COL
+                if (a.col_mapping) {
+                    const float4 v0 = __ldg(a.thin + node);
+                    cx = v0.z;
+                    cy = v0.w;
+                    cz = __ldg(a.thick + node).x;
+                }
+                const bool colmap = cx != 0.0f || cy != 0.0f || cz != 0.0f;
                 for (int m = 0; m < 8; ++m) {  // entries of every closest copy
                     if (m & ~ties) continue;
                     const int qx = copy_offset(ox, ties, 1, m, half), qy = copy_offset(oy, ties, 2, m, half),
                               qz = copy_offset(oz, ties, 4, m, half);
-                    const int Kx = alpha_key(qx, elog), Ky = alpha_key(qy, elog), Kz = alpha_key(qz, elog);
+                    const int Kx = colmap ? odd_key(small_int_to_float(qx) + cx, elog) : alpha_key(qx, elog);
+                    const int Ky = colmap ? odd_key(small_int_to_float(qy) + cy, elog) : alpha_key(qy, elog);
+                    const int Kz = colmap ? odd_key(small_int_to_float(qz) + cz, elog) : alpha_key(qz, elog);
                     if (abs(Kx) <= a.D && abs(Ky) <= a.D && abs(Kz) <= a.D) {
                         const int idx = ((Kz + a.D) * W + (Ky + a.D)) * W + (Kx + a.D);
                         nent += __ldg(a.aoff + idx + 1) - __ldg(a.aoff + idx);
@@ -276,24 +305,28 @@ __device__ __noinline__ void deposit_tied_copies(const EvalArgs& A, float* tL, f
     const int nb = A.nbins;
     const int64_t* thr = A.bin_thr + (int64_t)tl * nb;
     const float* R2 = A.R2 + (int64_t)tl * nb;
+    const int64_t* lo = A.str_lo + ((int64_t)tl * (A.lmax + 1) + lvl) * nb;
+    const int64_t* hi = A.str_hi + ((int64_t)tl * (A.lmax + 1) + lvl) * nb;
     const int W = 2 * A.D + 1;
     const int half = 1 << A.lmax;
     const float inv_s3 = A.inv_s3;
     const float wt = 1.0f / (float)(1 << __popc(ties));
     const float4 v0 = __ldg(A.thin + node);
     const float4 v1 = __ldg(A.thick + node);
+    const bool thick = THICK && v1.w > 0.0f;
+    const bool colmap = A.col_mapping && (v0.z != 0.0f || v0.w != 0.0f || v1.x != 0.0f);
+    const float sd = 0.8660254f * (float)(2 << (A.lmax - lvl));
+    // at the geometric centre the copies share |offset| per axis, hence d^2, the segment
+    // and the straddled boundaries; at the COL each copy has its own
     const float fd2 = (float)d2;
-    const int i = fixup(guess_bin(fd2, lp), d2, thr, nb);
-    unsigned long long fmask = 0ull;
-    if (THICK && v1.w > 0.0f) {
-        const int64_t* lo = A.str_lo + ((int64_t)tl * (A.lmax + 1) + lvl) * nb;
-        const int64_t* hi = A.str_hi + ((int64_t)tl * (A.lmax + 1) + lvl) * nb;
+    const int i0 = fixup(guess_bin(fd2, lp), d2, thr, nb);
+    unsigned long long fmask0 = 0ull;
+    if (thick && !colmap) {
         const float d = sqrtf(fd2);
-        const float sd = 0.8660254f * (float)(2 << (A.lmax - lvl));
         const float dl = fmaxf(d - sd, 0.0f), dh = d + sd;
         const int ilo = fixup(guess_bin(dl * dl, lp), d2, lo, nb);
         const int ihi = fixup(guess_bin(dh * dh, lp), d2, hi, nb);
-        for (int j = ilo; j < ihi; ++j) fmask |= 1ull << j;
+        for (int j = ilo; j < ihi; ++j) fmask0 |= 1ull << j;
     }
     const int elog = A.lmax - lvl + 1;
     for (int m = 0; m < 8; ++m) {
@@ -302,8 +335,24 @@ __device__ __noinline__ void deposit_tied_copies(const EvalArgs& A, float* tL, f
                   qz = copy_offset(oz, ties, 4, m, half);
         const float rx = small_int_to_float(qx) + v0.z, ry = small_int_to_float(qy) + v0.w,
                     rz = small_int_to_float(qz) + v1.x;
+        int i = i0;
+        unsigned long long fmask = fmask0;
+        if (colmap) {
+            const float pd2 = sq3_rn(rx, ry, rz);
+            i = fixup_f(guess_bin(pd2, lp), pd2, thr, nb);
+            if (thick) {
+                const float d = sqrtf(pd2);
+                const float dl = fmaxf(d - sd, 0.0f), dh = d + sd;
+                const int ilo = fixup_f(guess_bin(dl * dl, lp), pd2, lo, nb);
+                const int ihi = fixup_f(guess_bin(dh * dh, lp), pd2, hi, nb);
+                fmask = 0ull;
+                for (int j = ilo; j < ihi; ++j) fmask |= 1ull << j;
+            }
+        }
         const float beta = __ldg(R2 + i) / (rx * rx + ry * ry + rz * rz);
-        const int Kx = alpha_key(qx, elog), Ky = alpha_key(qy, elog), Kz = alpha_key(qz, elog);
+        const int Kx = colmap ? odd_key(rx, elog) : alpha_key(qx, elog);
+        const int Ky = colmap ? odd_key(ry, elog) : alpha_key(qy, elog);
+        const int Kz = colmap ? odd_key(rz, elog) : alpha_key(qz, elog);
         if (abs(Kx) > A.D || abs(Ky) > A.D || abs(Kz) > A.D) {
             atomicOr(A.err, kErrAlphaKey);
             continue;
@@ -319,7 +368,7 @@ __device__ __noinline__ void deposit_tied_copies(const EvalArgs& A, float* tL, f
             const float w = count_to_float(ent >> 16);
             atomicAdd(tL + c, w * bL);
             atomicAdd(tA + c, w * bA);
-            if (THICK && v1.w > 0.0f) {
+            if (thick) {
                 const float wn = w * inv_s3;
                 atomicAdd(tLk + c, wn * v1.y * wt);
                 atomicAdd(tAk + c, v1.z * wt);
@@ -345,7 +394,7 @@ __device__ __noinline__ void deposit_tied_copies(const EvalArgs& A, float* tL, f
 //   rays:    threads integrate the rays' segments inside out (thin tiles with spare
 //            threads cut each ray into consecutive parts joined by their transmission),
 //            then the team reduces J and F.
-template <int NPIX, bool THICK, int WPT, bool PERIODIC>
+template <int NPIX, bool THICK, int WPT, bool GENERAL>
 __global__ void __launch_bounds__(WPT * 32, min_warps_per_sm(NPIX, THICK) / WPT)
     k_evaluate(EvalArgs a, const EvalArgs* __restrict__ boxes, const int64_t* __restrict__ box_start, int nbox) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -475,7 +524,7 @@ __global__ void __launch_bounds__(WPT * 32, min_warps_per_sm(NPIX, THICK) / WPT)
                 ox = gg.x - tx;
                 oy = gg.y - ty;
                 oz = (gg.z & 0xffffff) - tz;
-                if (PERIODIC && A.periodic) {
+                if (GENERAL && A.periodic) {
                     const int half = 1 << A.lmax;
                     if (A.periodic & 1) ox = closest_copy(ox, half, 1, ties);
                     if (A.periodic & 2) oy = closest_copy(oy, half, 2, ties);
@@ -506,20 +555,26 @@ __global__ void __launch_bounds__(WPT * 32, min_warps_per_sm(NPIX, THICK) / WPT)
             // of one segment); thick deposits stay with the node's thread.
             int ne = 0, ebase = 0, cbase = 0;
             float bL = 0.0f, bA = 0.0f;
-            if (PERIODIC && acc && ties) {
+            if (GENERAL && acc && ties) {
                 deposit_tied_copies<NPIX, THICK>(A, tL, tA, tLk, tAk, tVk, tQk, flags, node, ox, oy, oz, ties, lvl,
                                                  d2, tl, lp);
             } else if (acc) {
                 // the float distance only guesses the segment; the integer d^2 decides it
                 const float fx = small_int_to_float(ox), fy = small_int_to_float(oy), fz = small_int_to_float(oz);
                 const float fd2 = fx * fx + fy * fy + fz * fz;
-                const int i = fixup(guess_bin(fd2, lp), d2, thr, nb);
                 const float4 v0 = __ldg(A.thin + node);
                 const float4 v1 = __ldg(A.thick + node);
                 const float rx = fx + v0.z, ry = fy + v0.w, rz = fz + v1.x;
+                // mapping at the centre of luminosity (Sec. 6): segment, straddles and key
+                // from the COL position in FP32 for nodes whose COL is off centre
+                const bool colmap = GENERAL && A.col_mapping && (v0.z != 0.0f || v0.w != 0.0f || v1.x != 0.0f);
+                const float pd2 = colmap ? sq3_rn(rx, ry, rz) : 0.0f;
+                const int i = colmap ? fixup_f(guess_bin(pd2, lp), pd2, thr, nb) : fixup(guess_bin(fd2, lp), d2, thr, nb);
                 const float beta = __ldg(R2 + i) / (rx * rx + ry * ry + rz * rz);
                 const int elog = A.lmax - lvl + 1;
-                const int Kx = alpha_key(ox, elog), Ky = alpha_key(oy, elog), Kz = alpha_key(oz, elog);
+                const int Kx = colmap ? odd_key(rx, elog) : alpha_key(ox, elog);
+                const int Ky = colmap ? odd_key(ry, elog) : alpha_key(oy, elog);
+                const int Kz = colmap ? odd_key(rz, elog) : alpha_key(oz, elog);
                 if (abs(Kx) > A.D || abs(Ky) > A.D || abs(Kz) > A.D) {
                     atomicOr(A.err, kErrAlphaKey);
                 } else {
@@ -534,11 +589,13 @@ __global__ void __launch_bounds__(WPT * 32, min_warps_per_sm(NPIX, THICK) / WPT)
                     if (THICK && v1.w > 0.0f) {
                         const int64_t* lo = A.str_lo + ((int64_t)tl * (A.lmax + 1) + lvl) * nb;
                         const int64_t* hi = A.str_hi + ((int64_t)tl * (A.lmax + 1) + lvl) * nb;
-                        const float d = sqrtf(fd2);
+                        const float d = sqrtf(colmap ? pd2 : fd2);
                         const float sd = 0.8660254f * (float)(2 << (A.lmax - lvl));
                         const float dl = fmaxf(d - sd, 0.0f), dh = d + sd;
-                        const int ilo = fixup(guess_bin(dl * dl, lp), d2, lo, nb);
-                        const int ihi = fixup(guess_bin(dh * dh, lp), d2, hi, nb);
+                        const int ilo = colmap ? fixup_f(guess_bin(dl * dl, lp), pd2, lo, nb)
+                                               : fixup(guess_bin(dl * dl, lp), d2, lo, nb);
+                        const int ihi = colmap ? fixup_f(guess_bin(dh * dh, lp), pd2, hi, nb)
+                                               : fixup(guess_bin(dh * dh, lp), d2, hi, nb);
                         unsigned long long fmask = 0ull;
                         for (int j = ilo; j < ihi; ++j) fmask |= 1ull << j;
                         for (int e = e0; e < e1; ++e) {
@@ -833,7 +890,7 @@ size_t stack_bytes_for(int wpt, int lmax, int blocks) {
     return (size_t)blocks * (size_t)(32 * wpt * (lmax + 1) + 64) * sizeof(int);
 }
 
-template <int NPIX, bool THICK, int WPT, bool PERIODIC>
+template <int NPIX, bool THICK, int WPT, bool GENERAL>
 treeray_status launch_team(treeray_ctx* c, const EvalArgs& a, const EvalArgs* boxes,
                            const int64_t* box_start, int nbox, int layout_lmax, cudaStream_t s) {
     constexpr int nq = THICK ? 6 : 2;
@@ -847,7 +904,7 @@ treeray_status launch_team(treeray_ctx* c, const EvalArgs& a, const EvalArgs* bo
         set_error("evaluate: the per-target ray tile (npix x nbins) exceeds shared memory");
         return TREERAY_EINVAL;
     }
-    auto kern = k_evaluate<NPIX, THICK, WPT, PERIODIC>;
+    auto kern = k_evaluate<NPIX, THICK, WPT, GENERAL>;
     TR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     TR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WPT * 32, smem));
@@ -869,13 +926,13 @@ treeray_status launch_team(treeray_ctx* c, const EvalArgs& a, const EvalArgs* bo
     return TREERAY_OK;
 }
 
-template <int NPIX, bool THICK, bool PERIODIC>
+template <int NPIX, bool THICK, bool GENERAL>
 treeray_status launch_wpt(treeray_ctx* c, int wpt, const EvalArgs& a, const EvalArgs* boxes,
                           const int64_t* box_start, int nbox, int layout_lmax, cudaStream_t s) {
     switch (wpt) {
-        case 2: return launch_team<NPIX, THICK, 2, PERIODIC>(c, a, boxes, box_start, nbox, layout_lmax, s);
-        case 8: return launch_team<NPIX, THICK, 8, PERIODIC>(c, a, boxes, box_start, nbox, layout_lmax, s);
-        default: return launch_team<NPIX, THICK, 4, PERIODIC>(c, a, boxes, box_start, nbox, layout_lmax, s);
+        case 2: return launch_team<NPIX, THICK, 2, GENERAL>(c, a, boxes, box_start, nbox, layout_lmax, s);
+        case 8: return launch_team<NPIX, THICK, 8, GENERAL>(c, a, boxes, box_start, nbox, layout_lmax, s);
+        default: return launch_team<NPIX, THICK, 4, GENERAL>(c, a, boxes, box_start, nbox, layout_lmax, s);
     }
 }
 
@@ -883,7 +940,8 @@ template <int NPIX>
 treeray_status launch_kind(treeray_ctx* c, bool thick, bool periodic, int wpt, const EvalArgs& a,
                            const EvalArgs* boxes, const int64_t* box_start, int nbox, int layout_lmax,
                            cudaStream_t s) {
-    // the periodic instantiations carry the closest-copy code; isolated grids run without it
+    // the general instantiations carry the closest-copy and COL-mapping code; isolated grids
+    // mapped at geometric centres run without it
     if (periodic)
         return thick ? launch_wpt<NPIX, true, true>(c, wpt, a, boxes, box_start, nbox, layout_lmax, s)
                      : launch_wpt<NPIX, false, true>(c, wpt, a, boxes, box_start, nbox, layout_lmax, s);
@@ -904,7 +962,8 @@ treeray_status dispatch_team(treeray_ctx* c, bool thick, bool periodic, int wpt,
 }
 
 treeray_status dispatch_eval(treeray_ctx* c, const EvalArgs& a, cudaStream_t s) {
-    return dispatch_team(c, c->has_thick || c->force_thick, c->p.periodic != 0, c->wpt, a, nullptr, nullptr, 1,
+    return dispatch_team(c, c->has_thick || c->force_thick, c->p.periodic != 0 || c->p.col_mapping != 0, c->wpt, a,
+                         nullptr, nullptr, 1,
                          c->lmax, s);
 }
 
@@ -941,6 +1000,7 @@ EvalArgs make_args(treeray_ctx* c, const int32_t* targets, int64_t n) {
     a.D = c->ht.D;
     a.npix = c->p.npix;
     a.periodic = c->p.periodic;
+    a.col_mapping = c->p.col_mapping;
     a.inv_s3 = 1.0f / (float)(c->ht.s * c->ht.s * c->ht.s);
     a.u = c->u;
     a.inv_u2 = 1.0 / (c->u * c->u);
@@ -1077,7 +1137,8 @@ treeray_status autotune(treeray_ctx* c, int64_t n_sample, int* best, float* ms, 
         treeray_status rc;
         for (int rep = 0; rep < 2; ++rep) {  // the second launch is timed
             if (rep == 1) TR_CUDA(cudaEventRecord(e0, s));
-            rc = dispatch_team(c, c->has_thick || c->force_thick, c->p.periodic != 0, cand[k], a, nullptr, nullptr,
+            rc = dispatch_team(c, c->has_thick || c->force_thick, c->p.periodic != 0 || c->p.col_mapping != 0,
+                               cand[k], a, nullptr, nullptr,
                                1, c->lmax, s);
             if (rc != TREERAY_OK) return rc;
         }
@@ -1110,7 +1171,7 @@ struct treeray_batch {
         int64_t* d_start = nullptr;
         unsigned long long* d_queue = nullptr;
         int max_lmax = 0;
-        bool periodic = false;  // some box of the group has periodic axes
+        bool periodic = false;  // some box has periodic axes or COL mapping (general kernel)
     };
     std::vector<treeray_t> ctx;
     Group g[2];
@@ -1158,7 +1219,7 @@ treeray_status treeray_batch_create(const treeray_t* ctxs, int n_boxes, treeray_
         g.desc.push_back(a);
         g.start.push_back(g.start.back() + c->nleaves);
         g.max_lmax = std::max(g.max_lmax, c->lmax);
-        g.periodic = g.periodic || c->p.periodic != 0;
+        g.periodic = g.periodic || c->p.periodic != 0 || c->p.col_mapping != 0;
     }
     auto fail = [&](treeray_status rc) {
         treeray_batch_destroy(b);

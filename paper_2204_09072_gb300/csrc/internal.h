@@ -47,7 +47,7 @@ int healpix_ang2pix(int nside, double x, double y, double z);
 void healpix_pix2vec(int nside, int pix, double* v);
 void alpha_counts(int npix, int s, const int64_t* K, int32_t* counts);
 // Build the alpha table for the keys the walk can reach on this grid shape.
-void build_alpha_table(HostTables& t, double theta, int lmax, bool amr);
+void build_alpha_table(HostTables& t, double theta, int lmax, bool amr, bool col);
 // Evaluation radii R_i (half-cells of the finest level) for a target of edge Et.
 void radii(int nbins, int lmax, int periodic, int spacing, int64_t Et, double* R);
 

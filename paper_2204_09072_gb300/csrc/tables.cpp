@@ -147,21 +147,25 @@ inline int key_class(int64_t k) {
 // only when accepted by the opening criterion, i.e. at 8 d / E > 8 / theta, unless the
 // grid is AMR (coarser and finer leaves next to the target, classes 1-3 anywhere).
 namespace {
-// tables already built in this process, keyed by (npix, samples, theta, D, amr)
+// tables already built in this process, keyed by (npix, samples, theta, D, amr, col)
 std::mutex g_tab_mutex;
-std::map<std::tuple<int, int, double, int64_t, bool>, std::pair<std::vector<int32_t>, std::vector<uint32_t>>>
+std::map<std::tuple<int, int, double, int64_t, bool, bool>,
+         std::pair<std::vector<int32_t>, std::vector<uint32_t>>>
     g_tab_cache;
 }  // namespace
 
-void build_alpha_table(HostTables& t, double theta, int lmax, bool amr) {
+// col: nodes may be mapped at their centre of luminosity, which moves a key by up to 4
+// per axis and gives odd keys at any distance
+void build_alpha_table(HostTables& t, double theta, int lmax, bool amr, bool col) {
     const double th = theta > 1e-6 ? theta : 1e-6;
     const double reach = std::max(2.0 / th, std::sqrt(3.0)) + 0.5 * std::sqrt(3.0);
-    int64_t D = (int64_t)std::ceil(8.0 * reach) + 1;
-    const int64_t cap = 8 * ((int64_t)1 << lmax) + 1;
+    const int64_t extra = col ? 4 : 0;
+    int64_t D = (int64_t)std::ceil(8.0 * reach) + 1 + extra;
+    const int64_t cap = 8 * ((int64_t)1 << lmax) + 1 + extra;
     D = std::min(D, cap);
-    D = std::min<int64_t>(D, 128);
+    D = std::min<int64_t>(D, 128 + extra);
     t.D = (int)D;
-    const auto key = std::make_tuple(t.npix, t.s, theta, D, amr);
+    const auto key = std::make_tuple(t.npix, t.s, theta, D, amr, col);
     {
         std::lock_guard<std::mutex> lock(g_tab_mutex);
         auto it = g_tab_cache.find(key);
@@ -184,7 +188,7 @@ void build_alpha_table(HostTables& t, double theta, int lmax, bool amr) {
                 if (x == 0 && y == 0 && z == 0) continue;  // own cell, uniform weights
                 if (!amr) {
                     if (c == 3) continue;
-                    if ((c == 1 || c == 2) && (double)(x * x + y * y + z * z) < shell2) continue;
+                    if ((c == 1 || (c == 2 && !col)) && (double)(x * x + y * y + z * z) < shell2) continue;
                 }
                 keys.push_back(((z + D) * W + (y + D)) * W + (x + D));
             }

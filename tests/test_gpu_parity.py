@@ -36,6 +36,11 @@ CASES = {
     # radii growing quadratically, and the opening angle matched to the ray size
     "rand16_quadratic": lambda: synth.random_uniform(16, seed=7, thick_frac=0.1, n_stars=2, bin_spacing=1),
     "clump16_raytheta": lambda: synth.gaussian_clump(16, theta=-1.0),
+    # accepted nodes mapped at their centre of luminosity; with periodic axes too
+    "clump16_col": lambda: synth.gaussian_clump(16, col_mapping=1),
+    "rand16_col": lambda: synth.random_uniform(16, seed=8, thick_frac=0.15, n_stars=3, col_mapping=1),
+    "rand16_periodic_col": lambda: synth.random_uniform(16, seed=9, thick_frac=0.1, n_stars=2, periodic=7,
+                                                        col_mapping=1),
 }
 
 
@@ -240,7 +245,7 @@ def test_errors_are_reported():
 
 
 @pytest.mark.parametrize("name", ["clump16", "rand16_thick", "rand16_periodic", "amr_periodic_x", "clump16_s4",
-                                  "rand16_quadratic", "clump16_raytheta"])
+                                  "rand16_quadratic", "clump16_raytheta", "rand16_col", "rand16_periodic_col"])
 def test_walk_stats_exact(orc, name):
     """Visited/accepted/angular-entry totals of the GPU walk equal the oracle's."""
     import torch

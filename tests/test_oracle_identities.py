@@ -272,3 +272,47 @@ def test_quadratic_radii_and_ray_matched_theta(orc):
     wt = synth.gaussian_clump(16, theta=-1.0)
     w5 = synth.gaussian_clump(16, theta=math.sqrt(4 * math.pi / 48))
     assert np.array_equal(orc.Tree(wt).accepted(2080), orc.Tree(w5).accepted(2080))
+
+
+def test_col_mapping_identities(orc):
+    """Mapping at the centre of luminosity (Sec. 6): emission only, J still equals the
+    sum over accepted nodes of L / (16 pi^2 r_COL^2) (beta cancels R_i^2 whatever segment
+    the COL picks); leaves (COL at the centre) map as before, so with every leaf accepted
+    the result equals geometric mapping exactly."""
+    w = synth.gaussian_clump(16, kappa_ext_scale=0.0, col_mapping=1)
+    t = orc.Tree(w)
+    ex = t.export()
+    u = t.unit_cm
+    for tk in [0, 1234, 2080, 4095]:
+        ids = t.accepted(tk)
+        own = ex["leaf"][ids] == tk
+        c = ex["vals"][ids, 8:11]
+        tc = ex["centre"][ids[own]][0]
+        r2 = (((c - tc) * u) ** 2).sum(1)
+        r2[own] = (0.5 * w.box_cm / 16) ** 2
+        J, _ = t.evaluate([tk])
+        assert math.isclose(J[0], (ex["vals"][ids, 0] / (16 * math.pi ** 2 * r2)).sum(), rel_tol=1e-12)
+    a = orc.Tree(synth.random_uniform(8, seed=2, theta=1e-9, col_mapping=1)).evaluate()
+    b = orc.Tree(synth.random_uniform(8, seed=2, theta=1e-9)).evaluate()
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_col_mapping_points_flux_at_an_offcentre_source(orc):
+    """A lone source off the centre of the nodes that carry it: mapped at the COL, the flux
+    seen by distant targets points closer to the true direction than mapped at the
+    geometric centres (the reason the paper shifts nodes to their centre of emission)."""
+    n = 32
+    errs = {}
+    for col in (0, 1):
+        w = synth.point_source(n, kappa0=0.0, cell=(5, 9, 13), col_mapping=col)
+        t = orc.Tree(w)
+        cen = synth.cell_centres(n, w.box_cm)
+        src = w.star_pos[0]
+        tg = np.array([k for k in range(0, n ** 3, 997)])
+        _, F = t.evaluate(tg)
+        true = cen[tg] - src
+        true /= np.linalg.norm(true, axis=1, keepdims=True)
+        far = np.linalg.norm(cen[tg] - src, axis=1) > 0.4 * w.box_cm
+        cosang = (F[far] * true[far]).sum(1) / np.linalg.norm(F[far], axis=1)
+        errs[col] = np.degrees(np.arccos(np.clip(cosang, -1, 1)))
+    assert errs[1].mean() < errs[0].mean()
