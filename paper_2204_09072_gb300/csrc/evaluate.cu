@@ -404,7 +404,7 @@ __global__ void __launch_bounds__(WPT * 32, min_warps_per_sm(NPIX, THICK) / WPT)
     const int cells = nb * NPIX;
     constexpr int nq = THICK ? 6 : 2;
     // layout: tile [nq][nb][NPIX] f32 | THICK: flags [NPIX] u64 |
-    //         per warp: node buffer int4[32], entry owners u8[kOwnerCap]
+    //         THICK: per warp node buffer int4[32] | per warp entry owners u8[kOwnerCap]
     // The team's stack of child groups is this block's slice of a global scratch array:
     // it stays in L1, and leaving it out of shared memory lets more teams share an SM.
     float* tL = reinterpret_cast<float*>(smem);
@@ -414,9 +414,12 @@ __global__ void __launch_bounds__(WPT * 32, min_warps_per_sm(NPIX, THICK) / WPT)
     float* tVk = tAk + cells;
     float* tQk = tVk + cells;
     unsigned long long* flags = reinterpret_cast<unsigned long long*>(smem + (size_t)nq * cells * 4);
+    // each entry's node data: thin kernels take it from the owner lane by shuffles (fewer
+    // shared-memory operations and registers, measured faster); thick kernels, whose
+    // occupancy is bound by their larger tile anyway, through a per-warp node buffer
     int4* nodebufs = reinterpret_cast<int4*>(smem + (size_t)nq * cells * 4 + (THICK ? NPIX * 8 : 0));
     int4* nodebuf = nodebufs + warp * 32;
-    unsigned char* owner = reinterpret_cast<unsigned char*>(nodebufs + WPT * 32) + warp * kOwnerCap;
+    unsigned char* owner = reinterpret_cast<unsigned char*>(nodebufs + (THICK ? WPT * 32 : 0)) + warp * kOwnerCap;
     const int stack_cap = a.stack_cap;
     int* stack = a.stack + (size_t)blockIdx.x * stack_cap;
     __shared__ int s_sp, s_overflow;
@@ -626,26 +629,57 @@ __global__ void __launch_bounds__(WPT * 32, min_warps_per_sm(NPIX, THICK) / WPT)
             if (tw > 0) {
                 if (tw <= kOwnerCap) {
                     if (ne > 0) {
-                        nodebuf[lane] = make_int4(cbase, ebase - pre, __float_as_int(bL), __float_as_int(bA));
+                        if (THICK) nodebuf[lane] = make_int4(cbase, ebase - pre, __float_as_int(bL), __float_as_int(bA));
                         for (int k = 0; k < ne; ++k) owner[pre + k] = (unsigned char)lane;
                     }
                     __syncwarp();
-                    // two entries per lane per pass: their loads and atomics overlap
-                    for (int r = lane; r < tw; r += 64) {
-                        const int r2 = r + 32;
-                        const int4 nd = nodebuf[owner[r]];
-                        const int4 nd2 = r2 < tw ? nodebuf[owner[r2]] : nd;
-                        const uint32_t ent = __ldg(A.aent + nd.y + r);
-                        const uint32_t ent2 = r2 < tw ? __ldg(A.aent + nd2.y + r2) : 0u;
-                        const int c = nd.x + (int)(ent & 0xffffu);
-                        const float w = count_to_float(ent >> 16);
-                        atomicAdd(tL + c, w * __int_as_float(nd.z));
-                        atomicAdd(tA + c, w * __int_as_float(nd.w));
-                        if (r2 < tw) {
-                            const int c2 = nd2.x + (int)(ent2 & 0xffffu);
-                            const float w2 = count_to_float(ent2 >> 16);
-                            atomicAdd(tL + c2, w2 * __int_as_float(nd2.z));
-                            atomicAdd(tA + c2, w2 * __int_as_float(nd2.w));
+                    if constexpr (THICK) {
+                        // two entries per lane per pass: their loads and atomics overlap
+                        for (int r = lane; r < tw; r += 64) {
+                            const int r2 = r + 32;
+                            const int4 nd = nodebuf[owner[r]];
+                            const int4 nd2 = r2 < tw ? nodebuf[owner[r2]] : nd;
+                            const uint32_t ent = __ldg(A.aent + nd.y + r);
+                            const uint32_t ent2 = r2 < tw ? __ldg(A.aent + nd2.y + r2) : 0u;
+                            const int c = nd.x + (int)(ent & 0xffffu);
+                            const float w = count_to_float(ent >> 16);
+                            atomicAdd(tL + c, w * __int_as_float(nd.z));
+                            atomicAdd(tA + c, w * __int_as_float(nd.w));
+                            if (r2 < tw) {
+                                const int c2 = nd2.x + (int)(ent2 & 0xffffu);
+                                const float w2 = count_to_float(ent2 >> 16);
+                                atomicAdd(tL + c2, w2 * __int_as_float(nd2.z));
+                                atomicAdd(tA + c2, w2 * __int_as_float(nd2.w));
+                            }
+                        }
+                    } else {
+                        // two entries per lane per pass; each entry's node data comes from its
+                        // owner lane by shuffles (warp-uniform passes, full-mask shuffles)
+                        const int eb = ebase - pre;
+                        for (int r0 = 0; r0 < tw; r0 += 64) {
+                            const int r = r0 + lane, r2 = r + 32;
+                            const int o1 = r < tw ? (int)owner[r] : 0;
+                            const int o2 = r2 < tw ? (int)owner[r2] : 0;
+                            const int4 nd = make_int4(__shfl_sync(full, cbase, o1), __shfl_sync(full, eb, o1),
+                                                      __shfl_sync(full, __float_as_int(bL), o1),
+                                                      __shfl_sync(full, __float_as_int(bA), o1));
+                            const int4 nd2 = make_int4(__shfl_sync(full, cbase, o2), __shfl_sync(full, eb, o2),
+                                                       __shfl_sync(full, __float_as_int(bL), o2),
+                                                       __shfl_sync(full, __float_as_int(bA), o2));
+                            const uint32_t ent = r < tw ? __ldg(A.aent + nd.y + r) : 0u;
+                            const uint32_t ent2 = r2 < tw ? __ldg(A.aent + nd2.y + r2) : 0u;
+                            if (r < tw) {
+                                const int c = nd.x + (int)(ent & 0xffffu);
+                                const float w = count_to_float(ent >> 16);
+                                atomicAdd(tL + c, w * __int_as_float(nd.z));
+                                atomicAdd(tA + c, w * __int_as_float(nd.w));
+                            }
+                            if (r2 < tw) {
+                                const int c2 = nd2.x + (int)(ent2 & 0xffffu);
+                                const float w2 = count_to_float(ent2 >> 16);
+                                atomicAdd(tL + c2, w2 * __int_as_float(nd2.z));
+                                atomicAdd(tA + c2, w2 * __int_as_float(nd2.w));
+                            }
                         }
                     }
                     __syncwarp();
@@ -896,7 +930,8 @@ treeray_status launch_team(treeray_ctx* c, const EvalArgs& a, const EvalArgs* bo
     constexpr int nq = THICK ? 6 : 2;
     EvalArgs b = a;
     b.stack_cap = (int)(stack_bytes_for(WPT, layout_lmax, 1) / sizeof(int));
-    const size_t smem = (size_t)nq * a.nbins * NPIX * 4 + (THICK ? NPIX * 8 : 0) + (size_t)WPT * (32 * 16 + kOwnerCap);
+    const size_t smem = (size_t)nq * a.nbins * NPIX * 4 + (THICK ? NPIX * 8 + (size_t)WPT * 32 * 16 : 0) +
+                        (size_t)WPT * kOwnerCap;
     int smem_optin = 0, sms = 0;
     TR_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
     TR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
