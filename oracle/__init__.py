@@ -86,6 +86,10 @@ def lib():
             L.or_target_radii.argtypes = [C.c_void_p, C.c_int64, P(C.c_double)]
             L.or_alpha_key.argtypes = [P(C.c_int64), C.c_int64, P(C.c_int64)]
             L.or_alpha_counts.argtypes = [C.c_int, C.c_int, P(C.c_int64), P(C.c_int)]
+            L.or_alpha_counts_rot.argtypes = [C.c_int, C.c_int, P(C.c_int64), P(C.c_double),
+                                              P(C.c_int)]
+            L.or_set_orientations.argtypes = [C.c_void_p, C.c_int, P(C.c_double), P(C.c_uint8)]
+            L.or_set_orientations.restype = C.c_int
             L.or_ang2pix.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double]
             L.or_ang2pix.restype = C.c_int
             L.or_pix2vec.argtypes = [C.c_int, C.c_int, P(C.c_double)]
@@ -125,10 +129,15 @@ def alpha_key(o, E: int) -> np.ndarray:
     return K
 
 
-def alpha_counts(npix: int, K, s: int = 8) -> np.ndarray:
+def alpha_counts(npix: int, K, s: int = 8, rot=None) -> np.ndarray:
+    """Angular-kernel hit counts of key K; rot: a 3x3 rotation of the ray set."""
     K = np.ascontiguousarray(K, dtype=np.int64)
     out = np.zeros(npix, np.int32)
-    lib().or_alpha_counts(npix, s, _p(K, C.c_int64), _p(out, C.c_int))
+    if rot is None:
+        lib().or_alpha_counts(npix, s, _p(K, C.c_int64), _p(out, C.c_int))
+    else:
+        R = np.ascontiguousarray(rot, dtype=np.float64).reshape(9)
+        lib().or_alpha_counts_rot(npix, s, _p(K, C.c_int64), _p(R, C.c_double), _p(out, C.c_int))
     return out
 
 
@@ -194,6 +203,17 @@ class Tree:
         if rc != 0:
             raise RuntimeError(f"oracle evaluate failed ({rc})")
         return J, F
+
+    def set_orientations(self, rot, orient=None):
+        """Several HEALPix orientations: rot [k, 3, 3] rotations, orient [n_leaves] uint8
+        (None: leaf mod k). An empty rot goes back to the single unturned ray set."""
+        R = np.ascontiguousarray(rot, dtype=np.float64).reshape(-1)
+        k = len(R) // 9
+        o = None if orient is None else np.ascontiguousarray(orient, np.uint8)
+        self._orient = (R, o)
+        rc = lib().or_set_orientations(self.h, k, _p(R, C.c_double) if k else None, _p(o, C.c_uint8))
+        if rc != 0:
+            raise ValueError("bad orientations")
 
     def radpressure(self, J, F, targets=None):
         n = len(J)

@@ -207,8 +207,12 @@ static void or_key(const int64_t* o, int64_t E, int64_t* K) {
     }
 }
 
-/* Hit counts of the s^3 sample directions per pixel for key K. counts: int[npix]. */
-void or_alpha_counts(int npix, int s, const int64_t* K, int* counts) {
+/* Hit counts of the s^3 sample directions per pixel for key K. counts: int[npix].
+ * rot (may be NULL): the ray set of a turned HEALPix orientation (Sec. 6), a row-major
+ * rotation R; ray h of that orientation points along R n_h, so a sample direction v is
+ * counted in ray h when R^T v lies in pixel h. (R^T v)_a = R_0a v_x + R_1a v_y + R_2a v_z,
+ * summed in that order. */
+void or_alpha_counts_rot(int npix, int s, const int64_t* K, const double* rot, int* counts) {
     int nside = or_nside(npix);
     memset(counts, 0, sizeof(int) * npix);
     for (int c = 0; c < s; ++c)
@@ -218,8 +222,20 @@ void or_alpha_counts(int npix, int s, const int64_t* K, int* counts) {
                 double vx = (double)(2 * s * K[0] / 8 + 2 * a + 1 - s);
                 double vy = (double)(2 * s * K[1] / 8 + 2 * b + 1 - s);
                 double vz = (double)(2 * s * K[2] / 8 + 2 * c + 1 - s);
+                if (rot) {
+                    double wx = rot[0] * vx + rot[3] * vy + rot[6] * vz;
+                    double wy = rot[1] * vx + rot[4] * vy + rot[7] * vz;
+                    double wz = rot[2] * vx + rot[5] * vy + rot[8] * vz;
+                    vx = wx;
+                    vy = wy;
+                    vz = wz;
+                }
                 counts[or_ang2pix(nside, vx, vy, vz)]++;
             }
+}
+
+void or_alpha_counts(int npix, int s, const int64_t* K, int* counts) {
+    or_alpha_counts_rot(npix, s, K, NULL, counts);
 }
 
 /* Lazily filled alpha cache: open-addressing hash table of fixed capacity,
@@ -230,6 +246,7 @@ typedef struct {
     int npix, s, D;
     uint64_t* keys;   /* packed key + 1, 0 = empty */
     int** lists;      /* per slot: pairs (pixel, count), terminated by -1 */
+    const double* rot;/* orientation of the ray set (NULL: the unturned HEALPix grid) */
 } or_alpha_table;
 
 static uint64_t or_pack(const int64_t* K) {
@@ -239,7 +256,7 @@ static uint64_t or_pack(const int64_t* K) {
 
 static int* or_alpha_make(const or_alpha_table* t, const int64_t* K) {
     int* counts = (int*)malloc(sizeof(int) * t->npix);
-    or_alpha_counts(t->npix, t->s, K, counts);
+    or_alpha_counts_rot(t->npix, t->s, K, t->rot, counts);
     int n = 0;
     for (int h = 0; h < t->npix; ++h) n += counts[h] > 0;
     int* out = (int*)malloc(sizeof(int) * (2 * n + 1));
@@ -316,6 +333,11 @@ typedef struct {
     double* rho;
     or_alpha_table alpha;
     int level_first[64], level_count[64];
+    /* several HEALPix orientations (Sec. 6); n_orient = 0: the single unturned one */
+    int n_orient;
+    double* rot;            /* [n_orient][9] row-major rotations R_o */
+    uint8_t* orient;        /* per leaf: its orientation (caller leaf index) */
+    or_alpha_table* oalpha; /* [n_orient] angular kernels of the turned ray sets */
 } or_tree;
 
 static uint64_t or_morton(uint64_t x, uint64_t y, uint64_t z, int bits) {
@@ -398,13 +420,31 @@ static double or_kappa(const or_params* p, double T, const float* kin, int64_t k
     return 1.0e-3 * (Tc * Tc); /* 0.1 cm^2/g x (T / 10 K)^2, Sec. 2 */
 }
 
+static void or_alpha_free(or_alpha_table* a) {
+    if (a->lists) {
+        for (int64_t i = 0; i < OR_HCAP; ++i) free(a->lists[i]);
+        free(a->lists);
+        free(a->keys);
+    }
+    a->lists = NULL;
+    a->keys = NULL;
+}
+
+static void or_orient_free(or_tree* t) {
+    for (int o = 0; o < t->n_orient; ++o) or_alpha_free(&t->oalpha[o]);
+    free(t->oalpha);
+    free(t->rot);
+    free(t->orient);
+    t->oalpha = NULL;
+    t->rot = NULL;
+    t->orient = NULL;
+    t->n_orient = 0;
+}
+
 void or_tree_free(or_tree* t) {
     if (!t) return;
-    if (t->alpha.lists) {
-        for (int64_t i = 0; i < OR_HCAP; ++i) free(t->alpha.lists[i]);
-        free(t->alpha.lists);
-        free(t->alpha.keys);
-    }
+    or_alpha_free(&t->alpha);
+    or_orient_free(t);
     free(t->nodes);
     free(t->leaf_node);
     free(t->leaf_level);
@@ -861,12 +901,62 @@ double or_ray_integrate(int nbins, int npix, double* Lth, double* Ath, double* L
 }
 
 /*
+ * Several HEALPix orientations (Sec. 6: with one orientation for every target the ray
+ * pattern shows in the radiation field; turning the ray set from target to target spreads
+ * it, at the price of one angular-kernel table per orientation).
+ * k orientations with rotations rot[k][9] (row-major; orthonormal with determinant +1,
+ * checked to 1e-9); orient[nleaves] (caller leaf order, may be NULL: leaf mod k) picks
+ * each target's orientation. Ray h of orientation o points along R_o n_h. k = 0 goes back
+ * to the single unturned grid. Returns 0, or -1 for a bad argument (nothing changed).
+ */
+int or_set_orientations(or_tree* t, int k, const double* rot, const uint8_t* orient) {
+    if (k < 0 || k > 255 || (k > 0 && !rot)) return -1;
+    for (int o = 0; o < k; ++o) {
+        const double* R = rot + 9 * o;
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                double d = R[3 * a] * R[3 * b] + R[3 * a + 1] * R[3 * b + 1] + R[3 * a + 2] * R[3 * b + 2];
+                if (fabs(d - (a == b ? 1.0 : 0.0)) > 1e-9) return -1;
+            }
+        double det = R[0] * (R[4] * R[8] - R[5] * R[7]) - R[1] * (R[3] * R[8] - R[5] * R[6]) +
+                     R[2] * (R[3] * R[7] - R[4] * R[6]);
+        if (det < 0.0) return -1;
+    }
+    if (orient)
+        for (int64_t i = 0; i < t->nleaves; ++i)
+            if ((int)orient[i] >= k) return -1;
+    or_orient_free(t);
+    if (k == 0) return 0;
+    t->rot = (double*)malloc(sizeof(double) * 9 * (size_t)k);
+    memcpy(t->rot, rot, sizeof(double) * 9 * (size_t)k);
+    t->orient = (uint8_t*)malloc((size_t)t->nleaves);
+    for (int64_t i = 0; i < t->nleaves; ++i) t->orient[i] = orient ? orient[i] : (uint8_t)(i % k);
+    t->oalpha = (or_alpha_table*)calloc((size_t)k, sizeof(or_alpha_table));
+    for (int o = 0; o < k; ++o) {
+        t->oalpha[o].npix = t->p.npix;
+        t->oalpha[o].s = t->p.alpha_s;
+        t->oalpha[o].keys = (uint64_t*)calloc(OR_HCAP, sizeof(uint64_t));
+        t->oalpha[o].lists = (int**)calloc(OR_HCAP, sizeof(int*));
+        t->oalpha[o].rot = t->rot + 9 * o;
+    }
+    t->n_orient = k;
+    return 0;
+}
+
+/* Angular-kernel table of a target leaf's orientation. */
+static or_alpha_table* or_target_alpha(or_tree* t, int64_t leaf) {
+    return t->n_orient > 0 ? &t->oalpha[t->orient[leaf]] : &t->alpha;
+}
+
+/*
  * Per-target evaluation: walk, mapping, integration and finalization.
  * Opening criterion (Sec. 4 intro): a node is opened when it appears larger than
  * theta_lim. Reading: open iff E^2 >= theta^2 d^2 (E edge, d distance from the
  * target centre to the node's geometric centre), and always open a node that
  * contains the target; leaves are always accepted.
  * Finalization (Sec. 4.4): F = sum_h -F^h n^h, J = (1/4 pi) sum_h F^h + J_src.
+ * With several orientations, target leaf l uses the rays of orientation o = orient[l]:
+ * its angular kernel and the directions R_o n^h.
  * targets: caller leaf indices; J[n], F[3n].
  */
 int or_evaluate(or_tree* t, int64_t ntargets, const int64_t* targets, double* J, double* F,
@@ -874,8 +964,22 @@ int or_evaluate(or_tree* t, int64_t ntargets, const int64_t* targets, double* J,
     const or_params* p = &t->p;
     int np = p->npix, nb = p->nbins;
     int nside = or_nside(np);
-    double* nhat = (double*)malloc(sizeof(double) * 3 * np);
-    for (int h = 0; h < np; ++h) or_pix2vec(nside, h, nhat + 3 * h);
+    int no = t->n_orient > 0 ? t->n_orient : 1;
+    double* nhat = (double*)malloc(sizeof(double) * 3 * np * (size_t)no);
+    for (int h = 0; h < np; ++h) {
+        double v[3];
+        or_pix2vec(nside, h, v);
+        for (int o = 0; o < no; ++o) { /* orientation o: R_o n^h */
+            for (int a = 0; a < 3; ++a) {
+                double w = v[a];
+                if (t->n_orient > 0) {
+                    const double* R = t->rot + 9 * o + 3 * a;
+                    w = R[0] * v[0] + R[1] * v[1] + R[2] * v[2];
+                }
+                nhat[3 * ((size_t)o * np + h) + a] = w;
+            }
+        }
+    }
     double th2 = p->theta * p->theta;
     int err = 0;
 #ifdef _OPENMP
@@ -905,6 +1009,8 @@ int or_evaluate(or_tree* t, int64_t ntargets, const int64_t* targets, double* J,
         for (int64_t q = 0; q < ntargets; ++q) {
             int64_t leaf = targets[q];
             const or_node* tn = &t->nodes[t->leaf_node[leaf]];
+            or_alpha_table* at = or_target_alpha(t, leaf);
+            const double* nh = nhat + 3 * (size_t)np * (t->n_orient > 0 ? t->orient[leaf] : 0);
             memset(buf, 0, sizeof(double) * 6 * cells);
             memset(ry.flag, 0, sizeof(uint64_t) * np);
             or_radii(nb, t->lmax, p->periodic, p->bin_spacing, tn->E, R);
@@ -931,7 +1037,7 @@ int or_evaluate(or_tree* t, int64_t ntargets, const int64_t* targets, double* J,
                 if (open) {
                     for (int k = 7; k >= 0; --k) stack[sp++] = nd->child[k];
                 } else if (!ties) {
-                    or_map_node(t, &t->alpha, nd, o, d2, R, &ry, 1.0);
+                    or_map_node(t, at, nd, o, d2, R, &ry, 1.0);
                 } else { /* every closest copy, 1/2 per tied axis */
                     int nt = ((ties & 1) != 0) + ((ties & 2) != 0) + ((ties & 4) != 0);
                     double w = 1.0 / (double)(1 << nt);
@@ -941,7 +1047,7 @@ int or_evaluate(or_tree* t, int64_t ntargets, const int64_t* targets, double* J,
                         int64_t oi[3];
                         for (int a = 0; a < 3; ++a)
                             oi[a] = ((ties >> a) & 1) ? (((m >> a) & 1) ? half : -half) : o[a];
-                        or_map_node(t, &t->alpha, nd, oi, d2, R, &ry, w);
+                        or_map_node(t, at, nd, oi, d2, R, &ry, w);
                     }
                 }
             }
@@ -959,9 +1065,9 @@ int or_evaluate(or_tree* t, int64_t ntargets, const int64_t* targets, double* J,
                 }
                 double Fh = or_ray_integrate(nb, np, Lr, Ar, Lkr, Akr, Vkr, Qkr, Rcm, ry.flag[h]);
                 Jsum += Fh;
-                Fx -= Fh * nhat[3 * h];
-                Fy -= Fh * nhat[3 * h + 1];
-                Fz -= Fh * nhat[3 * h + 2];
+                Fx -= Fh * nh[3 * h];
+                Fy -= Fh * nh[3 * h + 1];
+                Fz -= Fh * nh[3 * h + 2];
             }
             J[q] = Jsum / (4.0 * OR_PI) + t->Jsrc[leaf];
             F[3 * q] = Fx;
@@ -1220,7 +1326,7 @@ void or_walk_stats(or_tree* t, int64_t leaf, int64_t* out) {
                         oi[a] = ((ties >> a) & 1) ? (((m >> a) & 1) ? half : -half) : o[a];
                     int owned = 0;
                     or_node_key(t, nd, oi, K);
-                    const int* l = or_alpha_get(&t->alpha, K, &owned);
+                    const int* l = or_alpha_get(or_target_alpha(t, leaf), K, &owned);
                     int n = 0;
                     while (l[2 * n] >= 0) ++n;
                     ent += n;

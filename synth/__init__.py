@@ -397,3 +397,25 @@ def sample_targets(n_leaves: int, count: int, seed: int = 11) -> np.ndarray:
     rng = np.random.Generator(np.random.PCG64(seed))
     count = min(count, n_leaves)
     return np.sort(rng.choice(n_leaves, size=count, replace=False)).astype(np.int64)
+
+
+def random_rotations(count: int, seed: int = 13) -> np.ndarray:
+    """Seeded uniformly distributed rotations, row-major [count, 3, 3] float64: turned
+    orientations of the HEALPix ray set. Unit quaternions from three uniform numbers by
+    Shoemake's construction (Graphics Gems III, 1992), then the usual rotation matrix."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    u1, u2, u3 = rng.uniform(0.0, 1.0, (3, count))
+    a, b = np.sqrt(1.0 - u1), np.sqrt(u1)
+    x, y = a * np.sin(2 * math.pi * u2), a * np.cos(2 * math.pi * u2)
+    z, w = b * np.sin(2 * math.pi * u3), b * np.cos(2 * math.pi * u3)
+    R = np.empty((count, 3, 3))
+    R[:, 0, 0] = 1 - 2 * (y * y + z * z)
+    R[:, 0, 1] = 2 * (x * y - z * w)
+    R[:, 0, 2] = 2 * (x * z + y * w)
+    R[:, 1, 0] = 2 * (x * y + z * w)
+    R[:, 1, 1] = 1 - 2 * (x * x + z * z)
+    R[:, 1, 2] = 2 * (y * z - x * w)
+    R[:, 2, 0] = 2 * (x * z - y * w)
+    R[:, 2, 1] = 2 * (y * z + x * w)
+    R[:, 2, 2] = 1 - 2 * (x * x + y * y)
+    return R
