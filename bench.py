@@ -456,6 +456,68 @@ def run_sweep(args):
         c.close()
 
 
+def run_orientations(args):
+    """Several HEALPix orientations (Sec. 6) on the 128^3 cloud: evaluate time for k turned
+    ray sets (one seeded random orientation per cell) against the single unturned set,
+    and the residual of J at 48 rays against 192 rays (ray-matched opening angles, as the
+    paper's ray-count study): mean and spread over all cells, and the part of the spread
+    that survives averaging over 4^3-cell blocks (the coherent ray pattern) versus the
+    part that does not (cell-to-cell noise). One JSON line per k."""
+    import torch
+
+    import paper_2204_09072_gb300 as tr
+    import synth
+    dev = torch.device("cuda:0")
+
+    def ctx_for(npix):
+        w = synth.turbulent_cloud(128, npix=npix, theta=-1.0)
+        c = tr.Context(w.params)
+        c.build(w.box_cm, torch.as_tensor(w.rho, device=dev), torch.as_tensor(w.td, device=dev), n=128,
+                star_pos=w.star_pos, star_lum=w.star_lum)
+        return w, c
+
+    def timed_eval(c, n):
+        J = torch.empty(n, dtype=torch.float32, device=dev)
+        F = torch.empty(3 * n, dtype=torch.float64, device=dev)
+        c.evaluate(J, F)
+        ms = []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            c.evaluate(J, F)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        c.check()
+        return J.double().cpu().numpy(), statistics.median(ms)
+
+    w, c192 = ctx_for(192)
+    c192.autotune(65536)
+    J192, ms192 = timed_eval(c192, w.n_leaves)
+    c192.close()
+    w, c = ctx_for(48)
+    c.autotune(65536)
+    n = w.n_leaves
+    for k in (0, 4, 16, 64):
+        t0 = time.time()
+        if k:
+            rot = synth.random_rotations(k, seed=100 + k)
+            m = np.random.Generator(np.random.PCG64(200 + k)).integers(0, k, n).astype(np.uint8)
+            c.set_orientations(rot, torch.as_tensor(m, device=dev))
+        else:
+            c.set_orientations(np.zeros((0, 3, 3)))
+        t_tab = time.time() - t0
+        J, ms = timed_eval(c, n)
+        r = J / J192 - 1.0
+        blk = r.reshape(32, 4, 32, 4, 32, 4).mean(axis=(1, 3, 5))  # x-fastest cells -> 4^3 blocks
+        inner = r.reshape(32, 4, 32, 4, 32, 4) - blk[:, None, :, None, :, None]
+        print(json.dumps({"orientations": k, "workload": "turb128_npix48_raytheta", "ms_evaluate": ms,
+                          "ray_evals_per_s": n * 48 / (ms * 1e-3), "table_build_s": t_tab,
+                          "ms_evaluate_192": ms192, "resid_mean": float(r.mean()), "resid_std": float(r.std()),
+                          "resid_block4_std": float(blk.std()), "resid_in_block_std": float(inner.std())}))
+    c.close()
+
+
 def _cloud(n, seed, sigma, n_stars, npix, uv_heating=False):
     """Turbulent cloud with stars and an ionising flux field. The flux is a network
     feature; its UV dust heating is left out unless asked for: with it, dense cells near
@@ -748,6 +810,8 @@ def main():
                     help="training solves at the test resolution (seeds 200, 201, ...)")
     ap.add_argument("--amr-core", action="store_true",
                     help="collapsing-core AMR grid: throughput and the plain fixed point to 1e-4")
+    ap.add_argument("--orientations", action="store_true",
+                    help="several HEALPix orientations: cost and J residuals against 192 rays")
     ap.add_argument("--fp-max-iter", type=int, default=100)
     ap.add_argument("--fp-diag-iter", type=int, default=20)
     args = ap.parse_args()
@@ -763,6 +827,8 @@ def main():
         run_warmstart(args)
     elif args.amr_core:
         run_amr_core(args)
+    elif args.orientations:
+        run_orientations(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

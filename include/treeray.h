@@ -127,6 +127,30 @@ treeray_status treeray_create(const treeray_params* params, treeray_t* out);
 treeray_status treeray_destroy(treeray_t ctx);
 
 /*
+ * Several HEALPix orientations (Sec. 6: with one orientation for every target the rays
+ * imprint a ray-like pattern on the radiation field; turning the ray set from target to
+ * target breaks it up, at the price of one angular-kernel table per orientation).
+ *  k       number of orientations, 1..64; 0 goes back to the single unturned ray set
+ *          (the default).
+ *  rot     HOST double[9 k], row-major 3x3 rotations R_o (orthonormal to 1e-9,
+ *          determinant +1; copied). Ray h of orientation o points along R_o n_h, n_h the
+ *          HEALPix pixel centre; a direction v lies in ray h of orientation o when
+ *          R_o^T v lies in pixel h. The angular kernel of orientation o counts each of
+ *          a node's alpha_s^3 sample directions v in the pixel of R_o^T v, computed in
+ *          FP64 as (R^T v)_a = R_0a v_x + R_1a v_y + R_2a v_z.
+ *  orient  DEVICE uint8[N] (N leaves of the built grid, caller order; copied): the
+ *          orientation of each target, every value < k. NULL: leaf l uses l mod k. A
+ *          caller map needs a built tree, and a later build with another leaf count
+ *          replaces it by l mod k.
+ * The tables are rebuilt at once (host FP64, about 0.1-0.2 s per orientation at
+ * theta = 0.5) when a tree is built, else at the next build. Synchronises the device.
+ * EINVAL: k out of range, rot missing or not a rotation, a map value >= k, a map
+ * without k; ENOTBUILT: a map before any build; ENOMEM: the tables of all orientations
+ * outgrow 2^31 entries or device memory.
+ */
+treeray_status treeray_set_orientations(treeray_t ctx, int k, const double* rot, const uint8_t* orient);
+
+/*
  * Tree build (Sec. 4.1 and App. A): leaf quantities, Morton sort, node structure,
  * node moments and the centre of luminosity, plus the angular-kernel table.
  *  rho, Td         device float[N]: gas density (g/cm^3), dust temperature (K).
@@ -244,8 +268,9 @@ treeray_status treeray_set_warps_per_target(treeray_t ctx, int wpt);
  * Batches: many independent boxes (contexts with built trees, the same npix and nbins,
  * any grids and parameters otherwise) evaluated by one persistent launch whose work
  * counter spans the targets of all boxes, so uneven boxes balance across the GPU.
- * A batch records the boxes' trees when created; rebuilding a box invalidates it
- * (destroy and create again). Contexts must outlive the batch.
+ * A batch records the boxes' trees and ray orientations when created; rebuilding a box or
+ * changing its orientations invalidates it (destroy and create again). Contexts must
+ * outlive the batch.
  */
 typedef struct treeray_batch* treeray_batch_t;
 treeray_status treeray_batch_create(const treeray_t* ctxs, int n_boxes, treeray_batch_t* out);
@@ -386,6 +411,11 @@ treeray_status treeray_morton_order_noalloc(const treeray_grid* grid, uint64_t* 
  * per axis, written to counts[npix]. Needs no GPU; used to check the table builder.
  */
 treeray_status treeray_alpha_counts_host(int npix, int s, const int64_t* K, int32_t* counts);
+
+/* Host-only: the same counts for the ray set turned by the row-major rotation rot[9]
+ * (Sec. 6, several orientations): sample direction v counts in the pixel of R^T v. */
+treeray_status treeray_alpha_counts_rotated_host(int npix, int s, const int64_t* K, const double* rot,
+                                                 int32_t* counts);
 
 /* Number of CUDA kernels this context has launched since it was created
  * (instrumentation for benchmarks; counted on the host at each launch). */

@@ -74,6 +74,8 @@ def lib():
     L.treeray_leaf_export.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     L.treeray_accepted.argtypes = [vp, vp, i64, C.c_int32, vp, vp, vp]
     L.treeray_alpha_counts_host.argtypes = [C.c_int, C.c_int, vp, i32p]
+    L.treeray_alpha_counts_rotated_host.argtypes = [C.c_int, C.c_int, vp, vp, i32p]
+    L.treeray_set_orientations.argtypes = [vp, C.c_int, vp, vp]
     L.treeray_walk_stats.argtypes = [vp, vp, i64, vp, vp]
     L.treeray_refresh.argtypes = [vp, vp, vp]
     L.treeray_fixed_point.argtypes = [vp, vp, vp, vp, C.c_int, C.c_double, C.c_int,
@@ -100,7 +102,8 @@ def lib():
     for f in ("treeray_create", "treeray_destroy", "treeray_build", "treeray_evaluate",
               "treeray_radpressure", "treeray_uv_radpressure", "treeray_dust_temperature", "treeray_check",
               "treeray_tree_export", "treeray_leaf_export", "treeray_accepted",
-              "treeray_alpha_counts_host", "treeray_walk_stats", "treeray_morton_order_noalloc",
+              "treeray_alpha_counts_host", "treeray_alpha_counts_rotated_host", "treeray_set_orientations",
+              "treeray_walk_stats", "treeray_morton_order_noalloc",
               "treeray_refresh", "treeray_fixed_point", "treeray_autotune",
               "treeray_set_warps_per_target", "treeray_batch_create", "treeray_batch_destroy",
               "treeray_batch_evaluate", "treeray_features", "treeray_mlp_create",
@@ -135,13 +138,20 @@ def _stream(s):
     return C.c_void_p(s.cuda_stream)
 
 
-def alpha_counts_host(npix: int, s: int, K):
-    """Angular-kernel hit counts of key K (host-only call, needs no GPU)."""
+def alpha_counts_host(npix: int, s: int, K, rot=None):
+    """Angular-kernel hit counts of key K (host-only call, needs no GPU); rot: a 3x3
+    rotation of the ray set (C: treeray_alpha_counts_rotated_host)."""
     import numpy as np
     k = np.ascontiguousarray(K, dtype=np.int64)
     out = np.zeros(npix, np.int32)
-    _raise(lib().treeray_alpha_counts_host(npix, s, C.c_void_p(k.ctypes.data),
-                                           out.ctypes.data_as(C.POINTER(C.c_int32))))
+    if rot is None:
+        _raise(lib().treeray_alpha_counts_host(npix, s, C.c_void_p(k.ctypes.data),
+                                               out.ctypes.data_as(C.POINTER(C.c_int32))))
+    else:
+        r = np.ascontiguousarray(rot, dtype=np.float64).reshape(9)
+        _raise(lib().treeray_alpha_counts_rotated_host(npix, s, C.c_void_p(k.ctypes.data),
+                                                       C.c_void_p(r.ctypes.data),
+                                                       out.ctypes.data_as(C.POINTER(C.c_int32))))
     return out
 
 
@@ -270,6 +280,19 @@ class Context:
         ms = (C.c_float * 3)()
         _raise(lib().treeray_autotune(self.h, int(n_sample), C.byref(best), ms, _stream(stream)))
         return best.value, list(ms)
+
+    # -- C: treeray_set_orientations
+    def set_orientations(self, rot, orient=None):
+        """Several HEALPix orientations: rot [k, 3, 3] rotations (host), orient a CUDA
+        uint8 tensor of one orientation per leaf (None: leaf mod k). Empty rot: the
+        single unturned ray set."""
+        import numpy as np
+        import torch
+        r = np.ascontiguousarray(rot, dtype=np.float64).reshape(-1)
+        k = r.size // 9
+        self._rot = r
+        _raise(lib().treeray_set_orientations(self.h, k, C.c_void_p(r.ctypes.data) if k else None,
+                                              _dev(orient, torch.uint8, "orient", allow_none=True)))
 
     # -- C: treeray_set_warps_per_target
     def set_warps_per_target(self, wpt: int):

@@ -37,6 +37,47 @@ treeray_status upload(T** dst, const std::vector<T>& src, cudaStream_t s) {
 }
 }  // namespace
 
+// Ray directions n_h (pixel centres), per orientation R_o n_h, rounded to FP32 from FP64.
+treeray_status upload_directions(treeray_ctx* c, cudaStream_t s) {
+    const int np = c->p.npix;
+    const size_t k = std::max<size_t>(1, c->rot.size() / 9);
+    std::vector<float> nh(3 * (size_t)np * k);
+    for (int h = 0; h < np; ++h) {
+        double v[3];
+        healpix_pix2vec(c->ht.nside, h, v);
+        for (size_t o = 0; o < k; ++o)
+            for (int a = 0; a < 3; ++a) {
+                double w = v[a];
+                if (!c->rot.empty()) {
+                    const double* R = c->rot.data() + 9 * o + 3 * a;
+                    w = R[0] * v[0] + R[1] * v[1] + R[2] * v[2];
+                }
+                nh[3 * (o * np + h) + a] = (float)w;
+            }
+    }
+    c->ht.nhat = nh;
+    treeray_status rc = upload(&c->dt.nhat, nh, s);
+    if (rc != TREERAY_OK) return rc;
+    TR_CUDA(cudaStreamSynchronize(s));  // the host vector is replaced on the next call
+    return TREERAY_OK;
+}
+
+// The default orientation map of a grid, leaf l -> l mod k, unless the caller's map fits it.
+treeray_status ensure_orient_map(treeray_ctx* c, cudaStream_t s) {
+    if (c->rot.empty()) return TREERAY_OK;
+    if (c->orient && c->orient_n == c->nleaves) return TREERAY_OK;
+    const int k = (int)(c->rot.size() / 9);
+    std::vector<uint8_t> m((size_t)c->nleaves);
+    for (int64_t l = 0; l < c->nleaves; ++l) m[l] = (uint8_t)(l % k);
+    c->orient_user = false;
+    c->orient_n = 0;
+    treeray_status rc = upload(&c->orient, m, s);
+    if (rc != TREERAY_OK) return rc;
+    TR_CUDA(cudaStreamSynchronize(s));
+    c->orient_n = c->nleaves;
+    return TREERAY_OK;
+}
+
 // Per-grid tables: the alpha table (cached by grid shape) and, for every target level,
 // the integer thresholds of the walk's decisions:
 //   bin i      : d^2 >= ceil(R_i^2)                      (segment index, i >= 1)
@@ -48,13 +89,16 @@ treeray_status upload_tables(treeray_ctx* c, cudaStream_t s) {
     const int L = c->lmax, nb = c->p.nbins;
     if (c->tab_lmax == L && c->tab_amr == c->amr) {
         c->built = true;  // tables depend only on the grid shape: reuse
-        return TREERAY_OK;
+        return ensure_orient_map(c, s);
     }
     {
         c->ht.npix = c->p.npix;
         c->ht.nside = healpix_nside(c->p.npix);
         c->ht.s = c->p.alpha_s;
-        build_alpha_table(c->ht, c->p.theta, L, c->amr, c->p.col_mapping != 0);
+        if (!build_alpha_table(c->ht, c->p.theta, L, c->amr, c->p.col_mapping != 0, c->rot)) {
+            set_error("angular-kernel tables of all orientations exceed 2^31 entries");
+            return TREERAY_ENOMEM;
+        }
         treeray_status rc;
         if ((rc = upload(&c->dt.alpha_off, c->ht.alpha_off, s)) != TREERAY_OK) return rc;
         if ((rc = upload(&c->dt.alpha_ent, c->ht.alpha_ent, s)) != TREERAY_OK) return rc;
@@ -118,7 +162,7 @@ treeray_status upload_tables(treeray_ctx* c, cudaStream_t s) {
     c->tab_lmax = L;
     c->tab_amr = c->amr;
     c->built = true;
-    return TREERAY_OK;
+    return ensure_orient_map(c, s);
 }
 
 }  // namespace tr
@@ -192,19 +236,12 @@ treeray_status treeray_create(const treeray_params* p, treeray_t* out) {
     c->ht.npix = p->npix;
     c->ht.nside = healpix_nside(p->npix);
     c->ht.s = p->alpha_s;
-    std::vector<float> nh(3 * (size_t)p->npix);
-    for (int h = 0; h < p->npix; ++h) {
-        double v[3];
-        healpix_pix2vec(c->ht.nside, h, v);
-        for (int a = 0; a < 3; ++a) nh[3 * h + a] = (float)v[a];
-    }
-    c->ht.nhat = nh;
     auto fail = [&](treeray_status rc) {
         free_tables(c->dt);
         delete c;
         return rc;
     };
-    treeray_status rc = upload(&c->dt.nhat, nh, nullptr);
+    treeray_status rc = upload_directions(c, nullptr);
     if (rc != TREERAY_OK) return fail(rc);
     if (cudaMalloc(&c->dt.scal, sizeof(double) * 4) != cudaSuccess ||
         cudaMalloc(&c->dt.err, sizeof(unsigned)) != cudaSuccess ||
@@ -228,6 +265,7 @@ treeray_status treeray_destroy(treeray_t c) {
     if (c->fp_F) cudaFree(c->fp_F);
     if (c->fp_flags) cudaFree(c->fp_flags);
     if (c->stack_scr) cudaFree(c->stack_scr);
+    if (c->orient) cudaFree(c->orient);
     if (c->fp_stream) cudaStreamDestroy(c->fp_stream);
     for (cudaEvent_t e : c->fp_ev)
         if (e) cudaEventDestroy(e);
@@ -249,6 +287,58 @@ treeray_status treeray_build(treeray_t c, const treeray_grid* g, const float* rh
     rc = build_tree(c, g, rho, Td, kappa, n_stars, star_pos, star_lum, (cudaStream_t)stream);
     if (rc != TREERAY_OK) return rc;
     return reserve_eval_stacks(c, c->lmax, (cudaStream_t)stream);
+}
+
+treeray_status treeray_set_orientations(treeray_t c, int k, const double* rot, const uint8_t* orient) {
+    treeray_status rc = check_ctx(c, orient != nullptr);
+    if (rc != TREERAY_OK) return rc;
+    if (k < 0 || k > kMaxOrientations || (k > 0 && !rot) || (k == 0 && orient)) {
+        set_error("set_orientations: k in 0..64, rot required for k > 0, no map for k = 0");
+        return TREERAY_EINVAL;
+    }
+    for (int o = 0; o < k; ++o) {
+        const double* R = rot + 9 * o;
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                const double d = R[3 * a] * R[3 * b] + R[3 * a + 1] * R[3 * b + 1] + R[3 * a + 2] * R[3 * b + 2];
+                if (!(std::fabs(d - (a == b ? 1.0 : 0.0)) <= 1e-9)) {
+                    set_error("set_orientations: rotation " + std::to_string(o) + " is not orthonormal");
+                    return TREERAY_EINVAL;
+                }
+            }
+        const double det = R[0] * (R[4] * R[8] - R[5] * R[7]) - R[1] * (R[3] * R[8] - R[5] * R[6]) +
+                           R[2] * (R[3] * R[7] - R[4] * R[6]);
+        if (!(det > 0.0)) {
+            set_error("set_orientations: rotation " + std::to_string(o) + " is a reflection");
+            return TREERAY_EINVAL;
+        }
+    }
+    std::vector<uint8_t> m;
+    if (orient) {  // checked on the host: every value < k
+        m.resize((size_t)c->nleaves);
+        TR_CUDA(cudaMemcpy(m.data(), orient, m.size(), cudaMemcpyDeviceToHost));
+        for (uint8_t v : m)
+            if ((int)v >= k) {
+                set_error("set_orientations: map value " + std::to_string((int)v) + " >= k");
+                return TREERAY_EINVAL;
+            }
+    }
+    TR_CUDA(cudaDeviceSynchronize());  // no launch may still read the old tables
+    c->rot.assign(rot ? rot : nullptr, rot ? rot + 9 * (size_t)k : nullptr);
+    if (c->orient) cudaFree(c->orient);
+    c->orient = nullptr;
+    c->orient_n = 0;
+    c->orient_user = false;
+    if ((rc = upload_directions(c, nullptr)) != TREERAY_OK) return rc;
+    if (orient) {
+        if ((rc = upload(&c->orient, m, nullptr)) != TREERAY_OK) return rc;
+        TR_CUDA(cudaDeviceSynchronize());
+        c->orient_n = c->nleaves;
+        c->orient_user = true;
+    }
+    c->tab_lmax = -1;  // the angular-kernel tables follow the orientations
+    if (!c->built) return TREERAY_OK;
+    return upload_tables(c, nullptr);
 }
 
 treeray_status treeray_evaluate(treeray_t c, const int32_t* targets, int64_t n, float* J, double* F,
@@ -494,6 +584,16 @@ treeray_status treeray_alpha_counts_host(int npix, int s, const int64_t* K, int3
         return TREERAY_EINVAL;
     }
     alpha_counts(npix, s, K, counts);
+    return TREERAY_OK;
+}
+
+treeray_status treeray_alpha_counts_rotated_host(int npix, int s, const int64_t* K, const double* rot,
+                                                 int32_t* counts) {
+    if (healpix_nside(npix) < 0 || s < 4 || s % 4 != 0 || !K || !rot || !counts) {
+        set_error("alpha_counts_rotated_host: bad arguments");
+        return TREERAY_EINVAL;
+    }
+    alpha_counts(npix, s, K, counts, rot);
     return TREERAY_OK;
 }
 

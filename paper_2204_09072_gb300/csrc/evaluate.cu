@@ -35,9 +35,11 @@ struct __align__(16) EvalArgs {
     const int32_t* __restrict__ inv_perm;
     const int32_t* __restrict__ targets;
     const double* __restrict__ jsrc;
-    const float* __restrict__ nhat;
-    const int32_t* __restrict__ aoff;
+    const float* __restrict__ nhat;     // [orientations][npix][3]
+    const int32_t* __restrict__ aoff;   // [orientations][aoff_stride]
     const uint32_t* __restrict__ aent;
+    const uint8_t* __restrict__ orient;  // per leaf (caller order): its ray orientation, or null
+    int64_t aoff_stride;
     const int64_t* __restrict__ bin_thr;
     const float* __restrict__ R2;
     const int64_t* __restrict__ open_max;
@@ -170,7 +172,7 @@ __global__ void __launch_bounds__(256) k_walk_list(EvalArgs a) {
         if (lane == 0) q = (long long)atomicAdd(a.queue, 1ull);
         q = __shfl_sync(full, q, 0);
         if (q >= a.n) break;
-        int64_t s;
+        int64_t s, cell;
         if (a.targets) {
             const int32_t k = a.targets[q];
             if (k < 0 || k >= a.nleaves) {
@@ -178,9 +180,13 @@ __global__ void __launch_bounds__(256) k_walk_list(EvalArgs a) {
                 continue;
             }
             s = a.inv_perm[k];
+            cell = k;
         } else {
             s = q;
+            cell = a.perm[s];
         }
+        // angular-kernel table of the target's ray orientation
+        const int32_t* aoff = a.aoff + (a.orient ? (int64_t)a.orient[cell] * a.aoff_stride : 0);
         const int4 tg = a.geo[a.leaf_node[s]];
         const int tx = tg.x, ty = tg.y, tz = tg.z & 0xffffff;
         int nacc = 0;
@@ -262,7 +268,7 @@ __global__ void __launch_bounds__(256) k_walk_list(EvalArgs a) {
                     const int Kz = colmap ? odd_key(small_int_to_float(qz) + cz, elog) : alpha_key(qz, elog);
                     if (abs(Kx) <= a.D && abs(Ky) <= a.D && abs(Kz) <= a.D) {
                         const int idx = ((Kz + a.D) * W + (Ky + a.D)) * W + (Kx + a.D);
-                        nent += __ldg(a.aoff + idx + 1) - __ldg(a.aoff + idx);
+                        nent += __ldg(aoff + idx + 1) - __ldg(aoff + idx);
                     }
                 }
             }
@@ -298,7 +304,8 @@ constexpr int min_warps_per_sm(int npix, bool thick) { return thick ? 32 : (npix
 // d^2, the segment and the straddled boundaries; alpha and beta differ. Such nodes lie on
 // the planes half a box from the target, so this path is rare.
 template <int NPIX, bool THICK>
-__device__ __noinline__ void deposit_tied_copies(const EvalArgs& A, float* tL, float* tA, float* tLk, float* tAk,
+__device__ __noinline__ void deposit_tied_copies(const EvalArgs& A, const int32_t* aoff, float* tL, float* tA,
+                                                 float* tLk, float* tAk,
                                                  float* tVk, float* tQk, unsigned long long* flags, int node,
                                                  int ox, int oy, int oz, int ties, int lvl, int64_t d2, int tl,
                                                  float2 lp) {
@@ -358,7 +365,7 @@ __device__ __noinline__ void deposit_tied_copies(const EvalArgs& A, float* tL, f
             continue;
         }
         const int idx = ((Kz + A.D) * W + (Ky + A.D)) * W + (Kx + A.D);
-        const int e0 = __ldg(A.aoff + idx), e1 = __ldg(A.aoff + idx + 1);
+        const int e0 = __ldg(aoff + idx), e1 = __ldg(aoff + idx + 1);
         if (e1 == e0) atomicOr(A.err, kErrAlphaKey);
         const float bL = beta * v0.x * inv_s3 * wt, bA = beta * v0.y * inv_s3 * wt;
         for (int e = e0; e < e1; ++e) {
@@ -394,9 +401,13 @@ __device__ __noinline__ void deposit_tied_copies(const EvalArgs& A, float* tL, f
 //   rays:    threads integrate the rays' segments inside out (thin tiles with spare
 //            threads cut each ray into consecutive parts joined by their transmission),
 //            then the team reduces J and F.
-template <int NPIX, bool THICK, int WPT, bool GENERAL>
+// BATCH: the targets of several boxes share the work counter, each box with its own
+// descriptor (boxes, box_start); otherwise the one box's descriptor is the kernel
+// parameter itself, read from the constant bank.
+template <int NPIX, bool THICK, int WPT, bool GENERAL, bool BATCH>
 __global__ void __launch_bounds__(WPT * 32, min_warps_per_sm(NPIX, THICK) / WPT)
-    k_evaluate(EvalArgs a, const EvalArgs* __restrict__ boxes, const int64_t* __restrict__ box_start, int nbox) {
+    k_evaluate(const __grid_constant__ EvalArgs a, const EvalArgs* __restrict__ boxes,
+               const int64_t* __restrict__ box_start, int nbox) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int NT = WPT * 32;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -424,29 +435,27 @@ __global__ void __launch_bounds__(WPT * 32, min_warps_per_sm(NPIX, THICK) / WPT)
     int* stack = a.stack + (size_t)blockIdx.x * stack_cap;
     __shared__ int s_sp, s_overflow;
     __shared__ long long s_q;
+    __shared__ const int32_t* s_aoff;  // the target's orientation: angular-kernel table
+    __shared__ const float* s_nhat;    // and ray directions
     __shared__ float s_red[7][WPT];  // J, then (hi, lo) pairs of F_x, F_y, F_z
     __shared__ float s_tau[2][WPT];
     const unsigned full = 0xffffffffu;
     const unsigned lt_mask = (1u << lane) - 1u;
     const float omega = (float)(4.0 * kPi / NPIX);
     if (a.skip && *a.skip) return;
-    // the per-box descriptor lives in shared memory: copied once (one box) or per target (a
-    // batch of boxes whose targets share one work counter)
+    // the box descriptor: the kernel parameter (one box: uniform constant-bank operands, no
+    // shared-memory loads), or a shared-memory copy of the current target's box (a batch)
     __shared__ __align__(16) EvalArgs s_box;
     __shared__ int s_b, s_bcur;
-    const EvalArgs& A = s_box;
-    if (tid == 0) s_bcur = -1;
-    if (!boxes) {
-        for (int w = tid; w < (int)(sizeof(EvalArgs) / 8); w += NT)
-            reinterpret_cast<unsigned long long*>(&s_box)[w] = reinterpret_cast<const unsigned long long*>(&a)[w];
-    }
+    const EvalArgs& A = BATCH ? s_box : a;
+    if (BATCH && tid == 0) s_bcur = -1;
 
     for (;;) {
         if (tid == 0) s_q = (long long)atomicAdd(a.queue, 1ull);
         __syncthreads();
         long long q = s_q;
         if (q >= a.n) break;
-        if (boxes) {
+        if constexpr (BATCH) {
             if (tid == 0) {
                 int lo = 0, hi = nbox - 1;  // last box with box_start[b] <= q
                 while (lo < hi) {
@@ -472,7 +481,7 @@ __global__ void __launch_bounds__(WPT * 32, min_warps_per_sm(NPIX, THICK) / WPT)
         const int W = 2 * A.D + 1;
         const int4 root = A.geo[0];
         int64_t s;
-        int64_t out;
+        int64_t out, cell;
         if (A.targets) {
             const int32_t k = A.targets[q];
             if (k < 0 || k >= A.nleaves) {
@@ -482,9 +491,11 @@ __global__ void __launch_bounds__(WPT * 32, min_warps_per_sm(NPIX, THICK) / WPT)
             }
             s = A.inv_perm[k];
             out = q;
+            cell = k;
         } else {
             s = q;
             out = A.perm[s];
+            cell = out;
         }
         const int tnode = A.leaf_node[s];
         const int4 tg = A.geo[tnode];
@@ -504,6 +515,9 @@ __global__ void __launch_bounds__(WPT * 32, min_warps_per_sm(NPIX, THICK) / WPT)
                 stack[0] = root.w;
                 s_sp = 1;
             }
+            const int o = A.orient ? (int)A.orient[cell] : 0;
+            s_aoff = A.aoff + (int64_t)o * A.aoff_stride;
+            s_nhat = A.nhat + 3 * NPIX * o;
         }
         __syncthreads();
         for (;;) {
@@ -559,8 +573,8 @@ __global__ void __launch_bounds__(WPT * 32, min_warps_per_sm(NPIX, THICK) / WPT)
             int ne = 0, ebase = 0, cbase = 0;
             float bL = 0.0f, bA = 0.0f;
             if (GENERAL && acc && ties) {
-                deposit_tied_copies<NPIX, THICK>(A, tL, tA, tLk, tAk, tVk, tQk, flags, node, ox, oy, oz, ties, lvl,
-                                                 d2, tl, lp);
+                deposit_tied_copies<NPIX, THICK>(A, s_aoff, tL, tA, tLk, tAk, tVk, tQk, flags, node, ox, oy, oz,
+                                                 ties, lvl, d2, tl, lp);
             } else if (acc) {
                 // the float distance only guesses the segment; the integer d^2 decides it
                 const float fx = small_int_to_float(ox), fy = small_int_to_float(oy), fz = small_int_to_float(oz);
@@ -582,7 +596,8 @@ __global__ void __launch_bounds__(WPT * 32, min_warps_per_sm(NPIX, THICK) / WPT)
                     atomicOr(A.err, kErrAlphaKey);
                 } else {
                     const int idx = ((Kz + A.D) * W + (Ky + A.D)) * W + (Kx + A.D);
-                    const int e0 = __ldg(A.aoff + idx), e1 = __ldg(A.aoff + idx + 1);
+                    const int32_t* aoff = s_aoff;
+                    const int e0 = __ldg(aoff + idx), e1 = __ldg(aoff + idx + 1);
                     if (e1 == e0) atomicOr(A.err, kErrAlphaKey);
                     ne = e1 - e0;
                     ebase = e0;
@@ -773,9 +788,10 @@ __global__ void __launch_bounds__(WPT * 32, min_warps_per_sm(NPIX, THICK) / WPT)
                 tminv = fminf(tminv, tr);
             }
             Js += Fh;
-            add_product(Fxh, Fxl, -Fh, __ldg(A.nhat + 3 * h));
-            add_product(Fyh, Fyl, -Fh, __ldg(A.nhat + 3 * h + 1));
-            add_product(Fzh, Fzl, -Fh, __ldg(A.nhat + 3 * h + 2));
+            const float* nh = s_nhat;
+            add_product(Fxh, Fxl, -Fh, __ldg(nh + 3 * h));
+            add_product(Fyh, Fyl, -Fh, __ldg(nh + 3 * h + 1));
+            add_product(Fzh, Fzl, -Fh, __ldg(nh + 3 * h + 2));
         };
         // thin tiles with spare threads: the segments of a ray are cut into P consecutive
         // parts, one thread each; a part's result is carried outward by the transmission
@@ -924,7 +940,7 @@ size_t stack_bytes_for(int wpt, int lmax, int blocks) {
     return (size_t)blocks * (size_t)(32 * wpt * (lmax + 1) + 64) * sizeof(int);
 }
 
-template <int NPIX, bool THICK, int WPT, bool GENERAL>
+template <int NPIX, bool THICK, int WPT, bool GENERAL, bool BATCH>
 treeray_status launch_team(treeray_ctx* c, const EvalArgs& a, const EvalArgs* boxes,
                            const int64_t* box_start, int nbox, int layout_lmax, cudaStream_t s) {
     constexpr int nq = THICK ? 6 : 2;
@@ -939,7 +955,7 @@ treeray_status launch_team(treeray_ctx* c, const EvalArgs& a, const EvalArgs* bo
         set_error("evaluate: the per-target ray tile (npix x nbins) exceeds shared memory");
         return TREERAY_EINVAL;
     }
-    auto kern = k_evaluate<NPIX, THICK, WPT, GENERAL>;
+    auto kern = k_evaluate<NPIX, THICK, WPT, GENERAL, BATCH>;
     TR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     TR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WPT * 32, smem));
@@ -964,10 +980,12 @@ treeray_status launch_team(treeray_ctx* c, const EvalArgs& a, const EvalArgs* bo
 template <int NPIX, bool THICK, bool GENERAL>
 treeray_status launch_wpt(treeray_ctx* c, int wpt, const EvalArgs& a, const EvalArgs* boxes,
                           const int64_t* box_start, int nbox, int layout_lmax, cudaStream_t s) {
+    // batches run teams of 4 warps
+    if (boxes) return launch_team<NPIX, THICK, 4, GENERAL, true>(c, a, boxes, box_start, nbox, layout_lmax, s);
     switch (wpt) {
-        case 2: return launch_team<NPIX, THICK, 2, GENERAL>(c, a, boxes, box_start, nbox, layout_lmax, s);
-        case 8: return launch_team<NPIX, THICK, 8, GENERAL>(c, a, boxes, box_start, nbox, layout_lmax, s);
-        default: return launch_team<NPIX, THICK, 4, GENERAL>(c, a, boxes, box_start, nbox, layout_lmax, s);
+        case 2: return launch_team<NPIX, THICK, 2, GENERAL, false>(c, a, nullptr, nullptr, 0, layout_lmax, s);
+        case 8: return launch_team<NPIX, THICK, 8, GENERAL, false>(c, a, nullptr, nullptr, 0, layout_lmax, s);
+        default: return launch_team<NPIX, THICK, 4, GENERAL, false>(c, a, nullptr, nullptr, 0, layout_lmax, s);
     }
 }
 
@@ -1019,6 +1037,8 @@ EvalArgs make_args(treeray_ctx* c, const int32_t* targets, int64_t n) {
     a.nhat = c->dt.nhat;
     a.aoff = c->dt.alpha_off;
     a.aent = c->dt.alpha_ent;
+    a.orient = c->rot.empty() ? nullptr : c->orient;
+    a.aoff_stride = (int64_t)(2 * c->ht.D + 1) * (2 * c->ht.D + 1) * (2 * c->ht.D + 1) + 1;
     a.bin_thr = c->dt.bin_thr;
     a.R2 = c->dt.R2;
     a.open_max = c->dt.open_max;

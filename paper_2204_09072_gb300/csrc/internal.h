@@ -22,6 +22,7 @@ constexpr double kDustFloorK = 2.7;
 constexpr int kMaxLevel = 19;     // octree levels below the root
 constexpr int kMaxBins = 64;
 constexpr int kMaxStars = 4096;
+constexpr int kMaxOrientations = 64;
 
 // device error word bits
 enum : unsigned {
@@ -36,18 +37,20 @@ void set_error(const std::string& msg);
 // Host-built tables (FP64 on the host, fixed per context and grid shape).
 struct HostTables {
     int npix = 0, nside = 0, s = 8;
-    std::vector<float> nhat;          // [npix][3] ray directions (pixel centres)
+    std::vector<float> nhat;          // [orientations][npix][3] ray directions (pixel centres)
     int D = 0;                        // alpha keys cover |K_a| <= D
-    std::vector<int32_t> alpha_off;   // [(2D+1)^3 + 1]
+    std::vector<int32_t> alpha_off;   // [orientations][(2D+1)^3 + 1]
     std::vector<uint32_t> alpha_ent;  // pixel | count << 16
 };
 
 int healpix_nside(int npix);
 int healpix_ang2pix(int nside, double x, double y, double z);
 void healpix_pix2vec(int nside, int pix, double* v);
-void alpha_counts(int npix, int s, const int64_t* K, int32_t* counts);
-// Build the alpha table for the keys the walk can reach on this grid shape.
-void build_alpha_table(HostTables& t, double theta, int lmax, bool amr, bool col);
+void alpha_counts(int npix, int s, const int64_t* K, int32_t* counts, const double* rot = nullptr);
+// Build the alpha table for the keys the walk can reach on this grid shape, one per
+// orientation in rot (k row-major rotations; none: the unturned grid). False when the
+// entries outgrow 32-bit offsets.
+bool build_alpha_table(HostTables& t, double theta, int lmax, bool amr, bool col, const std::vector<double>& rot);
 // Evaluation radii R_i (half-cells of the finest level) for a target of edge Et.
 void radii(int nbins, int lmax, int periodic, int spacing, int64_t Et, double* R);
 
@@ -126,6 +129,11 @@ struct treeray_ctx {
     cudaEvent_t fp_ev[2] = {nullptr, nullptr};
     int* stack_scr = nullptr;    // evaluate: team stacks (global scratch, grow-only)
     size_t stack_scr_bytes = 0;
+    // several HEALPix orientations (Sec. 6)
+    std::vector<double> rot;     // [k][9] row-major rotations; empty: the single unturned ray set
+    uint8_t* orient = nullptr;   // device [orient_n]: orientation of each leaf (caller order)
+    int64_t orient_n = 0;        // leaves the map was made for
+    bool orient_user = false;    // the map came from the caller (else leaf mod k)
     int64_t launches = 0;  // kernels launched by this context
     int wpt = 4;           // warps per target team of the evaluate kernel (autotuned)
     // table cache key

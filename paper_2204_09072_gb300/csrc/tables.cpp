@@ -118,7 +118,9 @@ void healpix_pix2vec(int nside, int pix, double* v) {
 // alpha for a node at quantised offset K (units of 1/8 of its edge) from the target:
 // the s^3 sub-cube centres of the node, seen from the target along
 // (2 s K / 8 + 2 a + 1 - s) for a = 0..s-1 per axis, counted per pixel.
-void alpha_counts(int npix, int s, const int64_t* K, int32_t* counts) {
+// rot (row-major R, may be null): a turned ray set (Sec. 6), whose ray h points along
+// R n_h; a direction v then counts for ray h when R^T v lies in pixel h.
+void alpha_counts(int npix, int s, const int64_t* K, int32_t* counts, const double* rot) {
     const int ns = healpix_nside(npix);
     std::fill(counts, counts + npix, 0);
     const int64_t bx = 2 * s * K[0] / 8 + 1 - s;
@@ -126,9 +128,18 @@ void alpha_counts(int npix, int s, const int64_t* K, int32_t* counts) {
     const int64_t bz = 2 * s * K[2] / 8 + 1 - s;
     for (int c = 0; c < s; ++c)
         for (int b = 0; b < s; ++b)
-            for (int a = 0; a < s; ++a)
-                counts[healpix_ang2pix(ns, (double)(bx + 2 * a), (double)(by + 2 * b),
-                                       (double)(bz + 2 * c))]++;
+            for (int a = 0; a < s; ++a) {
+                const double vx = (double)(bx + 2 * a), vy = (double)(by + 2 * b), vz = (double)(bz + 2 * c);
+                if (!rot) {
+                    counts[healpix_ang2pix(ns, vx, vy, vz)]++;
+                    continue;
+                }
+                // R^T v, each component summed in the order of the vector's axes
+                const double wx = rot[0] * vx + rot[3] * vy + rot[6] * vz;
+                const double wy = rot[1] * vx + rot[4] * vy + rot[7] * vz;
+                const double wz = rot[2] * vx + rot[5] * vy + rot[8] * vz;
+                counts[healpix_ang2pix(ns, wx, wy, wz)]++;
+            }
 }
 
 namespace {
@@ -147,16 +158,19 @@ inline int key_class(int64_t k) {
 // only when accepted by the opening criterion, i.e. at 8 d / E > 8 / theta, unless the
 // grid is AMR (coarser and finer leaves next to the target, classes 1-3 anywhere).
 namespace {
-// tables already built in this process, keyed by (npix, samples, theta, D, amr, col)
+// tables already built in this process, keyed by (npix, samples, theta, D, amr, col,
+// rotations)
 std::mutex g_tab_mutex;
-std::map<std::tuple<int, int, double, int64_t, bool, bool>,
+std::map<std::tuple<int, int, double, int64_t, bool, bool, std::vector<double>>,
          std::pair<std::vector<int32_t>, std::vector<uint32_t>>>
     g_tab_cache;
 }  // namespace
 
 // col: nodes may be mapped at their centre of luminosity, which moves a key by up to 4
-// per axis and gives odd keys at any distance
-void build_alpha_table(HostTables& t, double theta, int lmax, bool amr, bool col) {
+// per axis and gives odd keys at any distance.
+// rot: k row-major rotations (k = 0: the unturned grid alone). Orientation o's offsets
+// are alpha_off[o (W^3 + 1) + key], all pointing into one shared entry array.
+bool build_alpha_table(HostTables& t, double theta, int lmax, bool amr, bool col, const std::vector<double>& rot) {
     const double th = theta > 1e-6 ? theta : 1e-6;
     const double reach = std::max(2.0 / th, std::sqrt(3.0)) + 0.5 * std::sqrt(3.0);
     const int64_t extra = col ? 4 : 0;
@@ -165,17 +179,18 @@ void build_alpha_table(HostTables& t, double theta, int lmax, bool amr, bool col
     D = std::min(D, cap);
     D = std::min<int64_t>(D, 128 + extra);
     t.D = (int)D;
-    const auto key = std::make_tuple(t.npix, t.s, theta, D, amr, col);
+    const auto key = std::make_tuple(t.npix, t.s, theta, D, amr, col, rot);
     {
         std::lock_guard<std::mutex> lock(g_tab_mutex);
         auto it = g_tab_cache.find(key);
         if (it != g_tab_cache.end()) {
             t.alpha_off = it->second.first;
             t.alpha_ent = it->second.second;
-            return;
+            return true;
         }
     }
     const int64_t W = 2 * D + 1, nk = W * W * W;
+    const int64_t norient = std::max<int64_t>(1, (int64_t)(rot.size() / 9));
     const double shell = std::max(0.0, 8.0 / th - std::sqrt(3.0));
     const double shell2 = shell * shell;
     // which keys get an entry
@@ -192,31 +207,48 @@ void build_alpha_table(HostTables& t, double theta, int lmax, bool amr, bool col
                 }
                 keys.push_back(((z + D) * W + (y + D)) * W + (x + D));
             }
-    std::vector<std::vector<uint32_t>> lists(keys.size());
+    const size_t nkeys = keys.size();
+    std::vector<std::vector<uint32_t>> lists(nkeys * norient);
     const int nth = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
     std::vector<std::thread> pool;
     for (int w = 0; w < nth; ++w)
         pool.emplace_back([&, w]() {
             std::vector<int32_t> cnt(t.npix);
-            for (size_t q = w; q < keys.size(); q += nth) {
+            for (size_t j = w; j < nkeys * norient; j += nth) {
+                const size_t q = j % nkeys, o = j / nkeys;
                 const int64_t idx = keys[q];
                 const int64_t K[3] = {idx % W - D, (idx / W) % W - D, idx / (W * W) - D};
-                alpha_counts(t.npix, t.s, K, cnt.data());
+                alpha_counts(t.npix, t.s, K, cnt.data(), rot.empty() ? nullptr : rot.data() + 9 * o);
                 for (int h = 0; h < t.npix; ++h)
-                    if (cnt[h] > 0) lists[q].push_back((uint32_t)h | ((uint32_t)cnt[h] << 16));
+                    if (cnt[h] > 0) lists[j].push_back((uint32_t)h | ((uint32_t)cnt[h] << 16));
             }
         });
     for (auto& th_ : pool) th_.join();
-    t.alpha_off.assign(nk + 1, 0);
-    std::vector<int32_t> len(nk, 0);
-    for (size_t q = 0; q < keys.size(); ++q) len[keys[q]] = (int32_t)lists[q].size();
-    for (int64_t i = 0; i < nk; ++i) t.alpha_off[i + 1] = t.alpha_off[i] + len[i];
-    t.alpha_ent.assign(t.alpha_off[nk], 0);
-    for (size_t q = 0; q < keys.size(); ++q)
-        std::copy(lists[q].begin(), lists[q].end(), t.alpha_ent.begin() + t.alpha_off[keys[q]]);
+    // offsets per orientation, one running count over all of them (int32: checked)
+    std::vector<int32_t> off((size_t)norient * (nk + 1), 0);
+    int64_t run = 0;
+    std::vector<int32_t> len(nk);
+    for (int64_t o = 0; o < norient; ++o) {
+        std::fill(len.begin(), len.end(), 0);
+        for (size_t q = 0; q < nkeys; ++q) len[keys[q]] = (int32_t)lists[o * nkeys + q].size();
+        int32_t* oo = off.data() + o * (nk + 1);
+        for (int64_t i = 0; i <= nk; ++i) {
+            if (run > INT32_MAX) return false;
+            oo[i] = (int32_t)run;
+            if (i < nk) run += len[i];
+        }
+    }
+    std::vector<uint32_t> ent((size_t)run, 0);
+    for (int64_t o = 0; o < norient; ++o)
+        for (size_t q = 0; q < nkeys; ++q)
+            std::copy(lists[o * nkeys + q].begin(), lists[o * nkeys + q].end(),
+                      ent.begin() + off[o * (nk + 1) + keys[q]]);
+    t.alpha_off.swap(off);
+    t.alpha_ent.swap(ent);
     std::lock_guard<std::mutex> lock(g_tab_mutex);
     if (g_tab_cache.size() > 16) g_tab_cache.clear();
     g_tab_cache[key] = std::make_pair(t.alpha_off, t.alpha_ent);
+    return true;
 }
 
 // R_i = R_0 (R_max / R_0)^(i / nbins), R_0 = Et / 2, R_max = sqrt(3) box (half-cells); with

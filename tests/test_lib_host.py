@@ -55,3 +55,24 @@ def test_alpha_table_matches_oracle(trlib, orc):
 def test_bad_args_host(trlib):
     with pytest.raises(trlib.TreeRayError):
         trlib.alpha_counts_host(50, 8, [1, 1, 1])
+
+
+def test_turned_alpha_table_matches_oracle(trlib, orc):
+    """Several HEALPix orientations (Sec. 6): the library's counts for a turned ray set
+    equal the oracle's, key for key, for random rotations and a quarter turn."""
+    import synth
+    rng = np.random.default_rng(1)
+    rots = list(synth.random_rotations(4, seed=31)) + [np.array([[0.0, -1, 0], [1, 0, 0], [0, 0, 1]])]
+    keys = []
+    for step, off in [(8, 0), (4, 2), (2, 1), (8, 4)]:
+        for _ in range(60):
+            keys.append(rng.integers(-6, 7, 3) * step + off)
+    for npix in (12, 48, 192):
+        for R in rots:
+            for K in keys:
+                if not np.any(K):
+                    continue
+                a = trlib.alpha_counts_host(npix, 8, K, rot=R)
+                b = orc.alpha_counts(npix, K, 8, rot=R)
+                assert (a == b).all(), (npix, K)
+                assert a.sum() == 512
