@@ -457,24 +457,42 @@ def run_sweep(args):
 
 
 def run_orientations(args):
-    """Several HEALPix orientations (Sec. 6) on the 128^3 cloud: evaluate time for k turned
-    ray sets (one seeded random orientation per cell) against the single unturned set,
-    and the residual of J at 48 rays against 192 rays (ray-matched opening angles, as the
-    paper's ray-count study): mean and spread over all cells, and the part of the spread
-    that survives averaging over 4^3-cell blocks (the coherent ray pattern) versus the
-    part that does not (cell-to-cell noise). One JSON line per k."""
+    """Several HEALPix orientations (Sec. 6) on the 128^3 cloud and on the collapsing-core
+    AMR grid (the paper's ray pattern shows around its embedded sources): evaluate time for
+    k turned ray sets (one seeded random orientation per cell) against the single unturned
+    set, and the residual of J at 48 rays against 192 rays (ray-matched opening angles, as
+    the paper's ray-count study): mean and spread over all cells, and the part of the
+    spread that survives averaging over blocks of 4^3 cells (uniform grid) or over the 8^3
+    blocks (AMR), the coherent ray pattern, versus the part left inside the blocks
+    (cell-to-cell noise). One JSON line per workload and k."""
     import torch
 
     import paper_2204_09072_gb300 as tr
     import synth
     dev = torch.device("cuda:0")
+    for wl in ("turb128", "amr_core"):
+        _orientations_on(tr, synth, torch, dev, wl)
 
+
+def _orientations_on(tr, synth, torch, dev, wl):
     def ctx_for(npix):
-        w = synth.turbulent_cloud(128, npix=npix, theta=-1.0)
+        if wl == "turb128":
+            w = synth.turbulent_cloud(128, npix=npix, theta=-1.0)
+        else:
+            w = synth.amr_core(npix=npix, theta=-1.0)
         c = tr.Context(w.params)
-        c.build(w.box_cm, torch.as_tensor(w.rho, device=dev), torch.as_tensor(w.td, device=dev), n=128,
-                star_pos=w.star_pos, star_lum=w.star_lum)
+        c.build(w.box_cm, torch.as_tensor(w.rho, device=dev), torch.as_tensor(w.td, device=dev),
+                n=w.uniform_n, blocks=w.blocks, star_pos=w.star_pos, star_lum=w.star_lum)
         return w, c
+
+    def blocks_of(r):
+        if wl == "turb128":  # x-fastest cells -> 4^3 blocks
+            b = r.reshape(32, 4, 32, 4, 32, 4)
+            m = b.mean(axis=(1, 3, 5))
+            return m, b - m[:, None, :, None, :, None]
+        b = r.reshape(-1, 512)  # block-major leaves -> the 8^3 blocks
+        m = b.mean(axis=1)
+        return m, b - m[:, None]
 
     def timed_eval(c, n):
         J = torch.empty(n, dtype=torch.float32, device=dev)
@@ -509,12 +527,13 @@ def run_orientations(args):
         t_tab = time.time() - t0
         J, ms = timed_eval(c, n)
         r = J / J192 - 1.0
-        blk = r.reshape(32, 4, 32, 4, 32, 4).mean(axis=(1, 3, 5))  # x-fastest cells -> 4^3 blocks
-        inner = r.reshape(32, 4, 32, 4, 32, 4) - blk[:, None, :, None, :, None]
-        print(json.dumps({"orientations": k, "workload": "turb128_npix48_raytheta", "ms_evaluate": ms,
+        blk, inner = blocks_of(r)
+        print(json.dumps({"orientations": k, "workload": f"{wl}_npix48_raytheta", "ms_evaluate": ms,
                           "ray_evals_per_s": n * 48 / (ms * 1e-3), "table_build_s": t_tab,
                           "ms_evaluate_192": ms192, "resid_mean": float(r.mean()), "resid_std": float(r.std()),
-                          "resid_block4_std": float(blk.std()), "resid_in_block_std": float(inner.std())}))
+                          "resid_block_std": float(blk.std()), "resid_in_block_std": float(inner.std()),
+                          "resid_abs_p50_p99": [float(np.percentile(np.abs(r), 50)),
+                                                float(np.percentile(np.abs(r), 99))]}))
     c.close()
 
 
@@ -730,12 +749,12 @@ def run_profile(args):
 
     import paper_2204_09072_gb300 as tr
     import synth
-    w = workload(args.npix)
+    w = workload(args.npix) if args.profile_workload == "turb128" else synth.amr_core(npix=args.npix)
     ctx = tr.Context(w.params)
     dev = torch.device("cuda:0")
     rho = torch.as_tensor(w.rho, device=dev)
     td = torch.as_tensor(w.td, device=dev)
-    ctx.build(w.box_cm, rho, td, n=w.uniform_n, star_pos=w.star_pos, star_lum=w.star_lum)
+    ctx.build(w.box_cm, rho, td, n=w.uniform_n, blocks=w.blocks, star_pos=w.star_pos, star_lum=w.star_lum)
     m = min(args.profile_targets, w.n_leaves)
     tg = torch.as_tensor(np.sort(synth.sample_targets(w.n_leaves, m, seed=5)).astype(np.int32),
                          device=dev)
@@ -744,7 +763,7 @@ def run_profile(args):
     for _ in range(3):
         ctx.evaluate(J, F, targets=tg)
     ctx.check()
-    print(json.dumps({"profile": "evaluate", "workload": f"turb128_npix{args.npix}", "targets": m,
+    print(json.dumps({"profile": "evaluate", "workload": f"{args.profile_workload}_npix{args.npix}", "targets": m,
                       "J_mean": float(J.double().mean())}))
     ctx.close()
 
@@ -799,6 +818,7 @@ def main():
     ap.add_argument("--profile-evaluate", action="store_true",
                     help="ncu driver: evaluate kernel only, on --profile-targets cells")
     ap.add_argument("--profile-targets", type=int, default=262144)
+    ap.add_argument("--profile-workload", default="turb128", choices=["turb128", "amr_core"])
     ap.add_argument("--batch64", action="store_true", help="64-box AMR batch: batched vs per-box launches")
     ap.add_argument("--sweep", action="store_true", help="N_pix x segments sweep with the autotuner")
     ap.add_argument("--warmstart", action="store_true", help="learned warm start of the T_d fixed point")

@@ -293,6 +293,14 @@ __global__ void __launch_bounds__(256) k_walk_list(EvalArgs a) {
 
 constexpr int kOwnerCap = 256;  // entries per warp and walk step spread one per lane
 
+// Row stride of the (segment x ray) tile in shared memory: a few words more than the rays,
+// so that the same ray in nearby segments (a common pair among the entries of one deposit
+// pass) falls into different banks (48 rays: 48 x 2 = 0 mod 32 banks). Thin tiles: 4 more
+// (measured best); thick tiles: 1 more, which keeps 8 six-quantity tiles of 20 segments
+// per SM.
+__host__ __device__ constexpr int tile_row(int npix, bool thick) { return npix + (thick ? 1 : 4); }
+__host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
 // Warps resident per SM that the register budget is cut for: thin tiles at N_pix <= 48 are
 // small enough for 64 warps per SM; larger thin tiles are limited by shared memory anyway;
 // thick kernels (six-quantity tiles) fit 32 warps without spilling.
@@ -371,7 +379,7 @@ __device__ __noinline__ void deposit_tied_copies(const EvalArgs& A, const int32_
         for (int e = e0; e < e1; ++e) {
             const uint32_t ent = __ldg(A.aent + e);
             const int h = (int)(ent & 0xffffu);
-            const int c = i * NPIX + h;
+            const int c = i * tile_row(NPIX, THICK) + h;
             const float w = count_to_float(ent >> 16);
             atomicAdd(tL + c, w * bL);
             atomicAdd(tA + c, w * bA);
@@ -412,10 +420,11 @@ __global__ void __launch_bounds__(WPT * 32, min_warps_per_sm(NPIX, THICK) / WPT)
     constexpr int NT = WPT * 32;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nb = a.nbins;
-    const int cells = nb * NPIX;
+    constexpr int ROW = tile_row(NPIX, THICK);
+    const int cells = nb * ROW;
     constexpr int nq = THICK ? 6 : 2;
-    // layout: tile [nq][nb][NPIX] f32 | THICK: flags [NPIX] u64 |
-    //         THICK: per warp node buffer int4[32] | per warp entry owners u8[kOwnerCap]
+    // layout: tile [nq][nb][ROW] f32 | THICK: flags [NPIX] u64 | THICK: per warp node
+    //         buffer int4[32] | per warp entry owners u8[kOwnerCap] (16-byte aligned parts)
     // The team's stack of child groups is this block's slice of a global scratch array:
     // it stays in L1, and leaving it out of shared memory lets more teams share an SM.
     float* tL = reinterpret_cast<float*>(smem);
@@ -424,11 +433,11 @@ __global__ void __launch_bounds__(WPT * 32, min_warps_per_sm(NPIX, THICK) / WPT)
     float* tAk = tLk + cells;
     float* tVk = tAk + cells;
     float* tQk = tVk + cells;
-    unsigned long long* flags = reinterpret_cast<unsigned long long*>(smem + (size_t)nq * cells * 4);
+    unsigned long long* flags = reinterpret_cast<unsigned long long*>(smem + align16((size_t)nq * cells * 4));
     // each entry's node data: thin kernels take it from the owner lane by shuffles (fewer
     // shared-memory operations and registers, measured faster); thick kernels, whose
     // occupancy is bound by their larger tile anyway, through a per-warp node buffer
-    int4* nodebufs = reinterpret_cast<int4*>(smem + (size_t)nq * cells * 4 + (THICK ? NPIX * 8 : 0));
+    int4* nodebufs = reinterpret_cast<int4*>(smem + align16(align16((size_t)nq * cells * 4) + (THICK ? NPIX * 8 : 0)));
     int4* nodebuf = nodebufs + warp * 32;
     unsigned char* owner = reinterpret_cast<unsigned char*>(nodebufs + (THICK ? WPT * 32 : 0)) + warp * kOwnerCap;
     const int stack_cap = a.stack_cap;
@@ -599,9 +608,11 @@ __global__ void __launch_bounds__(WPT * 32, min_warps_per_sm(NPIX, THICK) / WPT)
                     const int32_t* aoff = s_aoff;
                     const int e0 = __ldg(aoff + idx), e1 = __ldg(aoff + idx + 1);
                     if (e1 == e0) atomicOr(A.err, kErrAlphaKey);
-                    ne = e1 - e0;
+                    // a node without thin material (all of it thick) adds nothing to the thin
+                    // tile: its entries are left out of the warp's thin deposits
+                    ne = (!THICK || v0.x != 0.0f || v0.y != 0.0f) ? e1 - e0 : 0;
                     ebase = e0;
-                    cbase = i * NPIX;
+                    cbase = i * ROW;
                     bL = beta * v0.x * A.inv_s3;
                     bA = beta * v0.y * A.inv_s3;
                     if (THICK && v1.w > 0.0f) {
@@ -619,7 +630,7 @@ __global__ void __launch_bounds__(WPT * 32, min_warps_per_sm(NPIX, THICK) / WPT)
                         for (int e = e0; e < e1; ++e) {
                             const uint32_t ent = __ldg(A.aent + e);
                             const int h = (int)(ent & 0xffffu);
-                            const int cidx = i * NPIX + h;
+                            const int cidx = i * ROW + h;
                             const float wn = count_to_float(ent >> 16) * A.inv_s3;
                             atomicAdd(tLk + cidx, wn * v1.y);
                             atomicAdd(tAk + cidx, v1.z);
@@ -749,7 +760,7 @@ __global__ void __launch_bounds__(WPT * 32, min_warps_per_sm(NPIX, THICK) / WPT)
         //   Fp = sum_i eps_i F*_i,  (thi, tlo) = sum_i tau_thin,i,  ek = prod_i thick transmission.
         auto segments = [&](int h, int i0, int i1, float& Fp, float& thi, float& tlo, float& ek) {
             for (int i = i0; i < i1; ++i) {
-                const int ci = i * NPIX + h;
+                const int ci = i * ROW + h;
                 const float Lth = tL[ci], Ath = tA[ci];
                 const float Vk = THICK ? tVk[ci] : 0.0f;
                 if (Lth == 0.0f && Ath == 0.0f && Vk == 0.0f) continue;  // empty segment
@@ -805,9 +816,9 @@ __global__ void __launch_bounds__(WPT * 32, min_warps_per_sm(NPIX, THICK) / WPT)
                 segments(h, i0, i1, Fp, thi, tlo, ek);
                 // every part has >= 2 segments: its first two cells of ray h, read only by
                 // this thread, now hold (Fp, thi) and tlo
-                tL[i0 * NPIX + h] = Fp;
-                tA[i0 * NPIX + h] = thi;
-                tL[(i0 + 1) * NPIX + h] = tlo;
+                tL[i0 * ROW + h] = Fp;
+                tA[i0 * ROW + h] = thi;
+                tL[(i0 + 1) * ROW + h] = tlo;
             }
             __syncthreads();
             if (tid < NPIX) {
@@ -816,8 +827,8 @@ __global__ void __launch_bounds__(WPT * 32, min_warps_per_sm(NPIX, THICK) / WPT)
                 for (int p = 0; p < P; ++p) {
                     const int i0 = p * nb / P;
                     const float eps = expf(-chi) * (1.0f - clo);
-                    Fh += eps * tL[i0 * NPIX + h];
-                    add_pair(chi, clo, tA[i0 * NPIX + h], tL[(i0 + 1) * NPIX + h]);
+                    Fh += eps * tL[i0 * ROW + h];
+                    add_pair(chi, clo, tA[i0 * ROW + h], tL[(i0 + 1) * ROW + h]);
                 }
                 ray_done(h, Fh, chi + clo);
             }
@@ -828,7 +839,7 @@ __global__ void __launch_bounds__(WPT * 32, min_warps_per_sm(NPIX, THICK) / WPT)
                     if (fl)
                         for (int i = nb - 2; i >= 0; --i) {
                             if (!((fl >> i) & 1ull)) continue;
-                            const int c0 = i * NPIX + h, c1 = (i + 1) * NPIX + h;
+                            const int c0 = i * ROW + h, c1 = (i + 1) * ROW + h;
                             const float T = __ldg(R2 + i) / __ldg(R2 + i + 1);
                             tL[c0] += T * tL[c1];
                             tA[c0] += T * tA[c1];
@@ -946,8 +957,8 @@ treeray_status launch_team(treeray_ctx* c, const EvalArgs& a, const EvalArgs* bo
     constexpr int nq = THICK ? 6 : 2;
     EvalArgs b = a;
     b.stack_cap = (int)(stack_bytes_for(WPT, layout_lmax, 1) / sizeof(int));
-    const size_t smem = (size_t)nq * a.nbins * NPIX * 4 + (THICK ? NPIX * 8 + (size_t)WPT * 32 * 16 : 0) +
-                        (size_t)WPT * kOwnerCap;
+    const size_t smem = align16(align16((size_t)nq * a.nbins * tile_row(NPIX, THICK) * 4) + (THICK ? NPIX * 8 : 0)) +
+                        (THICK ? (size_t)WPT * 32 * 16 : 0) + (size_t)WPT * kOwnerCap;
     int smem_optin = 0, sms = 0;
     TR_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
     TR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
