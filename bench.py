@@ -24,6 +24,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -537,6 +538,59 @@ def _orientations_on(tr, synth, torch, dev, wl):
     c.close()
 
 
+def run_blob(args):
+    """The optically thick blob suite (S, M, L, S-, S+: 0.75-3 pc blobs at 30 K in a
+    (15 pc)^3 box, Sec. 5) on 128^3 cells: evaluate throughput of the thick kernel and the
+    radial structure of J on the GPU: the plateau inside the blob (J / J(30 K)), the
+    ambient level between 3.5 and 5.5 pc (J / J(10 K)), and the far field 4.5-7 pc
+    (J r^2 in units of the one-node-one-ray value sigma T^4 V^(2/3) / (4 pi^2)) with the
+    radial fraction of the flux. One JSON line per variant."""
+    import torch
+
+    import paper_2204_09072_gb300 as tr
+    import synth
+    dev = torch.device("cuda:0")
+    n, pc, sig = 128, 3.0857e18, 5.670374419e-5
+    for v in ("S", "M", "L", "S-", "S+"):
+        w = synth.blob_suite(v, n)
+        c = tr.Context(w.params)
+        c.build(w.box_cm, torch.as_tensor(w.rho, device=dev), torch.as_tensor(w.td, device=dev), n=n)
+        best, tune = c.autotune(65536)
+        J = torch.empty(w.n_leaves, dtype=torch.float32, device=dev)
+        F = torch.empty(3 * w.n_leaves, dtype=torch.float64, device=dev)
+        c.evaluate(J, F)
+        ms = []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            c.evaluate(J, F)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        c.check()
+        Jh = J.double().cpu().numpy()
+        Fh = F.cpu().numpy().reshape(-1, 3)
+        cen = synth.cell_centres(n, w.box_cm) - 0.5 * w.box_cm
+        r = np.sqrt((cen ** 2).sum(1))
+        core = w.rho > 5e-18
+        R = 0.5 * synth.BLOB_DIAMETER_PC[v[0]] * pc
+        dx = w.box_cm / n
+        inside = r < R - 1.5 * dx
+        amb = (r > 3.5 * pc) & (r < 5.5 * pc)
+        far = (r > 4.5 * pc) & (r < 7.0 * pc)
+        unit = sig * 30.0 ** 4 * (core.sum() * dx ** 3) ** (2.0 / 3.0) / (4 * math.pi ** 2)
+        radial = (Fh[far] * cen[far]).sum(1) / r[far] / (4 * math.pi * Jh[far])
+        print(json.dumps({"blob": v, "grid": f"{n}^3", "core_cells": int(core.sum()), "warps_per_target": best,
+                          "ms_evaluate": statistics.median(ms),
+                          "ray_evals_per_s": w.n_leaves * 48 / (statistics.median(ms) * 1e-3),
+                          "J_inside_over_J30": float((Jh[inside] / (sig * 30.0 ** 4 / math.pi)).mean())
+                          if inside.any() else None,
+                          "J_ambient_over_J10": float((Jh[amb] / (sig * 10.0 ** 4 / math.pi)).mean()),
+                          "far_Jr2_over_one_node": float((Jh[far] * r[far] ** 2 / unit).mean()),
+                          "far_radial_flux_fraction": float(radial.mean())}))
+        c.close()
+
+
 def _cloud(n, seed, sigma, n_stars, npix, uv_heating=False):
     """Turbulent cloud with stars and an ionising flux field. The flux is a network
     feature; its UV dust heating is left out unless asked for: with it, dense cells near
@@ -832,6 +886,7 @@ def main():
                     help="collapsing-core AMR grid: throughput and the plain fixed point to 1e-4")
     ap.add_argument("--orientations", action="store_true",
                     help="several HEALPix orientations: cost and J residuals against 192 rays")
+    ap.add_argument("--blob", action="store_true", help="optically thick blob suite S, M, L, S-, S+ on 128^3")
     ap.add_argument("--fp-max-iter", type=int, default=100)
     ap.add_argument("--fp-diag-iter", type=int, default=20)
     args = ap.parse_args()
@@ -849,6 +904,8 @@ def main():
         run_amr_core(args)
     elif args.orientations:
         run_orientations(args)
+    elif args.blob:
+        run_blob(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

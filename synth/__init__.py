@@ -419,3 +419,27 @@ def random_rotations(count: int, seed: int = 13) -> np.ndarray:
     R[:, 2, 1] = 2 * (y * z + x * w)
     R[:, 2, 2] = 1 - 2 * (x * x + y * y)
     return R
+
+
+BLOB_DIAMETER_PC = {"S": 0.75, "M": 1.5, "L": 3.0}
+
+
+def blob_suite(variant: str, n: int = 32, **pover) -> Workload:
+    """The optically thick blob test: a sphere at 30 K and 1e-17 g/cm^3 in a (15 pc)^3 box
+    of 10 K ambient gas at 1e-19 g/cm^3, no background radiation, Planck-mean opacity.
+    variant: "S", "M", "L" (diameters 0.75, 1.5, 3 pc); "S-" (S without ambient gas),
+    "S+" (S with the ambient density raised tenfold). Grid n^3, blob at the box centre.
+    Without ambient gas the ambient cells hold no material at all (density 0)."""
+    size = variant[0]
+    r_c = 0.5 * BLOB_DIAMETER_PC[size] * PC_CM
+    box = 15.0 * PC_CM
+    lmax, lev, ijk = uniform_structure(n)
+    x = cell_centres(n, box) - 0.5 * box
+    r = np.sqrt((x * x).sum(1))
+    core = r <= r_c
+    rho_a = {"-": 0.0, "+": 1e-18}.get(variant[1:], 1e-19)
+    rho = np.where(core, 1e-17, rho_a)
+    td = np.where(core, 30.0, 10.0)
+    return Workload(name=f"blob{variant}{n}", box_cm=box, lmax=lmax, leaf_level=lev, leaf_ijk=ijk,
+                    rho=rho.astype(np.float32), td=td.astype(np.float32),
+                    params=default_params(kappa_model=1, **pover), uniform_n=n)
