@@ -581,6 +581,11 @@ __global__ void __launch_bounds__(WPT * 32, min_warps_per_sm(NPIX, THICK) / WPT)
             // of one segment); thick deposits stay with the node's thread.
             int ne = 0, ebase = 0, cbase = 0;
             float bL = 0.0f, bA = 0.0f;
+            // thick deposits of this thread's node, spread over the warp after the thin ones:
+            // entry count, the node's L_V, A~, V (thick record) and beta, merge flags
+            int nk = 0;
+            float kLV = 0.0f, kA = 0.0f, kV = 0.0f, kbeta = 0.0f;
+            unsigned long long kfm = 0ull;
             if (GENERAL && acc && ties) {
                 deposit_tied_copies<NPIX, THICK>(A, s_aoff, tL, tA, tLk, tAk, tVk, tQk, flags, node, ox, oy, oz,
                                                  ties, lvl, d2, tl, lp);
@@ -627,17 +632,12 @@ __global__ void __launch_bounds__(WPT * 32, min_warps_per_sm(NPIX, THICK) / WPT)
                                                : fixup(guess_bin(dh * dh, lp), d2, hi, nb);
                         unsigned long long fmask = 0ull;
                         for (int j = ilo; j < ihi; ++j) fmask |= 1ull << j;
-                        for (int e = e0; e < e1; ++e) {
-                            const uint32_t ent = __ldg(A.aent + e);
-                            const int h = (int)(ent & 0xffffu);
-                            const int cidx = i * ROW + h;
-                            const float wn = count_to_float(ent >> 16) * A.inv_s3;
-                            atomicAdd(tLk + cidx, wn * v1.y);
-                            atomicAdd(tAk + cidx, v1.z);
-                            atomicAdd(tVk + cidx, wn * v1.w);
-                            atomicAdd(tQk + cidx, wn * beta * v1.w);
-                            if (fmask) atomicOr(flags + h, fmask);
-                        }
+                        nk = e1 - e0;
+                        kLV = v1.y;
+                        kA = v1.z;
+                        kV = v1.w;
+                        kbeta = beta;
+                        kfm = fmask;
                     }
                 }
             }
@@ -716,6 +716,58 @@ __global__ void __launch_bounds__(WPT * 32, min_warps_per_sm(NPIX, THICK) / WPT)
                         const float w = count_to_float(ent >> 16);
                         atomicAdd(tL + c, w * bL);
                         atomicAdd(tA + c, w * bA);
+                    }
+                }
+            }
+            if constexpr (THICK) {
+                // thick deposits: one entry per lane per pass, the node data from the owner
+                // lane by shuffles; owners recorded in the same per-warp byte array, which
+                // the thin passes above have finished reading
+                if (__any_sync(full, nk > 0)) {
+                    int tinc = nk;
+                    for (int off = 1; off < 32; off <<= 1) {
+                        const int t = __shfl_up_sync(full, tinc, off);
+                        if (lane >= off) tinc += t;
+                    }
+                    const int tt = __shfl_sync(full, tinc, 31);
+                    const int tpre = tinc - nk;
+                    if (tt <= kOwnerCap) {
+                        __syncwarp();
+                        for (int k = 0; k < nk; ++k) owner[tpre + k] = (unsigned char)lane;
+                        __syncwarp();
+                        const int teb = ebase - tpre;
+                        for (int r0 = 0; r0 < tt; r0 += 32) {
+                            const int r = r0 + lane;
+                            const int o = r < tt ? (int)owner[r] : 0;
+                            const int cb = __shfl_sync(full, cbase, o), eb = __shfl_sync(full, teb, o);
+                            const float y = __shfl_sync(full, kLV, o), z = __shfl_sync(full, kA, o);
+                            const float v = __shfl_sync(full, kV, o), bt = __shfl_sync(full, kbeta, o);
+                            const unsigned long long fm = __shfl_sync(full, kfm, o);
+                            if (r < tt) {
+                                const uint32_t ent = __ldg(A.aent + eb + r);
+                                const int h = (int)(ent & 0xffffu);
+                                const int cidx = cb + h;
+                                const float wn = count_to_float(ent >> 16) * A.inv_s3;
+                                atomicAdd(tLk + cidx, wn * y);
+                                atomicAdd(tAk + cidx, z);
+                                atomicAdd(tVk + cidx, wn * v);
+                                atomicAdd(tQk + cidx, wn * bt * v);
+                                if (fm) atomicOr(flags + h, fm);
+                            }
+                        }
+                        __syncwarp();
+                    } else {
+                        for (int e = ebase; e < ebase + nk; ++e) {
+                            const uint32_t ent = __ldg(A.aent + e);
+                            const int h = (int)(ent & 0xffffu);
+                            const int cidx = cbase + h;
+                            const float wn = count_to_float(ent >> 16) * A.inv_s3;
+                            atomicAdd(tLk + cidx, wn * kLV);
+                            atomicAdd(tAk + cidx, kA);
+                            atomicAdd(tVk + cidx, wn * kV);
+                            atomicAdd(tQk + cidx, wn * kbeta * kV);
+                            if (kfm) atomicOr(flags + h, kfm);
+                        }
                     }
                 }
             }
