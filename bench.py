@@ -458,7 +458,7 @@ def run_sweep(args):
 
 
 def run_orientations(args):
-    """Several HEALPix orientations (Sec. 6) on the 128^3 cloud and on the collapsing-core
+    """Several HEALPix orientations (Sec. 7.6) on the 128^3 cloud and on the collapsing-core
     AMR grid (the paper's ray pattern shows around its embedded sources): evaluate time for
     k turned ray sets (one seeded random orientation per cell) against the single unturned
     set, and the residual of J at 48 rays against 192 rays (ray-matched opening angles, as
@@ -540,7 +540,7 @@ def _orientations_on(tr, synth, torch, dev, wl):
 
 def run_blob(args):
     """The optically thick blob suite (S, M, L, S-, S+: 0.75-3 pc blobs at 30 K in a
-    (15 pc)^3 box, Sec. 5) on 128^3 cells: evaluate throughput of the thick kernel and the
+    (15 pc)^3 box, Sec. 5.2) on 128^3 cells: evaluate throughput of the thick kernel and the
     radial structure of J on the GPU: the plateau inside the blob (J / J(30 K)), the
     ambient level between 3.5 and 5.5 pc (J / J(10 K)), and the far field 4.5-7 pc
     (J r^2 in units of the one-node-one-ray value sigma T^4 V^(2/3) / (4 pi^2)) with the

@@ -61,7 +61,7 @@ typedef enum {
  *                  target (centre to centre) is opened iff E^2 >= theta^2 d^2, or if
  *                  it contains the target; leaves are always accepted (Sec. 4). In
  *                  (0, 2]; a negative value selects the angle matched to the ray size,
- *                  sqrt(4 pi / npix) (Sec. 6: more rays open nodes further).
+ *                  sqrt(4 pi / npix) (Sec. 7.6: more rays open nodes further).
  *  kappa_model     0: grey kappa0 per gram of gas; 1: Planck mean
  *                  0.1 cm^2/g (T/10 K)^2 capped at 150 K (Sec. 2).
  *  kappa0          grey opacity, cm^2/g (kappa_model 0).
@@ -81,7 +81,7 @@ typedef enum {
  *                  quadratically, R_i = R_0 + (R_max - R_0) (i / nbins)^2 (Sec. 4.2, "grows
  *                  quadratically").
  *  col_mapping     0: accepted nodes are mapped at their geometric centre (the default);
- *                  1: at their centre of luminosity (Sec. 6, nodes shifted towards their
+ *                  1: at their centre of luminosity (Sec. 7.6, nodes shifted towards their
  *                  centre of emission): for a node whose COL is off centre, the segment,
  *                  the straddled boundaries and the angular key come from the COL offset
  *                  in FP32 (p = centre offset + COL offset, p^2 against the integer
@@ -127,7 +127,7 @@ treeray_status treeray_create(const treeray_params* params, treeray_t* out);
 treeray_status treeray_destroy(treeray_t ctx);
 
 /*
- * Several HEALPix orientations (Sec. 6: with one orientation for every target the rays
+ * Several HEALPix orientations (Sec. 7.6: with one orientation for every target the rays
  * imprint a ray-like pattern on the radiation field; turning the ray set from target to
  * target breaks it up, at the price of one angular-kernel table per orientation).
  *  k       number of orientations, 1..64; 0 goes back to the single unturned ray set
@@ -413,7 +413,7 @@ treeray_status treeray_morton_order_noalloc(const treeray_grid* grid, uint64_t* 
 treeray_status treeray_alpha_counts_host(int npix, int s, const int64_t* K, int32_t* counts);
 
 /* Host-only: the same counts for the ray set turned by the row-major rotation rot[9]
- * (Sec. 6, several orientations): sample direction v counts in the pixel of R^T v. */
+ * (Sec. 7.6, several orientations): sample direction v counts in the pixel of R^T v. */
 treeray_status treeray_alpha_counts_rotated_host(int npix, int s, const int64_t* K, const double* rot,
                                                  int32_t* counts);
 

@@ -70,7 +70,7 @@ typedef struct {
     int alpha_s;           /* sub-points per axis of the angular kernel's sampling */
     int periodic;          /* bit a set: axis a is periodic (nearest copies, Sec. 4.2) */
     int bin_spacing;       /* 0: geometric radii, 1: quadratically growing radii (Sec. 4.2) */
-    int col_mapping;       /* 1: map accepted nodes at their centre of luminosity (Sec. 6) */
+    int col_mapping;       /* 1: map accepted nodes at their centre of luminosity (Sec. 7.6) */
 } or_params;
 
 /* ------------------------------------------------------------------ HEALPix
@@ -208,7 +208,7 @@ static void or_key(const int64_t* o, int64_t E, int64_t* K) {
 }
 
 /* Hit counts of the s^3 sample directions per pixel for key K. counts: int[npix].
- * rot (may be NULL): the ray set of a turned HEALPix orientation (Sec. 6), a row-major
+ * rot (may be NULL): the ray set of a turned HEALPix orientation (Sec. 7.6), a row-major
  * rotation R; ray h of that orientation points along R n_h, so a sample direction v is
  * counted in ray h when R^T v lies in pixel h. (R^T v)_a = R_0a v_x + R_1a v_y + R_2a v_z,
  * summed in that order. */
@@ -333,7 +333,7 @@ typedef struct {
     double* rho;
     or_alpha_table alpha;
     int level_first[64], level_count[64];
-    /* several HEALPix orientations (Sec. 6); n_orient = 0: the single unturned one */
+    /* several HEALPix orientations (Sec. 7.6); n_orient = 0: the single unturned one */
     int n_orient;
     double* rot;            /* [n_orient][9] row-major rotations R_o */
     uint8_t* orient;        /* per leaf: its orientation (caller leaf index) */
@@ -480,7 +480,7 @@ int or_build(const or_params* p, int lmax, double box_cm, int64_t nleaves,
     or_tree* t = (or_tree*)calloc(1, sizeof(or_tree));
     t->p = *p;
     /* theta < 0: the opening angle matched to the ray size, sqrt(4 pi / N_pix)
-     * (Sec. 6: more rays open nodes further, toward the ray's angular size) */
+     * (Sec. 7.6: more rays open nodes further, toward the ray's angular size) */
     if (t->p.theta < 0.0) t->p.theta = sqrt(4.0 * OR_PI / (double)p->npix);
     t->lmax = lmax;
     t->box = box_cm;
@@ -762,7 +762,7 @@ static void or_map_node(const or_tree* t, or_alpha_table* at, const or_node* nd,
     int nb = ry->nbins, np = ry->npix;
     double u = t->u;
     int own = (d2 == 0);
-    /* mapping at the centre of luminosity (Sec. 6: "we shift the nodes towards their
+    /* mapping at the centre of luminosity (Sec. 7.6: "we shift the nodes towards their
      * center of emission during mapping to rays"), for nodes whose COL is off centre.
      * Reading: the position p = o + c, c the COL offset rounded to FP32 (as a GPU node
      * record holds it), is formed and squared in FP32; the segment and the straddled
@@ -901,7 +901,7 @@ double or_ray_integrate(int nbins, int npix, double* Lth, double* Ath, double* L
 }
 
 /*
- * Several HEALPix orientations (Sec. 6: with one orientation for every target the ray
+ * Several HEALPix orientations (Sec. 7.6: with one orientation for every target the ray
  * pattern shows in the radiation field; turning the ray set from target to target spreads
  * it, at the price of one angular-kernel table per orientation).
  * k orientations with rotations rot[k][9] (row-major; orthonormal with determinant +1,

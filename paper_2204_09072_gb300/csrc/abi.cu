@@ -230,7 +230,7 @@ treeray_status treeray_create(const treeray_params* p, treeray_t* out) {
         return TREERAY_ENOMEM;
     }
     c->p = *p;
-    // negative theta: the opening angle matched to the ray size (Sec. 6)
+    // negative theta: the opening angle matched to the ray size (Sec. 7.6)
     if (c->p.theta < 0.0) c->p.theta = std::sqrt(4.0 * kPi / (double)p->npix);
     cudaGetDevice(&c->device);
     c->ht.npix = p->npix;

@@ -596,7 +596,7 @@ __global__ void __launch_bounds__(WPT * 32, min_warps_per_sm(NPIX, THICK) / WPT)
                 const float4 v0 = __ldg(A.thin + node);
                 const float4 v1 = __ldg(A.thick + node);
                 const float rx = fx + v0.z, ry = fy + v0.w, rz = fz + v1.x;
-                // mapping at the centre of luminosity (Sec. 6): segment, straddles and key
+                // mapping at the centre of luminosity (Sec. 7.6): segment, straddles and key
                 // from the COL position in FP32 for nodes whose COL is off centre
                 const bool colmap = GENERAL && A.col_mapping && (v0.z != 0.0f || v0.w != 0.0f || v1.x != 0.0f);
                 const float pd2 = colmap ? sq3_rn(rx, ry, rz) : 0.0f;

@@ -129,7 +129,7 @@ struct treeray_ctx {
     cudaEvent_t fp_ev[2] = {nullptr, nullptr};
     int* stack_scr = nullptr;    // evaluate: team stacks (global scratch, grow-only)
     size_t stack_scr_bytes = 0;
-    // several HEALPix orientations (Sec. 6)
+    // several HEALPix orientations (Sec. 7.6)
     std::vector<double> rot;     // [k][9] row-major rotations; empty: the single unturned ray set
     uint8_t* orient = nullptr;   // device [orient_n]: orientation of each leaf (caller order)
     int64_t orient_n = 0;        // leaves the map was made for

@@ -118,7 +118,7 @@ void healpix_pix2vec(int nside, int pix, double* v) {
 // alpha for a node at quantised offset K (units of 1/8 of its edge) from the target:
 // the s^3 sub-cube centres of the node, seen from the target along
 // (2 s K / 8 + 2 a + 1 - s) for a = 0..s-1 per axis, counted per pixel.
-// rot (row-major R, may be null): a turned ray set (Sec. 6), whose ray h points along
+// rot (row-major R, may be null): a turned ray set (Sec. 7.6), whose ray h points along
 // R n_h; a direction v then counts for ray h when R^T v lies in pixel h.
 void alpha_counts(int npix, int s, const int64_t* K, int32_t* counts, const double* rot) {
     const int ns = healpix_nside(npix);

@@ -1,4 +1,4 @@
-"""Several HEALPix orientations (Sec. 6) on the GPU against the FP64 oracle, through the
+"""Several HEALPix orientations (Sec. 7.6) on the GPU against the FP64 oracle, through the
 C ABI: each target uses the angular kernel and ray directions of its own orientation.
 J within 1e-4 relative, F within 1e-4 of max(|F|, 1e-2 x 4 pi J); walk totals exact."""
 import numpy as np

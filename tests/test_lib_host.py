@@ -58,7 +58,7 @@ def test_bad_args_host(trlib):
 
 
 def test_turned_alpha_table_matches_oracle(trlib, orc):
-    """Several HEALPix orientations (Sec. 6): the library's counts for a turned ray set
+    """Several HEALPix orientations (Sec. 7.6): the library's counts for a turned ray set
     equal the oracle's, key for key, for random rotations and a quarter turn."""
     import synth
     rng = np.random.default_rng(1)

@@ -1,4 +1,4 @@
-"""The optically thick blob test (Sec. 5, optically thick blob of dust) as pins of the
+"""The optically thick blob test (Sec. 5.2, optically thick blob of dust) as pins of the
 oracle's thick path: blobs S, M, L (0.75, 1.5, 3 pc across) at 30 K in a (15 pc)^3 box,
 with ambient gas at 10 K (S, M, L), without it (S-, M-, L-) or ten times denser (S+),
 on 64^3 cells (S is 2 x 2 x 2 cells, as in the paper's runs)."""

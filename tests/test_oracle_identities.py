@@ -275,7 +275,7 @@ def test_quadratic_radii_and_ray_matched_theta(orc):
 
 
 def test_col_mapping_identities(orc):
-    """Mapping at the centre of luminosity (Sec. 6): emission only, J still equals the
+    """Mapping at the centre of luminosity (Sec. 7.6): emission only, J still equals the
     sum over accepted nodes of L / (16 pi^2 r_COL^2) (beta cancels R_i^2 whatever segment
     the COL picks); leaves (COL at the centre) map as before, so with every leaf accepted
     the result equals geometric mapping exactly."""

@@ -1,4 +1,4 @@
-"""Pins of the oracle's several HEALPix orientations (Sec. 6): a turned ray set is the
+"""Pins of the oracle's several HEALPix orientations (Sec. 7.6): a turned ray set is the
 HEALPix grid rotated by R, so a direction v belongs to ray h when R^T v lies in pixel h,
 and ray h points along R n^h. Checked against what geometry fixes: the identity, the
 quarter turn about the polar axis (a symmetry of the HEALPix grid), the orientation
