@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <memory>
 #include <new>
 #include <vector>
 
@@ -68,6 +69,19 @@ struct __align__(16) EvalArgs {
     double u;
     double inv_u2;  // 1 / u^2: flux unit = L_scale / u^2 (L_scale a power of two)
 };
+
+// A batch launch's parameters: the launch-wide fields (work counter, total targets, team
+// stacks) in `launch`, then up to kMaxLaunchBoxes box descriptors and the first target
+// of each box; a batch with more boxes is launched in chunks. Sized to fit the 32764
+// bytes of kernel parameters.
+constexpr int kMaxLaunchBoxes = (32764 - (int)sizeof(EvalArgs) - 16) / ((int)sizeof(EvalArgs) + 8) - 1;
+struct __align__(16) BatchArgs {
+    EvalArgs launch;
+    EvalArgs box[kMaxLaunchBoxes];
+    int64_t start[kMaxLaunchBoxes + 1];
+    int nbox;
+};
+static_assert(sizeof(BatchArgs) <= 32764, "batch parameters exceed the kernel parameter space");
 
 namespace {
 
@@ -405,17 +419,15 @@ __device__ __noinline__ void deposit_tied_copies(const EvalArgs& A, const int32_
 //   deposit: the warp's thin deposits are spread one angular-kernel entry per lane, in
 //            child-major node order so that sibling nodes, which often hit the same cell,
 //            fall into different rounds; shared-memory atomics into the tile; thick
-//            deposits stay with the node's thread;
+//            deposits follow in a second pass, also one entry per lane;
 //   rays:    threads integrate the rays' segments inside out (thin tiles with spare
 //            threads cut each ray into consecutive parts joined by their transmission),
 //            then the team reduces J and F.
 // BATCH: the targets of several boxes share the work counter, each box with its own
-// descriptor (boxes, box_start); otherwise the one box's descriptor is the kernel
-// parameter itself, read from the constant bank.
+// descriptor. Either way the descriptors are kernel parameters, read from the constant
+// bank: one box's as the launch's own, a batch's as an array (BatchArgs).
 template <int NPIX, bool THICK, int WPT, bool GENERAL, bool BATCH>
-__global__ void __launch_bounds__(WPT * 32, min_warps_per_sm(NPIX, THICK) / WPT)
-    k_evaluate(const __grid_constant__ EvalArgs a, const EvalArgs* __restrict__ boxes,
-               const int64_t* __restrict__ box_start, int nbox) {
+__device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs* bp) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int NT = WPT * 32;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -452,41 +464,30 @@ __global__ void __launch_bounds__(WPT * 32, min_warps_per_sm(NPIX, THICK) / WPT)
     const unsigned lt_mask = (1u << lane) - 1u;
     const float omega = (float)(4.0 * kPi / NPIX);
     if (a.skip && *a.skip) return;
-    // the box descriptor: the kernel parameter (one box: uniform constant-bank operands, no
-    // shared-memory loads), or a shared-memory copy of the current target's box (a batch)
-    __shared__ __align__(16) EvalArgs s_box;
-    __shared__ int s_b, s_bcur;
-    const EvalArgs& A = BATCH ? s_box : a;
-    if (BATCH && tid == 0) s_bcur = -1;
+    __shared__ int s_b;  // batch: the box of the current target
 
     for (;;) {
         if (tid == 0) s_q = (long long)atomicAdd(a.queue, 1ull);
         __syncthreads();
         long long q = s_q;
         if (q >= a.n) break;
+        int b = 0;
         if constexpr (BATCH) {
             if (tid == 0) {
-                int lo = 0, hi = nbox - 1;  // last box with box_start[b] <= q
+                int lo = 0, hi = bp->nbox - 1;  // last box with start[b] <= q
                 while (lo < hi) {
                     const int mid = (lo + hi + 1) >> 1;
-                    if (box_start[mid] <= q) lo = mid;
+                    if (bp->start[mid] <= q) lo = mid;
                     else hi = mid - 1;
                 }
                 s_b = lo;
             }
             __syncthreads();
-            const int b = s_b;
-            if (b != s_bcur) {  // consecutive targets mostly come from the same box
-                const EvalArgs* src = boxes + b;
-                for (int w = tid; w < (int)(sizeof(EvalArgs) / 8); w += NT)
-                    reinterpret_cast<unsigned long long*>(&s_box)[w] =
-                        reinterpret_cast<const unsigned long long*>(src)[w];
-            }
-            q -= box_start[b];
-            __syncthreads();
-            if (tid == 0) s_bcur = b;
+            b = s_b;
+            q -= bp->start[b];
         }
         __syncthreads();
+        const EvalArgs& A = *(BATCH ? &bp->box[b] : &a);
         const int W = 2 * A.D + 1;
         const int4 root = A.geo[0];
         int64_t s;
@@ -967,6 +968,19 @@ __global__ void __launch_bounds__(WPT * 32, min_warps_per_sm(NPIX, THICK) / WPT)
     }
 }
 
+template <int NPIX, bool THICK, int WPT, bool GENERAL>
+__global__ void __launch_bounds__(WPT * 32, min_warps_per_sm(NPIX, THICK) / WPT)
+    k_evaluate(const __grid_constant__ EvalArgs a) {
+    evaluate_team<NPIX, THICK, WPT, GENERAL, false>(a, nullptr);
+}
+
+// batches run teams of 4 warps
+template <int NPIX, bool THICK, bool GENERAL>
+__global__ void __launch_bounds__(4 * 32, min_warps_per_sm(NPIX, THICK) / 4)
+    k_evaluate_batch(const __grid_constant__ BatchArgs p) {
+    evaluate_team<NPIX, THICK, 4, GENERAL, true>(p.launch, &p);
+}
+
 template <typename K>
 treeray_status launch_persistent(treeray_ctx* c, K kern, size_t per_warp, int max_warps, int64_t n,
                                  unsigned long long* queue, cudaStream_t s, const EvalArgs& a) {
@@ -1006,6 +1020,7 @@ size_t stack_bytes_for(int wpt, int lmax, int blocks) {
 template <int NPIX, bool THICK, int WPT, bool GENERAL, bool BATCH>
 treeray_status launch_team(treeray_ctx* c, const EvalArgs& a, const EvalArgs* boxes,
                            const int64_t* box_start, int nbox, int layout_lmax, cudaStream_t s) {
+    // batch: boxes and box_start are HOST arrays of the boxes' descriptors and first targets
     constexpr int nq = THICK ? 6 : 2;
     EvalArgs b = a;
     b.stack_cap = (int)(stack_bytes_for(WPT, layout_lmax, 1) / sizeof(int));
@@ -1018,25 +1033,59 @@ treeray_status launch_team(treeray_ctx* c, const EvalArgs& a, const EvalArgs* bo
         set_error("evaluate: the per-target ray tile (npix x nbins) exceeds shared memory");
         return TREERAY_EINVAL;
     }
-    auto kern = k_evaluate<NPIX, THICK, WPT, GENERAL, BATCH>;
-    TR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    TR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WPT * 32, smem));
-    if (per_sm < 1) {
-        set_error("evaluate: kernel does not fit on an SM");
-        return TREERAY_EINVAL;
+    // persistent grid for n targets: resident blocks of the kernel, and team stacks for them
+    auto grid_for = [&](auto kern, int64_t n, int64_t& blocks) -> treeray_status {
+        TR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int per_sm = 0;
+        TR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WPT * 32, smem));
+        if (per_sm < 1) {
+            set_error("evaluate: kernel does not fit on an SM");
+            return TREERAY_EINVAL;
+        }
+        blocks = std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * sms, n));
+        if (c->stack_scr_bytes < stack_bytes_for(WPT, layout_lmax, (int)blocks)) {
+            const treeray_status rc = reserve_eval_stacks(c, layout_lmax, s);
+            if (rc != TREERAY_OK) return rc;
+        }
+        return TREERAY_OK;
+    };
+    int64_t blocks = 0;
+    treeray_status rc;
+    if constexpr (!BATCH) {
+        auto kern = k_evaluate<NPIX, THICK, WPT, GENERAL>;
+        if ((rc = grid_for(kern, a.n, blocks)) != TREERAY_OK) return rc;
+        b.stack = c->stack_scr;
+        TR_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), s));
+        kern<<<(int)blocks, WPT * 32, smem, s>>>(b);
+        c->launches += 1;
+        TR_CUDA(cudaGetLastError());
+    } else {
+        static_assert(WPT == 4, "batches run teams of 4 warps");
+        auto kern = k_evaluate_batch<NPIX, THICK, GENERAL>;
+        std::unique_ptr<BatchArgs> p(new (std::nothrow) BatchArgs());
+        if (!p) {
+            set_error("out of host memory");
+            return TREERAY_ENOMEM;
+        }
+        for (int c0 = 0; c0 < nbox; c0 += kMaxLaunchBoxes) {  // one launch per chunk of boxes
+            const int c1 = std::min(nbox, c0 + kMaxLaunchBoxes);
+            p->launch = b;
+            p->launch.n = box_start[c1] - box_start[c0];
+            p->nbox = c1 - c0;
+            for (int k = 0; k < c1 - c0; ++k) {
+                p->box[k] = boxes[c0 + k];
+                p->start[k] = box_start[c0 + k] - box_start[c0];
+            }
+            p->start[c1 - c0] = p->launch.n;
+            if (p->launch.n == 0) continue;
+            if ((rc = grid_for(kern, p->launch.n, blocks)) != TREERAY_OK) return rc;
+            p->launch.stack = c->stack_scr;
+            TR_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), s));
+            kern<<<(int)blocks, 4 * 32, smem, s>>>(*p);
+            c->launches += 1;
+            TR_CUDA(cudaGetLastError());
+        }
     }
-    int64_t blocks = (int64_t)per_sm * sms;
-    if (blocks > a.n) blocks = a.n;
-    if (c->stack_scr_bytes < stack_bytes_for(WPT, layout_lmax, (int)blocks)) {
-        const treeray_status rc = reserve_eval_stacks(c, layout_lmax, s);
-        if (rc != TREERAY_OK) return rc;
-    }
-    b.stack = c->stack_scr;
-    TR_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), s));
-    kern<<<(int)blocks, WPT * 32, smem, s>>>(b, boxes, box_start, nbox);
-    c->launches += 1;
-    TR_CUDA(cudaGetLastError());
     return TREERAY_OK;
 }
 
@@ -1285,15 +1334,12 @@ struct treeray_batch {
         std::vector<int> box;  // indices into ctx
         std::vector<tr::EvalArgs> desc;
         std::vector<int64_t> start;
-        tr::EvalArgs* d_desc = nullptr;
-        int64_t* d_start = nullptr;
         unsigned long long* d_queue = nullptr;
         int max_lmax = 0;
         bool periodic = false;  // some box has periodic axes or COL mapping (general kernel)
     };
     std::vector<treeray_t> ctx;
     Group g[2];
-    bool uploaded = false;
     std::vector<void*> lastJ, lastF;
     cudaGraphExec_t graph = nullptr;
     cudaStream_t gstream = nullptr;
@@ -1349,17 +1395,9 @@ treeray_status treeray_batch_create(const treeray_t* ctxs, int n_boxes, treeray_
         // deepest tree of the group
         const treeray_status rs = reserve_eval_stacks(b->ctx[g.box[0]], g.max_lmax, nullptr);
         if (rs != TREERAY_OK) return fail(rs);
-        const size_t nb = g.box.size();
-        if (cudaMalloc(&g.d_desc, sizeof(EvalArgs) * nb) != cudaSuccess ||
-            cudaMalloc(&g.d_start, sizeof(int64_t) * (nb + 1)) != cudaSuccess ||
-            cudaMalloc(&g.d_queue, sizeof(unsigned long long)) != cudaSuccess) {
+        if (cudaMalloc(&g.d_queue, sizeof(unsigned long long)) != cudaSuccess) {
             set_error("batch_create: device allocation failed");
             return fail(TREERAY_ENOMEM);
-        }
-        if (cudaMemcpy(g.d_start, g.start.data(), sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice) !=
-            cudaSuccess) {
-            set_error("batch_create: upload failed");
-            return fail(TREERAY_ECUDA);
         }
     }
     *out = b;
@@ -1373,8 +1411,6 @@ treeray_status treeray_batch_destroy(treeray_batch_t b) {
     for (cudaEvent_t e : b->ev)
         if (e) cudaEventDestroy(e);
     for (auto& g : b->g) {
-        if (g.d_desc) cudaFree(g.d_desc);
-        if (g.d_start) cudaFree(g.d_start);
         if (g.d_queue) cudaFree(g.d_queue);
     }
     delete b;
@@ -1393,7 +1429,7 @@ treeray_status batch_launch(treeray_batch_t b, cudaStream_t s) {
         a.targets = nullptr;
         a.skip = nullptr;
         const treeray_status rc =
-            dispatch_team(c0, t == 1, g.periodic, 4, a, g.d_desc, g.d_start, (int)g.box.size(), g.max_lmax, s);
+            dispatch_team(c0, t == 1, g.periodic, 4, a, g.desc.data(), g.start.data(), (int)g.box.size(), g.max_lmax, s);
         if (rc != TREERAY_OK) return rc;
     }
     return TREERAY_OK;
@@ -1406,7 +1442,7 @@ treeray_status treeray_batch_evaluate(treeray_batch_t b, float* const* J, double
         set_error("batch_evaluate: batch, J and F required");
         return TREERAY_EINVAL;
     }
-    bool changed = !b->uploaded;
+    bool changed = !b->graph;
     for (auto& g : b->g)
         for (size_t q = 0; q < g.box.size(); ++q) {
             const int k = g.box[q];
@@ -1419,17 +1455,11 @@ treeray_status treeray_batch_evaluate(treeray_batch_t b, float* const* J, double
             g.desc[q].F = F[k];
         }
     cudaStream_t us = (cudaStream_t)stream;
-    if (changed) {
-        if (b->graph) {
-            cudaGraphExecDestroy(b->graph);
-            b->graph = nullptr;
-        }
-        for (auto& g : b->g)
-            if (!g.box.empty())
-                TR_CUDA(cudaMemcpyAsync(g.d_desc, g.desc.data(), sizeof(EvalArgs) * g.box.size(),
-                                        cudaMemcpyHostToDevice, us));
-        TR_CUDA(cudaStreamSynchronize(us));  // the host descriptors may change on the next call
-        b->uploaded = true;
+    // the descriptors travel as kernel parameters: a captured graph holds the output
+    // pointers of its capture and is captured again when they change
+    if (changed && b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
     }
     if (!use_graph) return batch_launch(b, us);
     if (!b->gstream) TR_CUDA(cudaStreamCreateWithFlags(&b->gstream, cudaStreamNonBlocking));
