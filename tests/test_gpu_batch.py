@@ -64,3 +64,32 @@ def test_autotune_picks_a_team_size(orc):
     tg = synth.sample_targets(w.n_leaves, 256, seed=3)
     Jr, _ = orc.Tree(w).evaluate(tg)
     assert np.abs(J[tg] / Jr - 1).max() <= 1e-4
+
+
+def test_batch_larger_than_one_launch(orc):
+    """More boxes than one launch's parameters hold (97): the batch runs in chunks; every
+    box matches its own single-box evaluation, thin and thick boxes mixed."""
+    import torch
+
+    import paper_2204_09072_gb300 as tr
+    ws = [synth.random_uniform(8, seed=300 + k, thick_frac=0.1 if k % 3 == 0 else 0.0, n_stars=1)
+          for k in range(203)]
+    ctxs = [build_ctx(w)[0] for w in ws]
+    singles = [evaluate(c) for c in ctxs]
+    b = tr.Batch(ctxs)
+    Js = [torch.empty(c.leaf_count, dtype=torch.float32, device="cuda:0") for c in ctxs]
+    Fs = [torch.empty(3 * c.leaf_count, dtype=torch.float64, device="cuda:0") for c in ctxs]
+    b.evaluate(Js, Fs, use_graph=True)
+    for c in ctxs:
+        c.check()
+    for (Js1, Fs1), J, F in zip(singles, Js, Fs):
+        J = J.double().cpu().numpy()
+        F = F.cpu().numpy().reshape(-1, 3)
+        assert np.abs(J / Js1 - 1).max() < 1e-5
+        assert flux_err(F, Fs1, Js1).max() < 1e-5
+    Jr, Fr = orc.Tree(ws[150]).evaluate()
+    J = Js[150].double().cpu().numpy()
+    assert np.abs(J / Jr - 1).max() <= 1e-4
+    b.close()
+    for c in ctxs:
+        c.close()
