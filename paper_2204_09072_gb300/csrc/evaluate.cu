@@ -305,7 +305,10 @@ __global__ void __launch_bounds__(256) k_walk_list(EvalArgs a) {
     }
 }
 
-constexpr int kOwnerCap = 256;  // entries per warp and walk step spread one per lane
+// entries per warp and walk step spread one per lane (more go through a serial fallback);
+// thick teams keep a few bytes less so that nine of them fit an SM at 48 rays and 20
+// segments
+__host__ __device__ constexpr int owner_cap(bool thick) { return thick ? 240 : 256; }
 
 // Row stride of the (segment x ray) tile in shared memory: a few words more than the rays,
 // so that the same ray in nearby segments (a common pair among the entries of one deposit
@@ -318,7 +321,7 @@ __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~(siz
 // Warps resident per SM that the register budget is cut for: thin tiles at N_pix <= 48 are
 // small enough for 64 warps per SM; larger thin tiles are limited by shared memory anyway;
 // thick kernels (six-quantity tiles) fit 32 warps without spilling.
-constexpr int min_warps_per_sm(int npix, bool thick) { return thick ? 32 : (npix <= 48 ? 64 : 48); }
+constexpr int min_warps_per_sm(int npix, bool thick) { return thick ? 36 : (npix <= 48 ? 64 : 48); }
 
 // Deposit of an accepted node whose closest periodic copies are tied (it lies exactly half
 // a box away on a periodic axis): every closest copy, with weight 1/2 per tied axis, by the
@@ -436,7 +439,7 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
     const int cells = nb * ROW;
     constexpr int nq = THICK ? 6 : 2;
     // layout: tile [nq][nb][ROW] f32 | THICK: flags [NPIX] u64 | THICK: per warp node
-    //         buffer int4[32] | per warp entry owners u8[kOwnerCap] (16-byte aligned parts)
+    //         per warp entry owners u8[owner_cap] (16-byte aligned parts)
     // The team's stack of child groups is this block's slice of a global scratch array:
     // it stays in L1, and leaving it out of shared memory lets more teams share an SM.
     float* tL = reinterpret_cast<float*>(smem);
@@ -446,12 +449,10 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
     float* tVk = tAk + cells;
     float* tQk = tVk + cells;
     unsigned long long* flags = reinterpret_cast<unsigned long long*>(smem + align16((size_t)nq * cells * 4));
-    // each entry's node data: thin kernels take it from the owner lane by shuffles (fewer
-    // shared-memory operations and registers, measured faster); thick kernels, whose
-    // occupancy is bound by their larger tile anyway, through a per-warp node buffer
-    int4* nodebufs = reinterpret_cast<int4*>(smem + align16(align16((size_t)nq * cells * 4) + (THICK ? NPIX * 8 : 0)));
-    int4* nodebuf = nodebufs + warp * 32;
-    unsigned char* owner = reinterpret_cast<unsigned char*>(nodebufs + (THICK ? WPT * 32 : 0)) + warp * kOwnerCap;
+    // each entry's node data comes from the owner lane by shuffles (fewer shared-memory
+    // operations and registers than a per-warp node buffer, and smaller thick teams)
+    constexpr int OCAP = owner_cap(THICK);
+    unsigned char* owner = smem + align16(align16((size_t)nq * cells * 4) + (THICK ? NPIX * 8 : 0)) + warp * OCAP;
     const int stack_cap = a.stack_cap;
     int* stack = a.stack + (size_t)blockIdx.x * stack_cap;
     __shared__ int s_sp, s_overflow;
@@ -654,59 +655,37 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
             const int tw = __shfl_sync(full, inc, 31);
             const int pre = __shfl_sync(full, inc - nv, ((lane & 7) << 2) | (lane >> 3));
             if (tw > 0) {
-                if (tw <= kOwnerCap) {
+                if (tw <= OCAP) {
                     if (ne > 0) {
-                        if (THICK) nodebuf[lane] = make_int4(cbase, ebase - pre, __float_as_int(bL), __float_as_int(bA));
                         for (int k = 0; k < ne; ++k) owner[pre + k] = (unsigned char)lane;
                     }
                     __syncwarp();
-                    if constexpr (THICK) {
-                        // two entries per lane per pass: their loads and atomics overlap
-                        for (int r = lane; r < tw; r += 64) {
-                            const int r2 = r + 32;
-                            const int4 nd = nodebuf[owner[r]];
-                            const int4 nd2 = r2 < tw ? nodebuf[owner[r2]] : nd;
-                            const uint32_t ent = __ldg(A.aent + nd.y + r);
-                            const uint32_t ent2 = r2 < tw ? __ldg(A.aent + nd2.y + r2) : 0u;
+                    // two entries per lane per pass; each entry's node data comes from its
+                    // owner lane by shuffles (warp-uniform passes, full-mask shuffles)
+                    const int eb = ebase - pre;
+                    for (int r0 = 0; r0 < tw; r0 += 64) {
+                        const int r = r0 + lane, r2 = r + 32;
+                        const int o1 = r < tw ? (int)owner[r] : 0;
+                        const int o2 = r2 < tw ? (int)owner[r2] : 0;
+                        const int4 nd = make_int4(__shfl_sync(full, cbase, o1), __shfl_sync(full, eb, o1),
+                                                  __shfl_sync(full, __float_as_int(bL), o1),
+                                                  __shfl_sync(full, __float_as_int(bA), o1));
+                        const int4 nd2 = make_int4(__shfl_sync(full, cbase, o2), __shfl_sync(full, eb, o2),
+                                                   __shfl_sync(full, __float_as_int(bL), o2),
+                                                   __shfl_sync(full, __float_as_int(bA), o2));
+                        const uint32_t ent = r < tw ? __ldg(A.aent + nd.y + r) : 0u;
+                        const uint32_t ent2 = r2 < tw ? __ldg(A.aent + nd2.y + r2) : 0u;
+                        if (r < tw) {
                             const int c = nd.x + (int)(ent & 0xffffu);
                             const float w = count_to_float(ent >> 16);
                             atomicAdd(tL + c, w * __int_as_float(nd.z));
                             atomicAdd(tA + c, w * __int_as_float(nd.w));
-                            if (r2 < tw) {
-                                const int c2 = nd2.x + (int)(ent2 & 0xffffu);
-                                const float w2 = count_to_float(ent2 >> 16);
-                                atomicAdd(tL + c2, w2 * __int_as_float(nd2.z));
-                                atomicAdd(tA + c2, w2 * __int_as_float(nd2.w));
-                            }
                         }
-                    } else {
-                        // two entries per lane per pass; each entry's node data comes from its
-                        // owner lane by shuffles (warp-uniform passes, full-mask shuffles)
-                        const int eb = ebase - pre;
-                        for (int r0 = 0; r0 < tw; r0 += 64) {
-                            const int r = r0 + lane, r2 = r + 32;
-                            const int o1 = r < tw ? (int)owner[r] : 0;
-                            const int o2 = r2 < tw ? (int)owner[r2] : 0;
-                            const int4 nd = make_int4(__shfl_sync(full, cbase, o1), __shfl_sync(full, eb, o1),
-                                                      __shfl_sync(full, __float_as_int(bL), o1),
-                                                      __shfl_sync(full, __float_as_int(bA), o1));
-                            const int4 nd2 = make_int4(__shfl_sync(full, cbase, o2), __shfl_sync(full, eb, o2),
-                                                       __shfl_sync(full, __float_as_int(bL), o2),
-                                                       __shfl_sync(full, __float_as_int(bA), o2));
-                            const uint32_t ent = r < tw ? __ldg(A.aent + nd.y + r) : 0u;
-                            const uint32_t ent2 = r2 < tw ? __ldg(A.aent + nd2.y + r2) : 0u;
-                            if (r < tw) {
-                                const int c = nd.x + (int)(ent & 0xffffu);
-                                const float w = count_to_float(ent >> 16);
-                                atomicAdd(tL + c, w * __int_as_float(nd.z));
-                                atomicAdd(tA + c, w * __int_as_float(nd.w));
-                            }
-                            if (r2 < tw) {
-                                const int c2 = nd2.x + (int)(ent2 & 0xffffu);
-                                const float w2 = count_to_float(ent2 >> 16);
-                                atomicAdd(tL + c2, w2 * __int_as_float(nd2.z));
-                                atomicAdd(tA + c2, w2 * __int_as_float(nd2.w));
-                            }
+                        if (r2 < tw) {
+                            const int c2 = nd2.x + (int)(ent2 & 0xffffu);
+                            const float w2 = count_to_float(ent2 >> 16);
+                            atomicAdd(tL + c2, w2 * __int_as_float(nd2.z));
+                            atomicAdd(tA + c2, w2 * __int_as_float(nd2.w));
                         }
                     }
                     __syncwarp();
@@ -732,7 +711,7 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
                     }
                     const int tt = __shfl_sync(full, tinc, 31);
                     const int tpre = tinc - nk;
-                    if (tt <= kOwnerCap) {
+                    if (tt <= OCAP) {
                         __syncwarp();
                         for (int k = 0; k < nk; ++k) owner[tpre + k] = (unsigned char)lane;
                         __syncwarp();
@@ -1025,7 +1004,7 @@ treeray_status launch_team(treeray_ctx* c, const EvalArgs& a, const EvalArgs* bo
     EvalArgs b = a;
     b.stack_cap = (int)(stack_bytes_for(WPT, layout_lmax, 1) / sizeof(int));
     const size_t smem = align16(align16((size_t)nq * a.nbins * tile_row(NPIX, THICK) * 4) + (THICK ? NPIX * 8 : 0)) +
-                        (THICK ? (size_t)WPT * 32 * 16 : 0) + (size_t)WPT * kOwnerCap;
+                        (size_t)WPT * owner_cap(THICK);
     int smem_optin = 0, sms = 0;
     TR_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
     TR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
