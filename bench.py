@@ -309,7 +309,7 @@ def run_ours(args):
                                     "ms_evaluate": ms_eval,
                                     "ms_radpressure_dust": statistics.mean(post_ms),
                                     "warps_per_target": best_wpt,
-                                    "autotune_ms_wpt2_4_8": tune_ms}),
+                                    "autotune_ms_wpt2_3_4_8": tune_ms}),
             "roofline": {"bound": "hbm", "kernel": "k_evaluate", "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_kind": peak_kind, "traffic": traffic,
@@ -451,7 +451,7 @@ def run_sweep(args):
         print(json.dumps({"sweep": "turb128", "npix": npix, "nbins": nb,
                           "theta": "ray-matched" if extra.get("theta", 0.5) < 0 else 0.5,
                           "bin_spacing": "quadratic" if extra.get("bin_spacing", 0) == 1 else "geometric",
-                          "warps_per_target": best, "autotune_ms_wpt2_4_8_on_65536": tune, "ms_evaluate": ms,
+                          "warps_per_target": best, "autotune_ms_wpt2_3_4_8_on_65536": tune, "ms_evaluate": ms,
                           "ray_evals_per_s": w.n_leaves * npix / (ms * 1e-3),
                           "walk_visits_accepted_entries": st}))
         c.close()
@@ -770,7 +770,7 @@ def run_amr_core(args):
     out = {
         "workload": f"amr_core: collapsing-core AMR, {n} leaves, levels {sorted(set(np.asarray(w.leaf_level).tolist()))}, "
                     f"{len(w.star_lum)} stars, N_pix {npix}, {w.params['nbins']} segments",
-        "s_generate": t_gen, "warps_per_target": best, "autotune_ms_wpt2_4_8": tune,
+        "s_generate": t_gen, "warps_per_target": best, "autotune_ms_wpt2_3_4_8": tune,
         "ms_per_step": ms_step, "ms_evaluate": ms_eval,
         "ray_evals_per_s": n * npix / (ms_step * 1e-3), "ray_evals_per_s_evaluate": n * npix / (ms_eval * 1e-3),
         "roofline": {"bound": "hbm", "achieved": alg / (ms_eval * 1e-3) / 1e9, "peak": peak, "peak_kind": kind,
@@ -809,6 +809,7 @@ def run_profile(args):
     rho = torch.as_tensor(w.rho, device=dev)
     td = torch.as_tensor(w.td, device=dev)
     ctx.build(w.box_cm, rho, td, n=w.uniform_n, blocks=w.blocks, star_pos=w.star_pos, star_lum=w.star_lum)
+    ctx.set_warps_per_target(args.profile_wpt)  # the team size the bench's autotuner picks
     m = min(args.profile_targets, w.n_leaves)
     tg = torch.as_tensor(np.sort(synth.sample_targets(w.n_leaves, m, seed=5)).astype(np.int32),
                          device=dev)
@@ -818,6 +819,7 @@ def run_profile(args):
         ctx.evaluate(J, F, targets=tg)
     ctx.check()
     print(json.dumps({"profile": "evaluate", "workload": f"{args.profile_workload}_npix{args.npix}", "targets": m,
+                      "warps_per_target": args.profile_wpt,
                       "J_mean": float(J.double().mean())}))
     ctx.close()
 
@@ -873,6 +875,8 @@ def main():
                     help="ncu driver: evaluate kernel only, on --profile-targets cells")
     ap.add_argument("--profile-targets", type=int, default=262144)
     ap.add_argument("--profile-workload", default="turb128", choices=["turb128", "amr_core"])
+    ap.add_argument("--profile-wpt", type=int, default=3, choices=[2, 3, 4, 8],
+                    help="warps per target of the profiled launches (thick trees run 3 as 4)")
     ap.add_argument("--batch64", action="store_true", help="64-box AMR batch: batched vs per-box launches")
     ap.add_argument("--sweep", action="store_true", help="N_pix x segments sweep with the autotuner")
     ap.add_argument("--warmstart", action="store_true", help="learned warm start of the T_d fixed point")

@@ -252,16 +252,18 @@ treeray_status treeray_fixed_point(treeray_t ctx, const float* Tgas, const float
 
 /*
  * Warps per target for the evaluate kernel, chosen by timing (autotuner): the evaluate
- * kernel runs a team of 2, 4 or 8 warps per target sharing one walk stack and one ray
- * tile; each choice is launched twice on n_sample targets of the current tree (a fixed
- * stride permutation of the leaves) and the second launch is timed. The fastest choice is
- * kept by the context. best_wpt (host int) and ms (host float[3], times for 2, 4, 8)
- * may be NULL. Synchronous.
+ * kernel runs a team of 2, 3, 4 or 8 warps per target sharing one walk stack and one ray
+ * tile (3 only for trees without thick material); each choice is launched twice on
+ * n_sample targets of the current tree (a fixed stride permutation of the leaves) and the
+ * second launch is timed. The fastest choice is kept by the context. best_wpt (host int)
+ * and ms (host float[4], times for 2, 3, 4, 8; -1 for a choice not tried) may be NULL.
+ * Synchronous.
  */
 treeray_status treeray_autotune(treeray_t ctx, int64_t n_sample, int* best_wpt, float* ms,
                                 treeray_stream_t stream);
 
-/* Set the evaluate kernel's warps per target (2, 4 or 8) by hand; 4 is the default. */
+/* Set the evaluate kernel's warps per target (2, 3, 4 or 8) by hand; 4 is the default.
+ * Trees with thick material run teams of 3 as teams of 4. */
 treeray_status treeray_set_warps_per_target(treeray_t ctx, int wpt);
 
 /*

@@ -275,9 +275,10 @@ class Context:
 
     # -- C: treeray_autotune
     def autotune(self, n_sample: int = 65536, stream=None):
-        """Time 2, 4 and 8 warps per target; keeps the fastest. Returns (best, [ms2, ms4, ms8])."""
+        """Time 2, 3, 4 and 8 warps per target (3: trees without thick material); keeps the
+        fastest. Returns (best, [ms2, ms3, ms4, ms8]), -1 for a choice not tried."""
         best = C.c_int(0)
-        ms = (C.c_float * 3)()
+        ms = (C.c_float * 4)()
         _raise(lib().treeray_autotune(self.h, int(n_sample), C.byref(best), ms, _stream(stream)))
         return best.value, list(ms)
 

@@ -1075,6 +1075,9 @@ treeray_status launch_wpt(treeray_ctx* c, int wpt, const EvalArgs& a, const Eval
     if (boxes) return launch_team<NPIX, THICK, 4, GENERAL, true>(c, a, boxes, box_start, nbox, layout_lmax, s);
     switch (wpt) {
         case 2: return launch_team<NPIX, THICK, 2, GENERAL, false>(c, a, nullptr, nullptr, 0, layout_lmax, s);
+        case 3:  // thin tiles only; thick teams of three were slower than four
+            if constexpr (!THICK) return launch_team<NPIX, THICK, 3, GENERAL, false>(c, a, nullptr, nullptr, 0, layout_lmax, s);
+            return launch_team<NPIX, THICK, 4, GENERAL, false>(c, a, nullptr, nullptr, 0, layout_lmax, s);
         case 8: return launch_team<NPIX, THICK, 8, GENERAL, false>(c, a, nullptr, nullptr, 0, layout_lmax, s);
         default: return launch_team<NPIX, THICK, 4, GENERAL, false>(c, a, nullptr, nullptr, 0, layout_lmax, s);
     }
@@ -1162,7 +1165,7 @@ treeray_status reserve_eval_stacks(treeray_ctx* c, int lmax, cudaStream_t s) {
     TR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
     // at most 2048 threads, i.e. 64 / WPT teams, per SM
     size_t need = 0;
-    for (int wpt : {2, 4, 8}) need = std::max(need, stack_bytes_for(wpt, lmax, sms * (64 / wpt)));
+    for (int wpt : {2, 3, 4, 8}) need = std::max(need, stack_bytes_for(wpt, lmax, sms * (64 / wpt)));
     if (c->stack_scr_bytes >= need) return TREERAY_OK;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     TR_CUDA(cudaStreamIsCapturing(s, &cs));
@@ -1273,10 +1276,17 @@ treeray_status autotune(treeray_ctx* c, int64_t n_sample, int* best, float* ms, 
     TR_CUDA(cudaEventCreate(&e1));
     k_sample_targets<<<(int)((n + 255) / 256), 256, 0, s>>>(t, n, N, step);
     ++c->launches;
-    const int cand[3] = {2, 4, 8};
+    // teams of three warps exist for thin tiles only
+    const bool thick = c->has_thick || c->force_thick;
+    const int cand[4] = {2, 3, 4, 8};
     float bestt = 0.0f;
     int bw = c->wpt;
-    for (int k = 0; k < 3; ++k) {
+    bool first = true;
+    for (int k = 0; k < 4; ++k) {
+        if (thick && cand[k] == 3) {
+            if (ms) ms[k] = -1.0f;
+            continue;
+        }
         EvalArgs a = make_args(c, t, n);
         a.J = J;
         a.F = F;
@@ -1293,9 +1303,10 @@ treeray_status autotune(treeray_ctx* c, int64_t n_sample, int* best, float* ms, 
         float t_ms = 0.0f;
         TR_CUDA(cudaEventElapsedTime(&t_ms, e0, e1));
         if (ms) ms[k] = t_ms;
-        if (k == 0 || t_ms < bestt) {
+        if (first || t_ms < bestt) {
             bestt = t_ms;
             bw = cand[k];
+            first = false;
         }
     }
     c->wpt = bw;
@@ -1468,8 +1479,8 @@ treeray_status treeray_batch_evaluate(treeray_batch_t b, float* const* J, double
 }
 
 treeray_status treeray_set_warps_per_target(treeray_t c, int wpt) {
-    if (!c || (wpt != 2 && wpt != 4 && wpt != 8)) {
-        set_error("set_warps_per_target: wpt must be 2, 4 or 8");
+    if (!c || (wpt != 2 && wpt != 3 && wpt != 4 && wpt != 8)) {
+        set_error("set_warps_per_target: wpt must be 2, 3, 4 or 8");
         return TREERAY_EINVAL;
     }
     c->wpt = wpt;

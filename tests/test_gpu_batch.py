@@ -43,9 +43,9 @@ def test_batch_matches_single_and_oracle(orc, use_graph):
     b.close()
 
 
-@pytest.mark.parametrize("wpt", [2, 8])
-def test_team_sizes_match_oracle(orc, wpt):
-    w = synth.random_uniform(16, seed=13, thick_frac=0.1)
+@pytest.mark.parametrize("wpt,thick_frac", [(2, 0.1), (8, 0.1), (3, 0.0), (2, 0.0), (8, 0.0)])
+def test_team_sizes_match_oracle(orc, wpt, thick_frac):
+    w = synth.random_uniform(16, seed=13, thick_frac=thick_frac)
     ctx, _ = build_ctx(w)
     ctx.set_warps_per_target(wpt)
     J, F = evaluate(ctx)
@@ -58,8 +58,8 @@ def test_autotune_picks_a_team_size(orc):
     w = synth.turbulent_cloud(32)
     ctx, _ = build_ctx(w)
     best, ms = ctx.autotune(8192)
-    assert best in (2, 4, 8) and all(m > 0 for m in ms)
-    assert ms[(2, 4, 8).index(best)] == min(ms)
+    assert best in (2, 3, 4, 8) and all(m > 0 for m in ms)  # no thick material: all four tried
+    assert ms[(2, 3, 4, 8).index(best)] == min(ms)
     J, F = evaluate(ctx)
     tg = synth.sample_targets(w.n_leaves, 256, seed=3)
     Jr, _ = orc.Tree(w).evaluate(tg)
@@ -93,3 +93,14 @@ def test_batch_larger_than_one_launch(orc):
     b.close()
     for c in ctxs:
         c.close()
+
+
+def test_autotune_skips_three_warps_with_thick_material(orc):
+    w = synth.random_uniform(16, seed=14, thick_frac=0.2)
+    ctx, _ = build_ctx(w)
+    best, ms = ctx.autotune(4096)
+    assert ms[1] == -1.0 and best in (2, 4, 8)
+    ctx.set_warps_per_target(3)  # runs as four on a tree with thick material
+    J, F = evaluate(ctx)
+    Jr, Fr = orc.Tree(w).evaluate()
+    assert np.abs(J / Jr - 1).max() <= 1e-4 and flux_err(F, Fr, Jr).max() <= 1e-4
