@@ -306,9 +306,9 @@ __global__ void __launch_bounds__(256) k_walk_list(EvalArgs a) {
 }
 
 // entries per warp and walk step spread one per lane (more go through a serial fallback);
-// thick teams keep a few bytes less so that nine of them fit an SM at 48 rays and 20
-// segments
-__host__ __device__ constexpr int owner_cap(bool thick) { return thick ? 240 : 256; }
+// thick teams keep fewer so that nine of them fit an SM at 48 rays and 20 segments with
+// the static shared memory and the per-block reservation (measured: 8 teams at 192)
+__host__ __device__ constexpr int owner_cap(bool thick) { return thick ? 160 : 256; }
 
 // Row stride of the (segment x ray) tile in shared memory: a few words more than the rays,
 // so that the same ray in nearby segments (a common pair among the entries of one deposit
