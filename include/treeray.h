@@ -176,7 +176,8 @@ treeray_status treeray_build(treeray_t ctx, const treeray_grid* grid, const floa
  * radial kernel beta = R_i^2 / r^2, segment merge, ray integration and finalization
  * F = sum_h -F^h n^h, J = (1/4pi) sum_h F^h + J_src.
  *  targets   device int32[n] caller leaf indices, or NULL for every leaf (then
- *            n must equal the leaf count and row k of the outputs is leaf k).
+ *            n must equal the leaf count and row k of the outputs is leaf k). n = 0 is
+ *            an empty list: nothing is launched or written.
  *  J         device float[n], mean intensity (erg/s/cm^2/sr).
  *  F         device double[3n], flux vector xyz interleaved (erg/s/cm^2).
  */

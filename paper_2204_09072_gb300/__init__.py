@@ -220,8 +220,12 @@ class Context:
 
     # -- C: treeray_evaluate
     def evaluate(self, J, F, targets=None, stream=None):
+        """C: treeray_evaluate. targets None: every leaf (J has one row per leaf); else one
+        row per target (an empty targets tensor is an empty list)."""
         import torch
-        n = J.numel()
+        n = J.numel() if targets is None else targets.numel()
+        if J.numel() < n or F.numel() < 3 * n:
+            raise ValueError("J needs n and F 3 n elements")
         _raise(lib().treeray_evaluate(self.h, _dev(targets, torch.int32, "targets", True), n,
                                       _dev(J, torch.float32, "J"), _dev(F, torch.float64, "F"),
                                       _stream(stream)))

@@ -345,6 +345,7 @@ treeray_status treeray_evaluate(treeray_t c, const int32_t* targets, int64_t n, 
                                 treeray_stream_t stream) {
     treeray_status rc = check_ctx(c, true);
     if (rc != TREERAY_OK) return rc;
+    if (n == 0 && targets == nullptr && c->nleaves != 0) return TREERAY_OK;  // an empty target list
     if (!J || !F || n < 0 || (!targets && n != c->nleaves)) {
         set_error("evaluate: J and F required; n must equal the leaf count when targets is NULL");
         return TREERAY_EINVAL;
@@ -558,11 +559,11 @@ treeray_status treeray_accepted(treeray_t c, const int32_t* targets, int64_t n, 
                                 int32_t* counts, int32_t* ids, treeray_stream_t stream) {
     treeray_status rc = check_ctx(c, true);
     if (rc != TREERAY_OK) return rc;
+    if (n == 0 && cap >= 1) return TREERAY_OK;  // an empty target list
     if (!targets || !counts || !ids || n < 0 || cap < 1) {
         set_error("accepted: targets, counts, ids and cap >= 1 required");
         return TREERAY_EINVAL;
     }
-    if (n == 0) return TREERAY_OK;
     return launch_accepted(c, targets, n, cap, counts, ids, (cudaStream_t)stream);
 }
 
@@ -570,6 +571,7 @@ treeray_status treeray_walk_stats(treeray_t c, const int32_t* targets, int64_t n
                                   treeray_stream_t stream) {
     treeray_status rc = check_ctx(c, true);
     if (rc != TREERAY_OK) return rc;
+    if (n == 0 && targets == nullptr && c->nleaves != 0) return TREERAY_OK;  // an empty target list
     if (!totals || n < 0 || (!targets && n != c->nleaves)) {
         set_error("walk_stats: totals required; n must equal the leaf count when targets is NULL");
         return TREERAY_EINVAL;
