@@ -35,10 +35,20 @@
  *
  * Parity pins (see tests/test_oracle_*.py): HEALPix round trips and textbook
  * pixel centres; alpha normalisation and antipodal symmetry; the no-extinction
- * brute-force identity J = sum_k L_k / (16 pi^2 r_k^2); the point-source inverse
- * square law; the thin-sphere closed form; the single-segment limits of App. B;
- * hand-evaluated two-segment extinction; tree moments against direct sums;
- * dust temperature against T_J in the radiative limit.
+ * brute-force identity J = sum_k L_k / (16 pi^2 r_k^2), also over closest periodic
+ * copies; the point-source inverse square law and the paper's extinction fits; the
+ * thin-sphere and slab closed forms; zero net flux in an isotropic periodic box; the
+ * single-segment limits of App. B; hand-evaluated two-segment extinction; tree moments
+ * against direct sums; dust temperature against T_J in the radiative limit and its
+ * fixed point; the quarter-turn symmetry of turned HEALPix ray sets; the thick blob's
+ * far field (V^(2/3) scaling), plateau and ambient level (Sec. 5.2); the Stroemgren
+ * balance of the UV radiation pressure (App. C).
+ *
+ * Parity unpinned: the readings of the thick path where the paper leaves the choice
+ * open (the full A~ of every thick node touching a ray segment, which quantities a
+ * segment merge scales, the blend of thin and thick flux when neither weighs) are pinned
+ * only through their limits (deep-thick plateau, compact thick body, blob far field and
+ * plateau), not against an independent transfer solution.
  */
 #include <math.h>
 #include <stdint.h>
