@@ -580,7 +580,7 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
             // ---- map the accepted nodes onto the rays. Per node (one per thread): segment,
             // beta, angular-kernel key. The thin deposits of the warp's nodes are then
             // spread one angular-kernel entry per lane (a node's entries are distinct rays
-            // of one segment); thick deposits stay with the node's thread.
+            // of one segment), and the thick deposits after them in a second such pass.
             int ne = 0, ebase = 0, cbase = 0;
             float bL = 0.0f, bA = 0.0f;
             // thick deposits of this thread's node, spread over the warp after the thin ones:
