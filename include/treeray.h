@@ -218,7 +218,9 @@ treeray_status treeray_uv_radpressure(treeray_t ctx, const float* nph, const flo
  * Equilibrium dust temperature (Sec. 4.6, App. D) per leaf (caller order): the root of
  *  Gamma_dust-gas + heat_extra + rho kappa(T_d) (4 pi J - 4 sigma T_d^4) = 0,
  *  Gamma_dust-gas = 3.8e-33 sqrt(T) (T - T_d)(1 - 0.8 e^(-75/T)) n_H^2 (xi/0.01),
- *  n_H = 0.7 rho / m_H, floor 2.7 K; found by bracketing and 60 bisections in ln T.
+ *  n_H = 0.7 rho / m_H, floor 2.7 K. The result is the FP32 value of the root that
+ *  bracketing and 60 bisections in ln T give in FP64 (reached by FP32 bisection with
+ *  FP64 sign checks of G around the final float).
  *  Tgas device float[N]; heat_extra device float[N] (erg/s/cm^3) or NULL; J device
  *  float[N]; Td device float[N] output. rho (and kappa if given) from the build.
  */
