@@ -401,6 +401,11 @@ treeray_status treeray_walk_stats(treeray_t ctx, const int32_t* targets, int64_t
  *         larger grids return TREERAY_EINVAL.
  *  keys   device uint64[N] output, sorted keys (level << 3 lmax | Morton code).
  *  perm   device int32[N] output, caller leaf index of each sorted position.
+ *         The caller sizes both outputs to the leaf count N (n^3, or 512 per AMR
+ *         block); the library cannot check their length.
+ * An AMR grid's block table is copied from host memory on each call, which a stream
+ * capture cannot record: for AMR grids this call returns TREERAY_EINVAL while the
+ * stream is being captured (uniform grids need no host copy).
  * All scratch memory (6.2 MiB) is one fixed device array inside the library, held by
  * every GPU that loads the library until the process exits. The first call on a
  * device looks up that array's device address (cudaGetSymbolAddress), so make the

@@ -169,6 +169,11 @@ def morton_order_noalloc(box: float, keys, perm, n: int = 0, blocks=None, stream
         b = np.ascontiguousarray(blocks, dtype=np.int32).reshape(-1)
         g.n_blocks = b.size // 4
         g.blocks = b.ctypes.data_as(C.POINTER(C.c_int32))
+    # the kernels write one key and one index per leaf: refuse outputs shorter than that
+    n_leaves = int(n) ** 3 if int(n) > 0 else 512 * (0 if b is None else b.size // 4)
+    for t, name in ((keys, "keys"), (perm, "perm")):
+        if t is not None and t.numel() < n_leaves:
+            raise ValueError(f"{name} holds {t.numel()} entries, the grid has {n_leaves} leaves")
     _raise(lib().treeray_morton_order_noalloc(C.byref(g), _dev(keys, torch.int64, "keys"),
                                               _dev(perm, torch.int32, "perm"), _stream(stream)))
 

@@ -501,6 +501,10 @@ treeray_status build_tree(treeray_ctx* c, const treeray_grid* gr, const float* r
     int lmax = 0;
     int64_t N = 0;
     std::vector<int4> hblocks;
+    if (gr->n < 0) {
+        set_error("grid: n must be a power of two (uniform) or 0 (AMR blocks)");
+        return TREERAY_EINVAL;
+    }
     if (gr->n > 0) {
         if (gr->n_blocks != 0) {
             set_error("grid: give either n (uniform) or n_blocks (AMR), not both");

@@ -66,6 +66,8 @@ struct __align__(16) EvalArgs {
     int periodic;     // bit a: axis a periodic (closest copies)
     int col_mapping;  // map accepted nodes at their centre of luminosity
     float inv_s3;  // 1 / alpha_s^3: weight of one sub-cube sample of the angular kernel
+    float tau_scale;  // thin tiles of the isolated, centre-mapped kernels: 2^Q, the fixed-point
+                      // unit of the segment optical depth (0: float tiles)
     double u;
     double inv_u2;  // 1 / u^2: flux unit = L_scale / u^2 (L_scale a power of two)
 };
@@ -134,6 +136,19 @@ __device__ __forceinline__ int fixup_f(int g, float x2, const int64_t* __restric
 __device__ __forceinline__ int odd_key(float p, int elog) {
     return 2 * (int)floorf(p * ldexpf(1.0f, 2 - elog)) + 1;
 }
+// Thin tiles of the isolated, centre-mapped kernels keep each segment's optical depth as an
+// unsigned fixed-point number (unit 2^-Q): the deposits are then integer shared-memory atomics,
+// which cost a third of an FP32 one and barely slow down when lanes hit the same cell. Each
+// deposit is rounded to the nearest unit; Q is chosen on the host so that no segment's optical
+// depth can reach 2^32 units (tau_fixed_point_q in abi.cu).
+__device__ __forceinline__ unsigned tau_units(float y) {  // round y >= 0 to the nearest integer
+    return y < 8388608.0f ? __float_as_uint(y + 8388608.0f) - 0x4B000000u : __float2uint_rn(y);
+}
+template <bool THICK, bool GENERAL>
+struct FixedTau {
+    static constexpr bool on = !THICK && !GENERAL;
+};
+
 // Squared length in FP32, evaluated in a fixed order and never fused, as the oracle does.
 __device__ __forceinline__ float sq3_rn(float x, float y, float z) {
     return __fadd_rn(__fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y)), __fmul_rn(z, z));
@@ -444,6 +459,8 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
     // it stays in L1, and leaving it out of shared memory lets more teams share an SM.
     float* tL = reinterpret_cast<float*>(smem);
     float* tA = tL + cells;
+    unsigned* tT = reinterpret_cast<unsigned*>(tA);  // fixed-point tiles: segment optical depth
+    constexpr bool FIXT = FixedTau<THICK, GENERAL>::on;
     float* tLk = tA + cells;
     float* tAk = tLk + cells;
     float* tVk = tAk + cells;
@@ -621,7 +638,11 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
                     ebase = e0;
                     cbase = i * ROW;
                     bL = beta * v0.x * A.inv_s3;
-                    bA = beta * v0.y * A.inv_s3;
+                    // fixed-point tiles carry the optical depth per sample, A~ / (s^3 omega r^2) in
+                    // units of 2^-Q (beta / R_i^2 = 1 / r^2); segment 0 never extinguishes
+                    bA = FIXT ? (i == 0 ? 0.0f
+                                        : v0.y * A.inv_s3 * A.tau_scale / (omega * (rx * rx + ry * ry + rz * rz)))
+                              : beta * v0.y * A.inv_s3;
                     if (THICK && v1.w > 0.0f) {
                         const int64_t* lo = A.str_lo + ((int64_t)tl * (A.lmax + 1) + lvl) * nb;
                         const int64_t* hi = A.str_hi + ((int64_t)tl * (A.lmax + 1) + lvl) * nb;
@@ -679,13 +700,23 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
                             const int c = nd.x + (int)(ent & 0xffffu);
                             const float w = count_to_float(ent >> 16);
                             atomicAdd(tL + c, w * __int_as_float(nd.z));
-                            atomicAdd(tA + c, w * __int_as_float(nd.w));
+                            if constexpr (FIXT) {
+                                const unsigned v = tau_units(w * __int_as_float(nd.w));
+                                if (v) atomicAdd(tT + c, v);
+                            } else {
+                                atomicAdd(tA + c, w * __int_as_float(nd.w));
+                            }
                         }
                         if (r2 < tw) {
                             const int c2 = nd2.x + (int)(ent2 & 0xffffu);
                             const float w2 = count_to_float(ent2 >> 16);
                             atomicAdd(tL + c2, w2 * __int_as_float(nd2.z));
-                            atomicAdd(tA + c2, w2 * __int_as_float(nd2.w));
+                            if constexpr (FIXT) {
+                                const unsigned v = tau_units(w2 * __int_as_float(nd2.w));
+                                if (v) atomicAdd(tT + c2, v);
+                            } else {
+                                atomicAdd(tA + c2, w2 * __int_as_float(nd2.w));
+                            }
                         }
                     }
                     __syncwarp();
@@ -695,7 +726,12 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
                         const int c = cbase + (int)(ent & 0xffffu);
                         const float w = count_to_float(ent >> 16);
                         atomicAdd(tL + c, w * bL);
-                        atomicAdd(tA + c, w * bA);
+                        if constexpr (FIXT) {
+                            const unsigned v = tau_units(w * bA);
+                            if (v) atomicAdd(tT + c, v);
+                        } else {
+                            atomicAdd(tA + c, w * bA);
+                        }
                     }
                 }
             }
@@ -772,7 +808,7 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
             const float w = 1.0f / NPIX;
             for (int h = tid; h < NPIX; h += NT) {
                 tL[h] += w * v0.x;
-                tA[h] += w * v0.y;
+                if constexpr (!FIXT) tA[h] += w * v0.y;  // fixed-point tiles: segment 0 holds no depth
                 if (THICK && v1.w > 0.0f) {
                     tLk[h] += w * v1.y;
                     tAk[h] += v1.z;
@@ -793,12 +829,19 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
         auto segments = [&](int h, int i0, int i1, float& Fp, float& thi, float& tlo, float& ek) {
             for (int i = i0; i < i1; ++i) {
                 const int ci = i * ROW + h;
-                const float Lth = tL[ci], Ath = tA[ci];
-                const float Vk = THICK ? tVk[ci] : 0.0f;
-                if (Lth == 0.0f && Ath == 0.0f && Vk == 0.0f) continue;  // empty segment
+                const float Lth = tL[ci];
                 const float R2i = __ldg(R2 + i);
                 const float inv_R2 = 1.0f / R2i;
-                const float tth = i == 0 ? 0.0f : Ath * inv_R2 * (1.0f / omega);
+                float Ath, tth;
+                if constexpr (FIXT) {
+                    Ath = (float)tT[ci];
+                    tth = Ath * (1.0f / A.tau_scale);  // a power of two: exact scaling
+                } else {
+                    Ath = tA[ci];
+                    tth = i == 0 ? 0.0f : Ath * inv_R2 * (1.0f / omega);
+                }
+                const float Vk = THICK ? tVk[ci] : 0.0f;
+                if (Lth == 0.0f && Ath == 0.0f && Vk == 0.0f) continue;  // empty segment
                 float f = 0.0f, Fk = 0.0f, Akv = 0.0f, tk = 0.0f;
                 if constexpr (THICK) {
                     if (Vk > 0.0f) {
@@ -813,8 +856,12 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
                 }
                 const float g = tth < 1e-4f ? 1.0f : -expm1f(-tth) / tth;
                 const float Fth = g * Lth * inv_R2 * (float)(1.0 / (4.0 * kPi));
-                const float den = Ath + f * Akv;
-                const float Fs = den > 0.0f ? (Fth * Ath + Fk * f * Akv) / den : Fth + Fk;
+                // eq. fcombined; without thick material the blend is F*_thin itself
+                float Fs = Fth;
+                if constexpr (THICK) {
+                    const float den = Ath + f * Akv;
+                    Fs = den > 0.0f ? (Fth * Ath + Fk * f * Akv) / den : Fth + Fk;
+                }
                 // exp(-(thi + tlo)) with |tlo| far below one unit of thi
                 const float eps = expf(-thi) * (1.0f - tlo) * ek;
                 Fp += eps * Fs;
@@ -1108,9 +1155,15 @@ treeray_status dispatch_team(treeray_ctx* c, bool thick, bool periodic, int wpt,
     return TREERAY_EINVAL;
 }
 
+// The general kernels carry periodic closest copies, mapping at the COL and float thin tiles;
+// the others map isolated grids at the geometric centres with fixed-point thin tiles.
+bool needs_general(const treeray_ctx* c) {
+    const bool thick = c->has_thick || c->force_thick;
+    return c->p.periodic != 0 || c->p.col_mapping != 0 || (!thick && c->tau_q == 0);
+}
+
 treeray_status dispatch_eval(treeray_ctx* c, const EvalArgs& a, cudaStream_t s) {
-    return dispatch_team(c, c->has_thick || c->force_thick, c->p.periodic != 0 || c->p.col_mapping != 0, c->wpt, a,
-                         nullptr, nullptr, 1,
+    return dispatch_team(c, c->has_thick || c->force_thick, needs_general(c), c->wpt, a, nullptr, nullptr, 1,
                          c->lmax, s);
 }
 
@@ -1151,6 +1204,7 @@ EvalArgs make_args(treeray_ctx* c, const int32_t* targets, int64_t n) {
     a.periodic = c->p.periodic;
     a.col_mapping = c->p.col_mapping;
     a.inv_s3 = 1.0f / (float)(c->ht.s * c->ht.s * c->ht.s);
+    a.tau_scale = c->tau_q > 0 ? ldexpf(1.0f, c->tau_q) : 0.0f;
     a.u = c->u;
     a.inv_u2 = 1.0 / (c->u * c->u);
     // the stack holds at most 28 leftover groups per level plus one batch of pushes
@@ -1293,9 +1347,8 @@ treeray_status autotune(treeray_ctx* c, int64_t n_sample, int* best, float* ms, 
         treeray_status rc;
         for (int rep = 0; rep < 2; ++rep) {  // the second launch is timed
             if (rep == 1) TR_CUDA(cudaEventRecord(e0, s));
-            rc = dispatch_team(c, c->has_thick || c->force_thick, c->p.periodic != 0 || c->p.col_mapping != 0,
-                               cand[k], a, nullptr, nullptr,
-                               1, c->lmax, s);
+            rc = dispatch_team(c, c->has_thick || c->force_thick, needs_general(c), cand[k], a, nullptr, nullptr, 1,
+                               c->lmax, s);
             if (rc != TREERAY_OK) return rc;
         }
         TR_CUDA(cudaEventRecord(e1, s));
@@ -1326,7 +1379,7 @@ struct treeray_batch {
         std::vector<int64_t> start;
         unsigned long long* d_queue = nullptr;
         int max_lmax = 0;
-        bool periodic = false;  // some box has periodic axes or COL mapping (general kernel)
+        bool periodic = false;  // some box needs the general kernel (periodic, COL, float thin tiles)
     };
     std::vector<treeray_t> ctx;
     Group g[2];
@@ -1373,7 +1426,7 @@ treeray_status treeray_batch_create(const treeray_t* ctxs, int n_boxes, treeray_
         g.desc.push_back(a);
         g.start.push_back(g.start.back() + c->nleaves);
         g.max_lmax = std::max(g.max_lmax, c->lmax);
-        g.periodic = g.periodic || c->p.periodic != 0 || c->p.col_mapping != 0;
+        g.periodic = g.periodic || needs_general(c);
     }
     auto fail = [&](treeray_status rc) {
         treeray_batch_destroy(b);

@@ -136,6 +136,7 @@ struct treeray_ctx {
     bool orient_user = false;    // the map came from the caller (else leaf mod k)
     int64_t launches = 0;  // kernels launched by this context
     int wpt = 4;           // warps per target team of the evaluate kernel (autotuned)
+    int tau_q = 0;         // thin tiles: fixed-point optical depth in units of 2^-tau_q (0: float)
     // table cache key
     int tab_lmax = -1;
     bool tab_amr = false;

@@ -188,6 +188,10 @@ extern "C" treeray_status treeray_morton_order_noalloc(const treeray_grid* g, ui
     int lmax = 0;
     int64_t N = 0;
     int4 hb[kNaMaxAmrBlocks];
+    if (g->n < 0) {
+        set_error("morton_order_noalloc: n must be a power of two (uniform) or 0 (AMR blocks)");
+        return TREERAY_EINVAL;
+    }
     if (g->n > 0) {
         if (g->n_blocks != 0) {
             set_error("morton_order_noalloc: give either n (uniform) or n_blocks (AMR), not both");
@@ -238,6 +242,13 @@ extern "C" treeray_status treeray_morton_order_noalloc(const treeray_grid* g, ui
     uint32_t* hist = reinterpret_cast<uint32_t*>(scratch + kOffHist);
     int4* dblocks = reinterpret_cast<int4*>(scratch + kOffBlocks);
     if (g->n == 0) {
+        // a pageable host copy cannot be recorded into a stream capture
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        TR_CUDA(cudaStreamIsCapturing(st, &cs));
+        if (cs != cudaStreamCaptureStatusNone) {
+            set_error("morton_order_noalloc: AMR grids copy their block table from the host and cannot be captured");
+            return TREERAY_EINVAL;
+        }
         // the host table is staged through pageable memory: the copy has completed
         // (from the host's point of view) when cudaMemcpyAsync returns
         TR_CUDA(cudaMemcpyAsync(dblocks, hb, sizeof(int4) * g->n_blocks, cudaMemcpyHostToDevice, st));

@@ -113,6 +113,21 @@ def test_evaluate_clump32_all_targets(orc):
     assert ej.max() <= J_TOL and ef.max() <= F_TOL
 
 
+def test_evaluate_dense_thin_32(orc):
+    """Thin tiles of the isolated kernels keep each segment's optical depth in fixed point
+    (2^-20 per unit at this depth): every cell as close to the thick class as it gets
+    (tau_b in [0.5, 0.99]) gives the deepest segments a thin grid can have; every target
+    against the oracle."""
+    w = synth.random_uniform(32, seed=12, thick_frac=0.0, n_stars=3)
+    rng = np.random.Generator(np.random.PCG64(13))
+    dx = w.box_cm / 32
+    w.rho = (rng.uniform(0.5, 0.99, w.n_leaves) / dx).astype(np.float32)
+    ej, ef = _parity(orc, w)
+    print(f"dense thin 32^3: J max {ej.max():.2e} p99 {np.percentile(ej, 99):.2e}; "
+          f"F max {ef.max():.2e}")
+    assert ej.max() <= J_TOL and ef.max() <= F_TOL
+
+
 @pytest.mark.parametrize("npix", [12, 48, 192])
 def test_evaluate_ragged_subset_npix(orc, npix):
     w = synth.random_uniform(16, seed=9, thick_frac=0.1, npix=npix, nbins=16)

@@ -76,3 +76,32 @@ def test_turned_alpha_table_matches_oracle(trlib, orc):
                 b = orc.alpha_counts(npix, K, 8, rot=R)
                 assert (a == b).all(), (npix, K)
                 assert a.sum() == 512
+
+
+def test_noalloc_rejects_negative_n_before_any_launch(trlib):
+    """A negative n is neither a uniform grid nor an AMR grid: the call returns EINVAL
+    during argument checking, before any CUDA call (so this runs without a GPU)."""
+    import ctypes as C
+    g = trlib.Grid()
+    g.n = -1
+    g.n_blocks = 1
+    blocks = (C.c_int32 * 4)(0, 0, 0, 3)
+    g.blocks = C.cast(blocks, C.POINTER(C.c_int32))
+    g.box = 1.0
+    # never dereferenced: the grid is rejected first
+    rc = trlib.lib().treeray_morton_order_noalloc(C.byref(g), C.c_void_p(256), C.c_void_p(512), None)
+    assert rc == 1
+    assert b"n must be" in trlib.lib().treeray_last_error()
+
+
+def test_noalloc_wrapper_checks_output_length(trlib):
+    """The binding refuses key/permutation outputs shorter than the leaf count (the kernels
+    write one entry per leaf), for uniform and AMR grids, before calling the library."""
+    import torch
+    short = torch.empty(7, dtype=torch.int64)
+    ok = torch.empty(8, dtype=torch.int32)
+    with pytest.raises(ValueError, match="keys holds 7"):
+        trlib.morton_order_noalloc(1.0, short, ok, n=2)
+    blocks = np.array([[0, 0, 0, 3], [0, 0, 0, 3]], np.int32)
+    with pytest.raises(ValueError, match="perm holds 8"):
+        trlib.morton_order_noalloc(1.0, torch.empty(1024, dtype=torch.int64), ok, blocks=blocks)

@@ -57,11 +57,59 @@ def test_noalloc_order_matches_build_twice():
 
 
 def test_noalloc_rejects_too_many_leaves():
+    """Through the C ABI directly (the binding would refuse the short outputs first): a grid
+    beyond the fixed scratch size returns EINVAL before anything is written."""
+    import ctypes as C
+
     import torch
 
     import paper_2204_09072_gb300 as tr
     keys = torch.empty(1, dtype=torch.int64, device="cuda:0")
     perm = torch.empty(1, dtype=torch.int32, device="cuda:0")
-    with pytest.raises(tr.TreeRayError) as e:
-        tr.morton_order_noalloc(1.0, keys, perm, n=128)   # 2097152 leaves > 524288
-    assert e.value.code == 1 and "524288" in str(e.value)
+    g = tr.Grid()
+    g.n = 128   # 2097152 leaves > 524288
+    g.box = 1.0
+    rc = tr.lib().treeray_morton_order_noalloc(C.byref(g), C.c_void_p(keys.data_ptr()),
+                                               C.c_void_p(perm.data_ptr()), None)
+    assert rc == 1 and b"524288" in tr.lib().treeray_last_error()
+    with pytest.raises(ValueError, match="2097152 leaves"):
+        tr.morton_order_noalloc(1.0, keys, perm, n=128)
+
+
+def test_noalloc_uniform_grid_under_capture_and_amr_refused():
+    """A uniform grid needs no host copy, so its ordering can be recorded into a CUDA graph
+    and replayed; an AMR grid copies its block table from the host on each call, which a
+    capture cannot hold, and is refused with EINVAL while the stream is capturing."""
+    import torch
+
+    import paper_2204_09072_gb300 as tr
+    w = synth.random_uniform(16, seed=6)
+    ref = _build_order(w)
+    _noalloc(w)  # the first call on the device (address look-up) precedes the capture
+    n = w.n_leaves
+    keys = torch.full((n,), -1, dtype=torch.int64, device="cuda:0")
+    perm = torch.full((n,), -1, dtype=torch.int32, device="cuda:0")
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g, stream=s):
+        tr.morton_order_noalloc(w.box_cm, keys, perm, n=w.uniform_n, stream=s)
+    perm.fill_(-1)
+    g.replay()
+    torch.cuda.synchronize()
+    assert (perm.cpu().numpy() == ref).all()
+
+    a = synth.amr_core(n_base_blocks=2, max_level=2, target_leaves=40 * 512, n_stars=1)
+    ka = torch.empty(a.n_leaves, dtype=torch.int64, device="cuda:0")
+    pa = torch.empty(a.n_leaves, dtype=torch.int32, device="cuda:0")
+    g2 = torch.cuda.CUDAGraph()
+    err = None
+    with torch.cuda.stream(s):
+        g2.capture_begin()
+        try:
+            tr.morton_order_noalloc(a.box_cm, ka, pa, blocks=a.blocks, stream=s)
+        except tr.TreeRayError as e:
+            err = e
+        finally:
+            g2.capture_end()
+    assert err is not None and err.code == 1 and "captured" in str(err)
