@@ -772,31 +772,24 @@ static void or_map_node(const or_tree* t, or_alpha_table* at, const or_node* nd,
     int nb = ry->nbins, np = ry->npix;
     double u = t->u;
     int own = (d2 == 0);
-    /* mapping at the centre of luminosity (Sec. 7.6: "we shift the nodes towards their
-     * center of emission during mapping to rays"), for nodes whose COL is off centre.
-     * Reading: the position p = o + c, c the COL offset rounded to FP32 (as a GPU node
-     * record holds it), is formed and squared in FP32; the segment and the straddled
-     * boundaries compare p^2 with the integer thresholds ceil(R_j^2), ceil((R_j +- s)^2)
-     * taken as FP32; the angular key is the odd grid point 2 floor(4 p / E) + 1 per axis.
-     * Every decision is then the same FP32 arithmetic on both implementations. */
-    float pf[3] = {0.0f, 0.0f, 0.0f}, pd2 = 0.0f;
+    /* mapping at the centre of luminosity (Sec. 7.6: the nodes are shifted towards their
+     * centre of emission when they are mapped to rays), for nodes whose COL is off centre.
+     * Reading: every mapping decision is taken at the COL position p = o + (COL - centre)
+     * instead of the centre, in FP64: the segment is the largest j with |p|^2 >= R_j^2, the
+     * straddled boundaries compare |p|^2 with (R_j +- s)^2, and the angular key is the odd
+     * grid point 2 floor(4 p / E) + 1 per axis (p is no grid point, so K = 8 o / E cannot
+     * be integral); |p|^2 = (p_x^2 + p_y^2) + p_z^2. The opening test stays at the centre. */
+    double pc[3] = {0.0, 0.0, 0.0}, pd2 = 0.0;
     int colmap = 0;
     if (t->p.col_mapping && !own) {
         for (int a = 0; a < 3; ++a) {
-            float c32 = (float)(nd->col[a] - (double)nd->c[a]);
-            if (c32 != 0.0f) colmap = 1;
-            pf[a] = (float)o[a] + c32;
+            double c = nd->col[a] - (double)nd->c[a];
+            if (c != 0.0) colmap = 1;
+            pc[a] = (double)o[a] + c;
         }
-        pd2 = (pf[0] * pf[0] + pf[1] * pf[1]) + pf[2] * pf[2];
+        pd2 = (pc[0] * pc[0] + pc[1] * pc[1]) + pc[2] * pc[2];
     }
-    int i;
-    if (colmap) {
-        i = 0;
-        for (int j = 1; j < nb; ++j)
-            if (pd2 >= (float)ceil(R[j] * R[j])) i = j;
-    } else {
-        i = or_bin(nb, R, (double)d2);
-    }
+    int i = or_bin(nb, R, colmap ? pd2 : (double)d2);
     double beta = 1.0;
     if (!own) {
         double r2 = 0.0;
@@ -811,7 +804,7 @@ static void or_map_node(const or_tree* t, or_alpha_table* at, const or_node* nd,
     int owned = 0;
     if (!own) {
         if (colmap) {
-            for (int a = 0; a < 3; ++a) K[a] = 2 * (int64_t)floorf(4.0f * pf[a] / (float)nd->E) + 1;
+            for (int a = 0; a < 3; ++a) K[a] = 2 * (int64_t)floor(4.0 * pc[a] / (double)nd->E) + 1;
         } else {
             or_key(o, nd->E, K);
         }
@@ -823,13 +816,9 @@ static void or_map_node(const or_tree* t, or_alpha_table* at, const or_node* nd,
         for (int j = 1; j < nb; ++j) {
             double up = R[j] + s;
             double dn = R[j] - s;
-            if (colmap) {
-                if (pd2 >= (float)ceil(up * up)) ilo = j;
-                if (dn <= 0.0 || pd2 >= (float)ceil(dn * dn)) ihi = j;
-            } else {
-                if ((double)d2 >= up * up) ilo = j;
-                if (dn <= 0.0 || (double)d2 >= dn * dn) ihi = j;
-            }
+            double x2 = colmap ? pd2 : (double)d2;
+            if (x2 >= up * up) ilo = j;
+            if (dn <= 0.0 || x2 >= dn * dn) ihi = j;
         }
     }
     /* values in CGS: luminosities erg/s, areas cm^2, volumes cm^3; w < 1 for one of
@@ -1283,18 +1272,18 @@ int64_t or_accepted(const or_tree* t, int64_t leaf, int32_t* ids, int64_t cap) {
 
 /* Angular key of an accepted node at offset o: at its geometric centre (or_key), or with
  * COL mapping, for a node whose COL is off centre, the odd grid point of its COL position
- * in FP32 (as in or_map_node). */
+ * in FP64 (as in or_map_node). */
 static void or_node_key(const or_tree* t, const or_node* nd, const int64_t* o, int64_t* K) {
     if (t->p.col_mapping) {
-        float pf[3];
+        double pc[3];
         int shifted = 0;
         for (int a = 0; a < 3; ++a) {
-            float c32 = (float)(nd->col[a] - (double)nd->c[a]);
-            if (c32 != 0.0f) shifted = 1;
-            pf[a] = (float)o[a] + c32;
+            double c = nd->col[a] - (double)nd->c[a];
+            if (c != 0.0) shifted = 1;
+            pc[a] = (double)o[a] + c;
         }
         if (shifted) {
-            for (int a = 0; a < 3; ++a) K[a] = 2 * (int64_t)floorf(4.0f * pf[a] / (float)nd->E) + 1;
+            for (int a = 0; a < 3; ++a) K[a] = 2 * (int64_t)floor(4.0 * pc[a] / (double)nd->E) + 1;
             return;
         }
     }

@@ -18,7 +18,7 @@ static thread_local std::string g_err;
 void set_error(const std::string& msg) { g_err = msg; }
 
 void free_tables(DeviceTables& t) {
-    void* ptrs[] = {t.nhat, t.alpha_off, t.alpha_ent, t.bin_thr, t.R2,   t.Rh, t.lvlp,
+    void* ptrs[] = {t.nhat, t.alpha_off, t.alpha_ent, t.bin_thr, t.R2,   t.Rh, t.Rd, t.lvlp,
                     t.open_max, t.str_lo, t.str_hi, t.scal, t.err, t.queue};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -135,6 +135,7 @@ treeray_status upload_tables(treeray_ctx* c, cudaStream_t s) {
     c->tau_q = tau_fixed_point_q(c);
     std::vector<int64_t> thr((size_t)(L + 1) * nb), omax(L + 1);
     std::vector<float> R2((size_t)(L + 1) * nb), Rh((size_t)(L + 1) * nb);
+    std::vector<double> Rd((size_t)(L + 1) * nb);
     std::vector<float2> lvlp(L + 1);
     std::vector<int64_t> slo((size_t)(L + 1) * (L + 1) * nb), shi(slo.size());
     std::vector<double> R(nb + 1);
@@ -167,6 +168,7 @@ treeray_status upload_tables(treeray_ctx* c, cudaStream_t s) {
             thr[(size_t)lt * nb + i] = (int64_t)std::ceil(R[i] * R[i]);
             R2[(size_t)lt * nb + i] = (float)(R[i] * R[i]);
             Rh[(size_t)lt * nb + i] = (float)R[i];
+            Rd[(size_t)lt * nb + i] = R[i];
         }
         for (int ln = 0; ln <= L; ++ln) {
             const int64_t E = (int64_t)2 << (L - ln);
@@ -184,6 +186,7 @@ treeray_status upload_tables(treeray_ctx* c, cudaStream_t s) {
     if ((rc = upload(&c->dt.bin_thr, thr, s)) != TREERAY_OK) return rc;
     if ((rc = upload(&c->dt.R2, R2, s)) != TREERAY_OK) return rc;
     if ((rc = upload(&c->dt.Rh, Rh, s)) != TREERAY_OK) return rc;
+    if ((rc = upload(&c->dt.Rd, Rd, s)) != TREERAY_OK) return rc;
     if ((rc = upload(&c->dt.open_max, omax, s)) != TREERAY_OK) return rc;
     if ((rc = upload(&c->dt.lvlp, lvlp, s)) != TREERAY_OK) return rc;
     if ((rc = upload(&c->dt.str_lo, slo, s)) != TREERAY_OK) return rc;

@@ -43,6 +43,10 @@ struct __align__(16) EvalArgs {
     int64_t aoff_stride;
     const int64_t* __restrict__ bin_thr;
     const float* __restrict__ R2;
+    const float* __restrict__ Rh;       // [target level][nbins] R_i (half-cells)
+    const double* __restrict__ Rd;      // [target level][nbins] R_i in FP64 (COL decisions)
+    const double* __restrict__ mom;     // FP64 node moments [11][nn] (COL in rows 8..10)
+    int64_t nn;
     const int64_t* __restrict__ open_max;
     const int64_t* __restrict__ str_lo;
     const int64_t* __restrict__ str_hi;
@@ -123,18 +127,12 @@ __device__ __forceinline__ float count_to_float(uint32_t v) {  // exact for v < 
     return __uint_as_float(0x4B000000u | v) - 8388608.0f;
 }
 
-// Segment of a real squared distance x2 against the integer thresholds taken as FP32:
-// the largest j in [1, nb-1] with x2 >= (float)arr[j], else 0 (mapping at the COL).
-__device__ __forceinline__ int fixup_f(int g, float x2, const int64_t* __restrict__ arr, int nb) {
+// Largest j in [1, nb-1] with x2 >= R2[j] (R2 = R_j^2 in FP32), else 0.
+__device__ __forceinline__ int fixup_r2(int g, float x2, const float* __restrict__ R2, int nb) {
     g = max(0, min(g, nb - 1));
-    while (g + 1 < nb && x2 >= (float)__ldg(arr + g + 1)) ++g;
-    while (g > 0 && x2 < (float)__ldg(arr + g)) --g;
+    while (g + 1 < nb && x2 >= __ldg(R2 + g + 1)) ++g;
+    while (g > 0 && x2 < __ldg(R2 + g)) --g;
     return g;
-}
-// Angular key of a real offset p (half-cells) of a node of edge 2^elog: the odd grid point
-// 2 floor(4 p / E) + 1 (the scaling by a power of two is exact).
-__device__ __forceinline__ int odd_key(float p, int elog) {
-    return 2 * (int)floorf(p * ldexpf(1.0f, 2 - elog)) + 1;
 }
 // Thin tiles of the isolated, centre-mapped kernels keep each segment's optical depth as an
 // unsigned fixed-point number (unit 2^-Q): the deposits are then integer shared-memory atomics,
@@ -152,6 +150,92 @@ struct FixedTau {
 // Squared length in FP32, evaluated in a fixed order and never fused, as the oracle does.
 __device__ __forceinline__ float sq3_rn(float x, float y, float z) {
     return __fadd_rn(__fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y)), __fmul_rn(z, z));
+}
+
+// Mapping decisions of a node taken at its centre of luminosity (Sec. 7.6): segment i,
+// angular key K and, for thick material, the straddled segment boundaries [ilo, ihi).
+// They are defined on the COL position p = q + (COL - centre) in FP64: i is the largest j
+// with |p|^2 >= R_j^2, |p|^2 = (p_x^2 + p_y^2) + p_z^2; K = 2 floor(4 p / E) + 1 per axis;
+// a boundary j is straddled from below when |p|^2 >= (R_j + s)^2 and from above when
+// R_j <= s or |p|^2 >= (R_j - s)^2, s = sqrt(3)/2 E. The FP32 position (the node record's
+// COL offset) decides wherever it lies farther from every threshold than 2^-20 of the
+// compared magnitudes, which bounds its few FP32 roundings many times over; a node closer
+// to a threshold is decided from the FP64 COL of its moments, in FP64 as defined.
+struct ColMap {
+    int i, kx, ky, kz, ilo, ihi;
+};
+constexpr float kColTol = 9.5367431640625e-07f;  // 2^-20
+
+__device__ __noinline__ ColMap col_decide_fp64(const EvalArgs& A, int node, int qx, int qy, int qz, int lvl,
+                                               int tl, bool straddle) {
+    ColMap m{0, 0, 0, 0, 0, 0};
+    const int nb = A.nbins;
+    const double* Rd = A.Rd + (int64_t)tl * nb;
+    const int4 g = __ldg(A.geo + node);
+    const double px = __dadd_rn((double)qx, __dsub_rn(__ldg(A.mom + 8 * A.nn + node), (double)g.x));
+    const double py = __dadd_rn((double)qy, __dsub_rn(__ldg(A.mom + 9 * A.nn + node), (double)g.y));
+    const double pz = __dadd_rn((double)qz, __dsub_rn(__ldg(A.mom + 10 * A.nn + node), (double)(g.z & 0xffffff)));
+    const double pd2 = __dadd_rn(__dadd_rn(__dmul_rn(px, px), __dmul_rn(py, py)), __dmul_rn(pz, pz));
+    for (int j = 1; j < nb; ++j) {
+        const double R = __ldg(Rd + j);
+        if (pd2 >= __dmul_rn(R, R)) m.i = j;
+    }
+    const double E = (double)(2 << (A.lmax - lvl));
+    m.kx = 2 * (int)floor(__ddiv_rn(__dmul_rn(4.0, px), E)) + 1;
+    m.ky = 2 * (int)floor(__ddiv_rn(__dmul_rn(4.0, py), E)) + 1;
+    m.kz = 2 * (int)floor(__ddiv_rn(__dmul_rn(4.0, pz), E)) + 1;
+    if (straddle) {
+        const double sd = __dmul_rn(__dmul_rn(sqrt(3.0), 0.5), E);
+        for (int j = 1; j < nb; ++j) {
+            const double R = __ldg(Rd + j);
+            const double up = __dadd_rn(R, sd), dn = __dsub_rn(R, sd);
+            if (pd2 >= __dmul_rn(up, up)) m.ilo = j;
+            if (dn <= 0.0 || pd2 >= __dmul_rn(dn, dn)) m.ihi = j;
+        }
+    }
+    return m;
+}
+
+// The same decisions from the FP32 record (c: the COL offset held in the node record), with
+// the FP64 path where the FP32 position is too close to a threshold. (rx, ry, rz) = q + c in
+// FP32, as the radial kernel uses it.
+__device__ __forceinline__ ColMap col_decide(const EvalArgs& A, int node, int qx, int qy, int qz, float rx,
+                                             float ry, float rz, int lvl, int tl, float2 lp, bool straddle) {
+    ColMap m;
+    const int nb = A.nbins;
+    const float* R2 = A.R2 + (int64_t)tl * nb;
+    const float pd2 = sq3_rn(rx, ry, rz);
+    const float Ef = (float)(2 << (A.lmax - lvl));
+    const float tol = kColTol * (pd2 + Ef * Ef);
+    m.i = fixup_r2(guess_bin(pd2, lp), pd2, R2, nb);
+    bool unsure = (m.i > 0 && pd2 - __ldg(R2 + m.i) <= tol) || (m.i + 1 < nb && __ldg(R2 + m.i + 1) - pd2 <= tol);
+    const float sc = ldexpf(1.0f, 1 - (A.lmax - lvl));  // 4 / E
+    const float tx = rx * sc, ty = ry * sc, tz = rz * sc;
+    const float fx = floorf(tx), fy = floorf(ty), fz = floorf(tz);
+    unsure = unsure || tx - fx <= kColTol * (fabsf(tx) + 1.0f) || fx + 1.0f - tx <= kColTol * (fabsf(tx) + 1.0f) ||
+             ty - fy <= kColTol * (fabsf(ty) + 1.0f) || fy + 1.0f - ty <= kColTol * (fabsf(ty) + 1.0f) ||
+             tz - fz <= kColTol * (fabsf(tz) + 1.0f) || fz + 1.0f - tz <= kColTol * (fabsf(tz) + 1.0f);
+    m.kx = 2 * (int)fx + 1;
+    m.ky = 2 * (int)fy + 1;
+    m.kz = 2 * (int)fz + 1;
+    m.ilo = 0;
+    m.ihi = 0;
+    if (straddle) {
+        const float* Rh = A.Rh + (int64_t)tl * nb;
+        const float sd = 0.8660254f * Ef;
+        for (int j = 1; j < nb; ++j) {
+            const float R = __ldg(Rh + j);
+            const float up = R + sd, dn = R - sd;
+            const float u2 = up * up, d2f = dn * dn;
+            if (fabsf(pd2 - u2) <= kColTol * (pd2 + u2) || fabsf(dn) <= kColTol * up ||
+                (dn > 0.0f && fabsf(pd2 - d2f) <= kColTol * (pd2 + d2f)))
+                unsure = true;
+            if (pd2 >= u2) m.ilo = j;
+            if (dn <= 0.0f || pd2 >= d2f) m.ihi = j;
+        }
+    }
+    if (unsure) return col_decide_fp64(A, node, qx, qy, qz, lvl, tl, straddle);
+    return m;
 }
 
 // Closest periodic copy on one axis (Sec. 4.2): the offset o (half-cells) is brought into
@@ -288,13 +372,24 @@ __global__ void __launch_bounds__(256) k_walk_list(EvalArgs a) {
                     cz = __ldg(a.thick + node).x;
                 }
                 const bool colmap = cx != 0.0f || cy != 0.0f || cz != 0.0f;
+                const int tl = tg.z >> 24;
                 for (int m = 0; m < 8; ++m) {  // entries of every closest copy
                     if (m & ~ties) continue;
                     const int qx = copy_offset(ox, ties, 1, m, half), qy = copy_offset(oy, ties, 2, m, half),
                               qz = copy_offset(oz, ties, 4, m, half);
-                    const int Kx = colmap ? odd_key(small_int_to_float(qx) + cx, elog) : alpha_key(qx, elog);
-                    const int Ky = colmap ? odd_key(small_int_to_float(qy) + cy, elog) : alpha_key(qy, elog);
-                    const int Kz = colmap ? odd_key(small_int_to_float(qz) + cz, elog) : alpha_key(qz, elog);
+                    int Kx, Ky, Kz;
+                    if (colmap) {
+                        const ColMap cm = col_decide(a, node, qx, qy, qz, small_int_to_float(qx) + cx,
+                                                     small_int_to_float(qy) + cy, small_int_to_float(qz) + cz, lvl,
+                                                     tl, __ldg(a.lvlp + tl), false);
+                        Kx = cm.kx;
+                        Ky = cm.ky;
+                        Kz = cm.kz;
+                    } else {
+                        Kx = alpha_key(qx, elog);
+                        Ky = alpha_key(qy, elog);
+                        Kz = alpha_key(qz, elog);
+                    }
                     if (abs(Kx) <= a.D && abs(Ky) <= a.D && abs(Kz) <= a.D) {
                         const int idx = ((Kz + a.D) * W + (Ky + a.D)) * W + (Kx + a.D);
                         nent += __ldg(aoff + idx + 1) - __ldg(aoff + idx);
@@ -384,22 +479,19 @@ __device__ __noinline__ void deposit_tied_copies(const EvalArgs& A, const int32_
                     rz = small_int_to_float(qz) + v1.x;
         int i = i0;
         unsigned long long fmask = fmask0;
+        int Kx = alpha_key(qx, elog), Ky = alpha_key(qy, elog), Kz = alpha_key(qz, elog);
         if (colmap) {
-            const float pd2 = sq3_rn(rx, ry, rz);
-            i = fixup_f(guess_bin(pd2, lp), pd2, thr, nb);
+            const ColMap cm = col_decide(A, node, qx, qy, qz, rx, ry, rz, lvl, tl, lp, thick);
+            i = cm.i;
+            Kx = cm.kx;
+            Ky = cm.ky;
+            Kz = cm.kz;
             if (thick) {
-                const float d = sqrtf(pd2);
-                const float dl = fmaxf(d - sd, 0.0f), dh = d + sd;
-                const int ilo = fixup_f(guess_bin(dl * dl, lp), pd2, lo, nb);
-                const int ihi = fixup_f(guess_bin(dh * dh, lp), pd2, hi, nb);
                 fmask = 0ull;
-                for (int j = ilo; j < ihi; ++j) fmask |= 1ull << j;
+                for (int j = cm.ilo; j < cm.ihi; ++j) fmask |= 1ull << j;
             }
         }
         const float beta = __ldg(R2 + i) / (rx * rx + ry * ry + rz * rz);
-        const int Kx = colmap ? odd_key(rx, elog) : alpha_key(qx, elog);
-        const int Ky = colmap ? odd_key(ry, elog) : alpha_key(qy, elog);
-        const int Kz = colmap ? odd_key(rz, elog) : alpha_key(qz, elog);
         if (abs(Kx) > A.D || abs(Ky) > A.D || abs(Kz) > A.D) {
             atomicOr(A.err, kErrAlphaKey);
             continue;
@@ -616,15 +708,25 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
                 const float4 v1 = __ldg(A.thick + node);
                 const float rx = fx + v0.z, ry = fy + v0.w, rz = fz + v1.x;
                 // mapping at the centre of luminosity (Sec. 7.6): segment, straddles and key
-                // from the COL position in FP32 for nodes whose COL is off centre
+                // at the COL position for nodes whose COL is off centre (col_decide)
                 const bool colmap = GENERAL && A.col_mapping && (v0.z != 0.0f || v0.w != 0.0f || v1.x != 0.0f);
-                const float pd2 = colmap ? sq3_rn(rx, ry, rz) : 0.0f;
-                const int i = colmap ? fixup_f(guess_bin(pd2, lp), pd2, thr, nb) : fixup(guess_bin(fd2, lp), d2, thr, nb);
-                const float beta = __ldg(R2 + i) / (rx * rx + ry * ry + rz * rz);
                 const int elog = A.lmax - lvl + 1;
-                const int Kx = colmap ? odd_key(rx, elog) : alpha_key(ox, elog);
-                const int Ky = colmap ? odd_key(ry, elog) : alpha_key(oy, elog);
-                const int Kz = colmap ? odd_key(rz, elog) : alpha_key(oz, elog);
+                int i, Kx, Ky, Kz, cilo = 0, cihi = 0;
+                if (colmap) {
+                    const ColMap cm = col_decide(A, node, ox, oy, oz, rx, ry, rz, lvl, tl, lp, THICK && v1.w > 0.0f);
+                    i = cm.i;
+                    Kx = cm.kx;
+                    Ky = cm.ky;
+                    Kz = cm.kz;
+                    cilo = cm.ilo;
+                    cihi = cm.ihi;
+                } else {
+                    i = fixup(guess_bin(fd2, lp), d2, thr, nb);
+                    Kx = alpha_key(ox, elog);
+                    Ky = alpha_key(oy, elog);
+                    Kz = alpha_key(oz, elog);
+                }
+                const float beta = __ldg(R2 + i) / (rx * rx + ry * ry + rz * rz);
                 if (abs(Kx) > A.D || abs(Ky) > A.D || abs(Kz) > A.D) {
                     atomicOr(A.err, kErrAlphaKey);
                 } else {
@@ -644,15 +746,16 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
                                         : v0.y * A.inv_s3 * A.tau_scale / (omega * (rx * rx + ry * ry + rz * rz)))
                               : beta * v0.y * A.inv_s3;
                     if (THICK && v1.w > 0.0f) {
-                        const int64_t* lo = A.str_lo + ((int64_t)tl * (A.lmax + 1) + lvl) * nb;
-                        const int64_t* hi = A.str_hi + ((int64_t)tl * (A.lmax + 1) + lvl) * nb;
-                        const float d = sqrtf(colmap ? pd2 : fd2);
-                        const float sd = 0.8660254f * (float)(2 << (A.lmax - lvl));
-                        const float dl = fmaxf(d - sd, 0.0f), dh = d + sd;
-                        const int ilo = colmap ? fixup_f(guess_bin(dl * dl, lp), pd2, lo, nb)
-                                               : fixup(guess_bin(dl * dl, lp), d2, lo, nb);
-                        const int ihi = colmap ? fixup_f(guess_bin(dh * dh, lp), pd2, hi, nb)
-                                               : fixup(guess_bin(dh * dh, lp), d2, hi, nb);
+                        int ilo = cilo, ihi = cihi;
+                        if (!colmap) {
+                            const int64_t* lo = A.str_lo + ((int64_t)tl * (A.lmax + 1) + lvl) * nb;
+                            const int64_t* hi = A.str_hi + ((int64_t)tl * (A.lmax + 1) + lvl) * nb;
+                            const float d = sqrtf(fd2);
+                            const float sd = 0.8660254f * (float)(2 << (A.lmax - lvl));
+                            const float dl = fmaxf(d - sd, 0.0f), dh = d + sd;
+                            ilo = fixup(guess_bin(dl * dl, lp), d2, lo, nb);
+                            ihi = fixup(guess_bin(dh * dh, lp), d2, hi, nb);
+                        }
                         unsigned long long fmask = 0ull;
                         for (int j = ilo; j < ihi; ++j) fmask |= 1ull << j;
                         nk = e1 - e0;
@@ -1188,6 +1291,10 @@ EvalArgs make_args(treeray_ctx* c, const int32_t* targets, int64_t n) {
     a.aoff_stride = (int64_t)(2 * c->ht.D + 1) * (2 * c->ht.D + 1) * (2 * c->ht.D + 1) + 1;
     a.bin_thr = c->dt.bin_thr;
     a.R2 = c->dt.R2;
+    a.Rh = c->dt.Rh;
+    a.Rd = c->dt.Rd;
+    a.mom = c->tree.mom;
+    a.nn = c->nnodes;
     a.open_max = c->dt.open_max;
     a.str_lo = c->dt.str_lo;
     a.str_hi = c->dt.str_hi;

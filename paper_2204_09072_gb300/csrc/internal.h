@@ -90,6 +90,7 @@ struct DeviceTables {
     int64_t* bin_thr = nullptr;     // [lmax+1][nbins] ceil(R_i^2), i>=1 used
     float* R2 = nullptr;            // [lmax+1][nbins] R_i^2 (half-cells^2)
     float* Rh = nullptr;            // [lmax+1][nbins] R_i (half-cells)
+    double* Rd = nullptr;           // [lmax+1][nbins] R_i in FP64 (decisions at the COL)
     float2* lvlp = nullptr;         // [lmax+1] 1 / R_0^2 and 0.5 / log2(g) (segment guess)
     int64_t* open_max = nullptr;    // [lmax+1] largest d^2 at which a node of that level opens
     int64_t* str_lo = nullptr;      // [lmax+1 target][lmax+1 node][nbins] straddle thresholds

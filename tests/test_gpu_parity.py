@@ -113,6 +113,24 @@ def test_evaluate_clump32_all_targets(orc):
     assert ej.max() <= J_TOL and ef.max() <= F_TOL
 
 
+@pytest.mark.parametrize("name", ["rand32_col", "amr_col"])
+def test_col_mapping_decisions_agree(orc, name):
+    """Mapping at the centre of luminosity (Sec. 7.6): the oracle takes every decision
+    (segment, angular key, straddled boundaries) on the COL position in FP64; the library
+    takes it in FP32 where that position is safely away from every threshold and in FP64
+    from the node's FP64 COL otherwise. A decision taken differently would move a node's
+    whole contribution to another segment or ray, far above FP32 rounding, so every target
+    must agree to 1e-5 (J) and 2e-5 (F) here, well inside the 1e-4 tolerance."""
+    if name == "rand32_col":
+        w = synth.random_uniform(32, seed=21, thick_frac=0.12, n_stars=3, col_mapping=1)
+    else:
+        w = synth.amr_core(n_base_blocks=2, max_level=3, target_leaves=60 * 512, n_stars=4, col_mapping=1)
+    ej, ef = _parity(orc, w)
+    print(f"{name}: {w.n_leaves} targets, J max {ej.max():.2e}, F max {ef.max():.2e}; "
+          f"targets above 1e-5: {(ej > 1e-5).sum()} (J), {(ef > 2e-5).sum()} (F)")
+    assert ej.max() <= 1e-5 and ef.max() <= 2e-5
+
+
 def test_evaluate_dense_thin_32(orc):
     """Thin tiles of the isolated kernels keep each segment's optical depth in fixed point
     (2^-20 per unit at this depth): every cell as close to the thick class as it gets
