@@ -126,15 +126,16 @@ def kernel_source_sha():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(workload_name: str):
-    """DRAM bytes per evaluate launch from the committed ncu summary, if it was taken on
-    the current kernel source; else None."""
+def ncu_traffic(workload_name: str, key: str = "bytes_per_launch"):
+    """DRAM bytes (key "bytes_per_launch") or L2 bytes ("lts_bytes_per_launch") per evaluate
+    launch from the committed ncu summary, if it was taken on the current kernel source;
+    else None."""
     p = os.path.join(ROOT, "profiles", "evaluate_traffic.json")
     try:
         with open(p) as f:
             d = json.load(f)
-        if d.get("kernel_sha") == kernel_source_sha() and workload_name in d.get("bytes_per_launch", {}):
-            return float(d["bytes_per_launch"][workload_name])
+        if d.get("kernel_sha") == kernel_source_sha() and workload_name in d.get(key, {}):
+            return float(d[key][workload_name])
     except Exception:
         pass
     return None
@@ -158,11 +159,57 @@ def job_value(cells: int, npix: int, world: int, ms: float) -> float:
     return cells * npix * world / (ms * 1e-3)
 
 
-# Algorithmic bytes of the evaluate kernel: per visited node its 16 B geometry record;
-# per accepted node (own cell aside) its two 16 B value records and the 8 B angular-kernel
-# offset pair; 4 B per angular-kernel entry; per target 16 B own geometry, 32 B own values,
-# 8 B map lookups, 8 B J_src and 28 B of outputs.
+# Node-stream model of the evaluate kernel (the roofline's algorithmic bytes): every
+# visited node's 16 B geometry record (centre, level, first child) and every accepted
+# node's two 16 B value records (thin and thick moments, COL offset), own cell included.
+NODE_BYTES_VISIT, NODE_BYTES_ACCEPT = 16, 32
+# A wider count of the same launch's loads, reported beside it: the angular-kernel tables
+# too (8 B offset pair per accepted node but the own cell, 4 B per entry) and per target
+# 16 B own geometry, 32 B own values, 8 B map lookups, 8 B J_src and 28 B of outputs.
 BYTES_VISIT, BYTES_ACCEPT, BYTES_ENTRY, BYTES_TARGET = 16, 40, 4, 92
+
+
+def node_stream_bytes(visits: int, accepted: int) -> int:
+    return NODE_BYTES_VISIT * visits + NODE_BYTES_ACCEPT * accepted
+
+
+def time_evaluate(tr, torch, w, dev, steps: int, flush):
+    """Evaluate-kernel time (ms, CUDA events on the launching stream, L2 flushed before each
+    launch) of one workload, with the autotuner's team size and the walk totals."""
+    import numpy as np
+    st = torch.cuda.Stream(device=dev)
+    ctx = tr.Context(w.params)
+    n = w.n_leaves
+    with torch.cuda.stream(st):
+        rho = torch.as_tensor(w.rho, device=dev)
+        td = torch.as_tensor(w.td, device=dev)
+        ctx.build(w.box_cm, rho, td, n=w.uniform_n, blocks=w.blocks,
+                  star_pos=w.star_pos if len(w.star_lum) else None,
+                  star_lum=w.star_lum if len(w.star_lum) else None, stream=st)
+        wpt, _ = ctx.autotune(65536, stream=st)
+        J = torch.empty(n, dtype=torch.float32, device=dev)
+        F = torch.empty(3 * n, dtype=torch.float64, device=dev)
+        for _ in range(3):
+            ctx.evaluate(J, F, stream=st)
+        ts = []
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            ctx.evaluate(J, F, stream=st)
+            e1.record(st)
+            st.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ctx.check(st)
+        tot = ctx.walk_stats(stream=st).cpu().numpy().astype(np.int64)
+    ctx.close()
+    ms = statistics.mean(ts)
+    visits, acc, ent = (int(x) for x in tot)
+    return {"ms": ms, "cells": n, "npix": w.params["npix"], "warps_per_target": wpt,
+            "ray_evals_per_s": n * w.params["npix"] / (ms * 1e-3),
+            "node_stream_GBps": node_stream_bytes(visits, acc) / (ms * 1e-3) / 1e9,
+            "walk": {"visits": visits, "accepted": acc, "alpha_entries": ent}}
 
 
 def run_ours(args):
@@ -247,15 +294,26 @@ def run_ours(args):
     ms, ms_eval = job_times([ms, ms_eval], dist, dev)
     value = job_value(n, npix, world, ms)
 
-    # ---- roofline of the evaluate kernel (algorithmic bytes / measured duration)
+    # ---- roofline of the evaluate kernel: node-stream bytes per launch / measured duration
     with torch.cuda.stream(st):
         tot = ctx.walk_stats(stream=st).cpu().numpy().astype(np.int64)
     visits, acc, ent = (int(x) for x in tot)
-    alg_bytes = (BYTES_VISIT * visits + BYTES_ACCEPT * (acc - n) + BYTES_ENTRY * ent
-                 + BYTES_TARGET * n)
+    ns_bytes = node_stream_bytes(visits, acc)
+    wide_bytes = (BYTES_VISIT * visits + BYTES_ACCEPT * (acc - n) + BYTES_ENTRY * ent
+                  + BYTES_TARGET * n)
     peak, peak_kind = measured_peak()
-    achieved = alg_bytes / (ms_eval * 1e-3) / 1e9
+    achieved = ns_bytes / (ms_eval * 1e-3) / 1e9
     traffic = ncu_traffic(f"turb128_npix{npix}")
+    l2_bytes = ncu_traffic(f"turb128_npix{npix}", key="lts_bytes_per_launch")
+
+    # ---- the other configurations' evaluate kernels (second ray count; collapsing core)
+    import synth
+    extra = {}
+    if not args.no_extra_configs:
+        w192 = workload(192) if npix != 192 else None
+        if w192 is not None:
+            extra["turb128_npix192"] = time_evaluate(tr, torch, w192, dev, args.steps, flush)
+        extra["amr_core_npix48"] = time_evaluate(tr, torch, synth.amr_core(), dev, args.steps, flush)
 
     # ---- end to end through the public API with host buffers
     rho_h = torch.as_tensor(w.rho).pin_memory()
@@ -309,11 +367,25 @@ def run_ours(args):
                                     "ms_evaluate": ms_eval,
                                     "ms_radpressure_dust": statistics.mean(post_ms),
                                     "warps_per_target": best_wpt,
-                                    "autotune_ms_wpt2_3_4_8": tune_ms}),
-            "roofline": {"bound": "hbm", "kernel": "k_evaluate", "achieved": achieved,
+                                    "autotune_ms_wpt2_3_4_8": tune_ms,
+                                    "ms_evaluate_npix192": extra.get("turb128_npix192", {}).get("ms"),
+                                    "ms_evaluate_amr_core": extra.get("amr_core_npix48", {}).get("ms"),
+                                    "other_configs": extra}),
+            # The walk's node records are served by L1/L2 (DRAM moves only the compulsory
+            # bytes); the kernel is bound by the SM's L1 data pipe (shared-memory deposits and
+            # node loads). `frac` is the node-stream rate against the measured HBM copy peak.
+            "roofline": {"bound": "l1", "kernel": "k_evaluate", "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "peak_kind": peak_kind, "traffic": traffic,
-                         "algorithmic_bytes_per_launch": alg_bytes,
+                         "peak_kind": peak_kind,
+                         "peak_basis": "measured HBM copy bandwidth (node-stream model)",
+                         "traffic": traffic,
+                         "dram_frac": None if traffic is None else traffic / (ms_eval * 1e-3) / 1e9 / peak,
+                         "l2_GBps": None if l2_bytes is None else l2_bytes / (ms_eval * 1e-3) / 1e9,
+                         "algorithmic_bytes_per_launch": ns_bytes,
+                         "bytes_model": f"{NODE_BYTES_VISIT} B per visited node + {NODE_BYTES_ACCEPT} B per accepted node",
+                         "with_angular_tables": {"bytes_per_launch": wide_bytes,
+                                                 "achieved": wide_bytes / (ms_eval * 1e-3) / 1e9,
+                                                 "frac": wide_bytes / (ms_eval * 1e-3) / 1e9 / peak},
                          "walk": {"visits": visits, "accepted": acc, "alpha_entries": ent}},
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
@@ -357,11 +429,22 @@ def cpu_baseline(w, seconds: float):
     t_s = time.perf_counter() - t0
     t_full = t_build + t_s * w.n_leaves / m
     cores = os.cpu_count()
+    # one core: the same steps on a smaller sample (about a quarter of the time budget)
+    m1 = int(max(256, min(m, m * 0.25 * seconds / max(t_s * cores, 1e-3))))
+    tg1 = synth.sample_targets(w.n_leaves, m1, seed=23)
+    t0 = time.perf_counter()
+    J1, F1 = tree.evaluate(tg1, threads=1)
+    tree.radpressure(J1, F1, tg1)
+    oracle.dust_temperature(w.params, w.rho[tg1], w.tgas[tg1], J1)
+    t_1 = time.perf_counter() - t0
     return {"value": w.n_leaves * w.params["npix"] / t_full, "unit": UNIT, "cores": cores,
             "kind": "oracle",
             "sample": f"{m} random cells of {w.n_leaves} (evaluate+radpressure+dust T, "
                       f"{t_s:.1f} s) plus the full tree build ({t_build:.1f} s), scaled to all cells",
-            "threads": cores}
+            "threads": cores,
+            "one_core": {"value": w.n_leaves * w.params["npix"] / (t_build + t_1 * w.n_leaves / m1),
+                         "sample": f"{m1} random cells on 1 thread ({t_1:.1f} s), same tree build "
+                                   f"time, scaled to all cells"}}
 
 
 def run_batch64(args):
@@ -871,6 +954,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-sample", type=int, default=16384)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra-configs", action="store_true",
+                    help="skip the 192-ray and collapsing-core evaluate timings")
     ap.add_argument("--profile-evaluate", action="store_true",
                     help="ncu driver: evaluate kernel only, on --profile-targets cells")
     ap.add_argument("--profile-targets", type=int, default=262144)

@@ -347,7 +347,9 @@ treeray_status treeray_warm_start(treeray_t ctx, treeray_mlp_t mlp, const float*
                                   treeray_stream_t stream);
 
 /* Synchronize the stream and report errors recorded by kernels since the last check
- * (TREERAY_ETIMEOUT for a bounded loop that ran out, TREERAY_ECUDA for CUDA errors). */
+ * (TREERAY_ETIMEOUT for a bounded loop that ran out, such as a walk stack that would have
+ * overflowed; TREERAY_EINVAL for a target index out of range or an input field with a
+ * negative or non-finite value; TREERAY_ECUDA for CUDA errors). Clears the record. */
 treeray_status treeray_check(treeray_t ctx, treeray_stream_t stream);
 
 /* Number of leaves and nodes of the current tree (0 before a build). */
@@ -430,6 +432,21 @@ treeray_status treeray_alpha_counts_rotated_host(int npix, int s, const int64_t*
 /* Number of CUDA kernels this context has launched since it was created
  * (instrumentation for benchmarks; counted on the host at each launch). */
 int64_t treeray_kernel_launches(treeray_t ctx);
+
+/*
+ * Test hooks for the error paths (no counterpart in the paper; they change no result when
+ * left at 0).
+ *  treeray_set_walk_stack_limit: cap the evaluation walk's stack at `entries` child groups
+ *    (0: the full stack, sized for the tree's depth). A walk that needs more stops for that
+ *    target, records a stack overflow in the device error word and returns normally;
+ *    treeray_check then reports TREERAY_ETIMEOUT. That target's J and F are not written.
+ *  treeray_inject_alloc_failure: the n-th device allocation made by this context from now
+ *    on fails as if the device were out of memory (n >= 1; 0 disables); the call that makes
+ *    it returns TREERAY_ENOMEM, leaves the context without a tree (TREERAY_ENOTBUILT until
+ *    the next successful treeray_build) and destroyable.
+ */
+treeray_status treeray_set_walk_stack_limit(treeray_t ctx, int entries);
+treeray_status treeray_inject_alloc_failure(treeray_t ctx, int n);
 
 /* Message of the last error on this thread (empty string if none). */
 const char* treeray_last_error(void);

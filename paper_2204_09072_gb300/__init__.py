@@ -97,6 +97,8 @@ def lib():
     L.treeray_warm_start.argtypes = [vp, vp, vp, vp, vp]
     L.treeray_morton_order_noalloc.argtypes = [C.POINTER(Grid), vp, vp, vp]
     L.treeray_kernel_launches.argtypes = [vp]
+    L.treeray_set_walk_stack_limit.argtypes = [vp, C.c_int]
+    L.treeray_inject_alloc_failure.argtypes = [vp, C.c_int]
     L.treeray_kernel_launches.restype = i64
     L.treeray_last_error.restype = C.c_char_p
     for f in ("treeray_create", "treeray_destroy", "treeray_build", "treeray_evaluate",
@@ -109,7 +111,8 @@ def lib():
               "treeray_batch_evaluate", "treeray_features", "treeray_mlp_create",
               "treeray_mlp_destroy", "treeray_mlp_set_params", "treeray_mlp_get_params",
               "treeray_mlp_fit_normalization", "treeray_mlp_train", "treeray_mlp_grad",
-              "treeray_mlp_infer", "treeray_warm_start"):
+              "treeray_mlp_infer", "treeray_warm_start", "treeray_set_walk_stack_limit",
+              "treeray_inject_alloc_failure"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -307,6 +310,14 @@ class Context:
     # -- C: treeray_set_warps_per_target
     def set_warps_per_target(self, wpt: int):
         _raise(lib().treeray_set_warps_per_target(self.h, int(wpt)))
+
+    # -- C: treeray_set_walk_stack_limit (test hook)
+    def set_walk_stack_limit(self, entries: int):
+        _raise(lib().treeray_set_walk_stack_limit(self.h, int(entries)))
+
+    # -- C: treeray_inject_alloc_failure (test hook)
+    def inject_alloc_failure(self, n: int):
+        _raise(lib().treeray_inject_alloc_failure(self.h, int(n)))
 
     # -- C: treeray_features
     def features(self, Tgas, phi=None, stream=None):

@@ -25,12 +25,24 @@ void free_tables(DeviceTables& t) {
     t = DeviceTables{};
 }
 
+treeray_status dev_alloc(treeray_ctx* c, void** p, size_t bytes) {
+    *p = nullptr;
+    if (c && c->alloc_fail_at > 0 && ++c->alloc_count >= c->alloc_fail_at) {
+        c->alloc_fail_at = 0;  // one failure per arrangement
+        set_error("device allocation failed (injected)");
+        return TREERAY_ENOMEM;
+    }
+    TR_CUDA(cudaMalloc(p, bytes));
+    return TREERAY_OK;
+}
+
 namespace {
 template <typename T>
-treeray_status upload(T** dst, const std::vector<T>& src, cudaStream_t s) {
+treeray_status upload(treeray_ctx* c, T** dst, const std::vector<T>& src, cudaStream_t s) {
     if (*dst) cudaFree(*dst);
     *dst = nullptr;
-    TR_CUDA(cudaMalloc((void**)dst, sizeof(T) * std::max<size_t>(src.size(), 1)));
+    const treeray_status rc = dev_alloc(c, (void**)dst, sizeof(T) * std::max<size_t>(src.size(), 1));
+    if (rc != TREERAY_OK) return rc;
     if (!src.empty())
         TR_CUDA(cudaMemcpyAsync(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice, s));
     return TREERAY_OK;
@@ -56,7 +68,7 @@ treeray_status upload_directions(treeray_ctx* c, cudaStream_t s) {
             }
     }
     c->ht.nhat = nh;
-    treeray_status rc = upload(&c->dt.nhat, nh, s);
+    treeray_status rc = upload(c, &c->dt.nhat, nh, s);
     if (rc != TREERAY_OK) return rc;
     TR_CUDA(cudaStreamSynchronize(s));  // the host vector is replaced on the next call
     return TREERAY_OK;
@@ -71,7 +83,7 @@ treeray_status ensure_orient_map(treeray_ctx* c, cudaStream_t s) {
     for (int64_t l = 0; l < c->nleaves; ++l) m[l] = (uint8_t)(l % k);
     c->orient_user = false;
     c->orient_n = 0;
-    treeray_status rc = upload(&c->orient, m, s);
+    treeray_status rc = upload(c, &c->orient, m, s);
     if (rc != TREERAY_OK) return rc;
     TR_CUDA(cudaStreamSynchronize(s));
     c->orient_n = c->nleaves;
@@ -129,8 +141,8 @@ treeray_status upload_tables(treeray_ctx* c, cudaStream_t s) {
             return TREERAY_ENOMEM;
         }
         treeray_status rc;
-        if ((rc = upload(&c->dt.alpha_off, c->ht.alpha_off, s)) != TREERAY_OK) return rc;
-        if ((rc = upload(&c->dt.alpha_ent, c->ht.alpha_ent, s)) != TREERAY_OK) return rc;
+        if ((rc = upload(c, &c->dt.alpha_off, c->ht.alpha_off, s)) != TREERAY_OK) return rc;
+        if ((rc = upload(c, &c->dt.alpha_ent, c->ht.alpha_ent, s)) != TREERAY_OK) return rc;
     }
     c->tau_q = tau_fixed_point_q(c);
     std::vector<int64_t> thr((size_t)(L + 1) * nb), omax(L + 1);
@@ -183,14 +195,14 @@ treeray_status upload_tables(treeray_ctx* c, cudaStream_t s) {
         }
     }
     treeray_status rc;
-    if ((rc = upload(&c->dt.bin_thr, thr, s)) != TREERAY_OK) return rc;
-    if ((rc = upload(&c->dt.R2, R2, s)) != TREERAY_OK) return rc;
-    if ((rc = upload(&c->dt.Rh, Rh, s)) != TREERAY_OK) return rc;
-    if ((rc = upload(&c->dt.Rd, Rd, s)) != TREERAY_OK) return rc;
-    if ((rc = upload(&c->dt.open_max, omax, s)) != TREERAY_OK) return rc;
-    if ((rc = upload(&c->dt.lvlp, lvlp, s)) != TREERAY_OK) return rc;
-    if ((rc = upload(&c->dt.str_lo, slo, s)) != TREERAY_OK) return rc;
-    if ((rc = upload(&c->dt.str_hi, shi, s)) != TREERAY_OK) return rc;
+    if ((rc = upload(c, &c->dt.bin_thr, thr, s)) != TREERAY_OK) return rc;
+    if ((rc = upload(c, &c->dt.R2, R2, s)) != TREERAY_OK) return rc;
+    if ((rc = upload(c, &c->dt.Rh, Rh, s)) != TREERAY_OK) return rc;
+    if ((rc = upload(c, &c->dt.Rd, Rd, s)) != TREERAY_OK) return rc;
+    if ((rc = upload(c, &c->dt.open_max, omax, s)) != TREERAY_OK) return rc;
+    if ((rc = upload(c, &c->dt.lvlp, lvlp, s)) != TREERAY_OK) return rc;
+    if ((rc = upload(c, &c->dt.str_lo, slo, s)) != TREERAY_OK) return rc;
+    if ((rc = upload(c, &c->dt.str_hi, shi, s)) != TREERAY_OK) return rc;
     TR_CUDA(cudaStreamSynchronize(s));  // host vectors die on return
     c->tab_lmax = L;
     c->tab_amr = c->amr;
@@ -319,7 +331,9 @@ treeray_status treeray_build(treeray_t c, const treeray_grid* g, const float* rh
     }
     rc = build_tree(c, g, rho, Td, kappa, n_stars, star_pos, star_lum, (cudaStream_t)stream);
     if (rc != TREERAY_OK) return rc;
-    return reserve_eval_stacks(c, c->lmax, (cudaStream_t)stream);
+    rc = reserve_eval_stacks(c, c->lmax, (cudaStream_t)stream);
+    if (rc != TREERAY_OK) c->built = false;  // a failed build leaves no usable tree
+    return rc;
 }
 
 treeray_status treeray_set_orientations(treeray_t c, int k, const double* rot, const uint8_t* orient) {
@@ -364,7 +378,7 @@ treeray_status treeray_set_orientations(treeray_t c, int k, const double* rot, c
     c->orient_user = false;
     if ((rc = upload_directions(c, nullptr)) != TREERAY_OK) return rc;
     if (orient) {
-        if ((rc = upload(&c->orient, m, nullptr)) != TREERAY_OK) return rc;
+        if ((rc = upload(c, &c->orient, m, nullptr)) != TREERAY_OK) return rc;
         TR_CUDA(cudaDeviceSynchronize());
         c->orient_n = c->nleaves;
         c->orient_user = true;
@@ -462,12 +476,13 @@ treeray_status treeray_fixed_point(treeray_t c, const float* Tgas, const float* 
         c->fp_J = nullptr;
         c->fp_F = nullptr;
         c->fp_cap = 0;
-        TR_CUDA(cudaMalloc(&c->fp_Tnew, sizeof(float) * N));
-        TR_CUDA(cudaMalloc(&c->fp_J, sizeof(float) * N));
-        TR_CUDA(cudaMalloc(&c->fp_F, sizeof(double) * 3 * N));
+        if ((rc = dev_alloc(c, (void**)&c->fp_Tnew, sizeof(float) * N)) != TREERAY_OK ||
+            (rc = dev_alloc(c, (void**)&c->fp_J, sizeof(float) * N)) != TREERAY_OK ||
+            (rc = dev_alloc(c, (void**)&c->fp_F, sizeof(double) * 3 * N)) != TREERAY_OK)
+            return rc;
         c->fp_cap = N;
     }
-    if (!c->fp_flags) TR_CUDA(cudaMalloc(&c->fp_flags, sizeof(int) * 4));
+    if (!c->fp_flags && (rc = dev_alloc(c, (void**)&c->fp_flags, sizeof(int) * 4)) != TREERAY_OK) return rc;
     if (!c->fp_stream) TR_CUDA(cudaStreamCreateWithFlags(&c->fp_stream, cudaStreamNonBlocking));
     for (cudaEvent_t& e : c->fp_ev)
         if (!e) TR_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
@@ -535,8 +550,9 @@ treeray_status treeray_check(treeray_t c, treeray_stream_t stream) {
         if (e & kErrAlphaKey) m += " angular-kernel key outside the table;";
         if (e & kErrOctree) m += " leaves do not form a complete octree;";
         if (e & kErrTarget) m += " target index out of range;";
+        if (e & kErrInput) m += " an input field holds a negative or non-finite value;";
         set_error(m);
-        return (e & kErrTarget) ? TREERAY_EINVAL : TREERAY_ETIMEOUT;
+        return (e & (kErrTarget | kErrInput)) ? TREERAY_EINVAL : TREERAY_ETIMEOUT;
     }
     return TREERAY_OK;
 }
@@ -633,6 +649,29 @@ treeray_status treeray_alpha_counts_rotated_host(int npix, int s, const int64_t*
 }
 
 int64_t treeray_kernel_launches(treeray_t c) { return c ? c->launches : 0; }
+
+treeray_status treeray_set_walk_stack_limit(treeray_t c, int entries) {
+    treeray_status rc = check_ctx(c, false);
+    if (rc != TREERAY_OK) return rc;
+    if (entries < 0) {
+        set_error("set_walk_stack_limit: entries >= 0");
+        return TREERAY_EINVAL;
+    }
+    c->stack_limit = entries;
+    return TREERAY_OK;
+}
+
+treeray_status treeray_inject_alloc_failure(treeray_t c, int n) {
+    treeray_status rc = check_ctx(c, false);
+    if (rc != TREERAY_OK) return rc;
+    if (n < 0) {
+        set_error("inject_alloc_failure: n >= 0");
+        return TREERAY_EINVAL;
+    }
+    c->alloc_fail_at = n;
+    c->alloc_count = 0;
+    return TREERAY_OK;
+}
 
 const char* treeray_last_error(void) { return g_err.c_str(); }
 

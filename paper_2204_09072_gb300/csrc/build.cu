@@ -304,6 +304,7 @@ struct MomArgs {
     float* rho_copy;
     float* kin_copy;
     const int* skip;     // fixed-point mode: return at once when *skip != 0
+    unsigned* err;       // device error word: kErrInput for a negative or non-finite input
 };
 
 // b-node quantities (Sec. 4.1.1); expression order fixed (see the file header)
@@ -324,6 +325,10 @@ __global__ void k_leaf_moments(MomArgs a) {
         const double Tc = T < 150.0 ? T : 150.0;
         kap = 1.0e-3 * (Tc * Tc);
     }
+    // inputs outside their domain (negative or NaN/inf) are reported, not used to index
+    // anything; the results of such a build are undefined
+    if (!(rh >= 0.0 && rh <= 3.4e38) || !(T >= 0.0 && T <= 3.4e38) || !(kap >= 0.0 && kap <= 3.4e38))
+        atomicOr(a.err, kErrInput);
     const double dx = ldexp(a.box, -l);
     const double dV = (dx * dx) * dx;
     const double rk = rh * kap;
@@ -474,12 +479,11 @@ __global__ void k_pack(const int4* geo, const double* mom, int64_t nn, double u,
 inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
 template <typename T>
-treeray_status grow(T** p, int64_t* cap, int64_t need) {
+treeray_status grow(treeray_ctx* c, T** p, int64_t* cap, int64_t need) {
     if (*p && *cap >= need) return TREERAY_OK;
     if (*p) cudaFree(*p);
     *p = nullptr;
-    TR_CUDA(cudaMalloc((void**)p, sizeof(T) * std::max<int64_t>(need, 1)));
-    return TREERAY_OK;
+    return dev_alloc(c, (void**)p, sizeof(T) * std::max<int64_t>(need, 1));
 }
 
 }  // namespace
@@ -552,6 +556,13 @@ treeray_status build_tree(treeray_ctx* c, const treeray_grid* gr, const float* r
         set_error("stars: 0..4096 with host position and luminosity arrays");
         return TREERAY_EINVAL;
     }
+    for (int q = 0; q < n_stars; ++q) {
+        const double x = star_pos[3 * q], y = star_pos[3 * q + 1], z = star_pos[3 * q + 2], L = star_lum[q];
+        if (!(std::isfinite(x) && std::isfinite(y) && std::isfinite(z) && L >= 0.0 && std::isfinite(L))) {
+            set_error("stars: positions must be finite and luminosities finite and >= 0");
+            return TREERAY_EINVAL;
+        }
+    }
     if (!rho || !Td) {
         set_error("rho and Td are required");
         return TREERAY_EINVAL;
@@ -569,7 +580,7 @@ treeray_status build_tree(treeray_ctx* c, const treeray_grid* gr, const float* r
 #define GROW(ptr, need, capv)                                   \
     do {                                                        \
         int64_t cc_ = (capv);                                   \
-        if ((rc = grow(&(ptr), &cc_, (need))) != TREERAY_OK) return rc; \
+        if ((rc = grow(c, &(ptr), &cc_, (need))) != TREERAY_OK) return rc; \
     } while (0)
     GROW(T.keys, N, cl);
     GROW(T.keys_alt, N, cl);
@@ -595,13 +606,13 @@ treeray_status build_tree(treeray_ctx* c, const treeray_grid* gr, const float* r
     }
     {
         int64_t cs = T.cap_stars;
-        if ((rc = grow(&T.stars, &cs, (int64_t)hst.size())) != TREERAY_OK) return rc;
+        if ((rc = grow(c, &T.stars, &cs, (int64_t)hst.size())) != TREERAY_OK) return rc;
         T.cap_stars = std::max(T.cap_stars, (int64_t)hst.size());
         int64_t cv = T.levels ? 2 * (kMaxLevel + 1) : 0;
-        if ((rc = grow(&T.levels, &cv, 2 * (kMaxLevel + 1))) != TREERAY_OK) return rc;
+        if ((rc = grow(c, &T.levels, &cv, 2 * (kMaxLevel + 1))) != TREERAY_OK) return rc;
         if (c->amr) {
             int64_t cb = T.cap_blocks;
-            if ((rc = grow(&T.blocks, &cb, (int64_t)hblocks.size())) != TREERAY_OK) return rc;
+            if ((rc = grow(c, &T.blocks, &cb, (int64_t)hblocks.size())) != TREERAY_OK) return rc;
             T.cap_blocks = std::max(T.cap_blocks, (int64_t)hblocks.size());
         }
     }
@@ -621,7 +632,7 @@ treeray_status build_tree(treeray_ctx* c, const treeray_grid* gr, const float* r
     const int nbk = nblk(N, kSortTile);
     const int64_t nh = 256 * (int64_t)nbk;
     int64_t ch = T.cap_hist;
-    if ((rc = grow(&T.hist, &ch, nh + 256)) != TREERAY_OK) return rc;
+    if ((rc = grow(c, &T.hist, &ch, nh + 256)) != TREERAY_OK) return rc;
     T.cap_hist = std::max(T.cap_hist, nh + 256);
     uint32_t* digit_base = T.hist + nh;
     const int bits = 3 * lmax + 5;
@@ -736,7 +747,7 @@ treeray_status build_tree(treeray_ctx* c, const treeray_grid* gr, const float* r
     MomArgs m{lg, T.perm, T.leaf_node, rho, Td, kappa, dstars, n_stars, gr->box,
               c->p.kappa_model, c->p.kappa0, c->p.kappa_ext_scale, c->p.dust_emission, nn, N,
               T.mom, T.geo, T.kap, T.tau, T.jsrc, T.psrc, T.thickflag, T.rho,
-              kappa ? T.kin : nullptr, nullptr};
+              kappa ? T.kin : nullptr, nullptr, c->dt.err};
     k_leaf_moments<<<nblk(N, 128), 128, 0, st>>>(m);
     ++c->launches;
     for (int l = lmax - 1; l >= 0; --l)
@@ -759,6 +770,13 @@ treeray_status build_tree(treeray_ctx* c, const treeray_grid* gr, const float* r
         set_error("grid: leaves do not form a complete octree");
         return TREERAY_EINVAL;
     }
+    if (herr & kErrInput) {
+        // reported here; the bit is cleared so that a later build on valid inputs succeeds
+        const unsigned rest = herr & ~(unsigned)kErrInput;
+        TR_CUDA(cudaMemcpy(c->dt.err, &rest, sizeof(unsigned), cudaMemcpyHostToDevice));
+        set_error("rho, Td and kappa must be finite and >= 0");
+        return TREERAY_EINVAL;
+    }
     c->has_thick = root_vk > 0.0;
     c->grid_n = gr->n;
     c->n_stars = n_stars;
@@ -777,7 +795,7 @@ treeray_status refresh_tree(treeray_ctx* c, const float* Td, const int* skip, cu
     LeafGrid lg{c->amr ? 0 : c->grid_n, c->lmax, T.blocks};
     MomArgs m{lg, T.perm, T.leaf_node, T.rho, Td, c->kin_given ? T.kin : nullptr, T.stars, c->n_stars,
               c->box, c->p.kappa_model, c->p.kappa0, c->p.kappa_ext_scale, c->p.dust_emission, nn, N,
-              T.mom, T.geo, T.kap, T.tau, T.jsrc, T.psrc, T.thickflag, T.rho, nullptr, skip};
+              T.mom, T.geo, T.kap, T.tau, T.jsrc, T.psrc, T.thickflag, T.rho, nullptr, skip, c->dt.err};
     k_leaf_moments<<<nblk(N, 128), 128, 0, st>>>(m);
     ++c->launches;
     for (int l = c->lmax - 1; l >= 0; --l)

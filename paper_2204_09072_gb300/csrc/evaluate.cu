@@ -1153,6 +1153,7 @@ treeray_status launch_team(treeray_ctx* c, const EvalArgs& a, const EvalArgs* bo
     constexpr int nq = THICK ? 6 : 2;
     EvalArgs b = a;
     b.stack_cap = (int)(stack_bytes_for(WPT, layout_lmax, 1) / sizeof(int));
+    if (c->stack_limit > 0) b.stack_cap = std::min(b.stack_cap, c->stack_limit);  // test hook
     const size_t smem = align16(align16((size_t)nq * a.nbins * tile_row(NPIX, THICK) * 4) + (THICK ? NPIX * 8 : 0)) +
                         (size_t)WPT * owner_cap(THICK);
     int smem_optin = 0, sms = 0;
@@ -1316,6 +1317,7 @@ EvalArgs make_args(treeray_ctx* c, const int32_t* targets, int64_t n) {
     a.inv_u2 = 1.0 / (c->u * c->u);
     // the stack holds at most 28 leftover groups per level plus one batch of pushes
     a.stack_cap = 28 * (c->lmax + 1) + 40;
+    if (c->stack_limit > 0) a.stack_cap = std::min(a.stack_cap, c->stack_limit);  // test hook
     return a;
 }
 
@@ -1339,10 +1341,10 @@ treeray_status reserve_eval_stacks(treeray_ctx* c, int lmax, cudaStream_t s) {
         c->stack_scr = nullptr;
         c->stack_scr_bytes = 0;
     }
-    if (cudaMalloc(&c->stack_scr, need) != cudaSuccess) {
+    const treeray_status rc = dev_alloc(c, (void**)&c->stack_scr, need);
+    if (rc != TREERAY_OK) {
         c->stack_scr = nullptr;
-        set_error("evaluate: cannot allocate the team-stack scratch");
-        return TREERAY_ENOMEM;
+        return rc;
     }
     c->stack_scr_bytes = need;
     return TREERAY_OK;

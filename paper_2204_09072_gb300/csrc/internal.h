@@ -30,6 +30,7 @@ enum : unsigned {
     kErrAlphaKey = 2u,    // angular-kernel key outside the table
     kErrOctree = 4u,      // the leaves do not form a complete octree
     kErrTarget = 8u,      // target index out of range
+    kErrInput = 16u,      // a density, temperature or opacity input is negative or not finite
 };
 
 void set_error(const std::string& msg);
@@ -138,6 +139,9 @@ struct treeray_ctx {
     int64_t launches = 0;  // kernels launched by this context
     int wpt = 4;           // warps per target team of the evaluate kernel (autotuned)
     int tau_q = 0;         // thin tiles: fixed-point optical depth in units of 2^-tau_q (0: float)
+    int stack_limit = 0;   // test hook: cap on the walk stack's entries (0: the full stack)
+    int alloc_fail_at = 0; // test hook: the n-th device allocation from now fails (0: none)
+    int alloc_count = 0;
     // table cache key
     int tab_lmax = -1;
     bool tab_amr = false;
@@ -146,6 +150,9 @@ struct treeray_ctx {
 
 // kernels entry points (defined in the .cu files)
 namespace tr {
+// Device allocation of a context's buffers (cudaMalloc), or the failure that
+// treeray_inject_alloc_failure arranged; on failure *p is null and TREERAY_ENOMEM returned.
+treeray_status dev_alloc(treeray_ctx* c, void** p, size_t bytes);
 // Team-stack scratch of the evaluate kernel large enough for any team size on a tree of
 // `lmax` levels below the root; never allocates while `s` is being captured.
 treeray_status reserve_eval_stacks(treeray_ctx* c, int lmax, cudaStream_t s);

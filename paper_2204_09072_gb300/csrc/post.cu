@@ -100,6 +100,7 @@ struct DustArgs {
     int64_t n;
     int model;
     double kappa0, xi;
+    unsigned* err;  // kErrInput for a negative or non-finite gas temperature or heating rate
 };
 
 __device__ inline double kappa_of(const DustArgs& d, int64_t k, double T) {
@@ -196,6 +197,7 @@ __global__ void k_dust(DustArgs d) {
     c.Tg = (double)d.tgas[k];
     c.J = (double)d.J[k];
     c.H = d.heat ? (double)d.heat[k] : 0.0;
+    if (!(c.Tg >= 0.0 && c.Tg <= 3.4e38) || !(c.H >= -3.4e38 && c.H <= 3.4e38)) atomicOr(d.err, kErrInput);
     c.c1 = 3.8e-33 * sqrt(c.Tg);
     c.c2 = 1.0 - 0.8 * exp(-75.0 / c.Tg);
     const double nH = kHydrogenFraction * c.rho / kHydrogenMass;
@@ -242,7 +244,7 @@ treeray_status launch_dust(treeray_ctx* c, const float* Tgas, const float* heat,
 treeray_status launch_dust_skip(treeray_ctx* c, const float* Tgas, const float* heat, const float* J,
                                 float* Td, const int* skip, cudaStream_t s) {
     DustArgs d{skip, c->tree.rho, Tgas, heat, J, c->kin_given ? c->tree.kin : nullptr, Td, c->nleaves,
-               c->p.kappa_model, c->p.kappa0, c->p.dust_to_gas};
+               c->p.kappa_model, c->p.kappa0, c->p.dust_to_gas, c->dt.err};
     k_dust<<<(int)((c->nleaves + 127) / 128), 128, 0, s>>>(d);
     c->launches += 1;
     TR_CUDA(cudaGetLastError());
