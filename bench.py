@@ -186,7 +186,7 @@ def time_evaluate(tr, torch, w, dev, steps: int, flush):
         ctx.build(w.box_cm, rho, td, n=w.uniform_n, blocks=w.blocks,
                   star_pos=w.star_pos if len(w.star_lum) else None,
                   star_lum=w.star_lum if len(w.star_lum) else None, stream=st)
-        wpt, _ = ctx.autotune(65536, stream=st)
+        wpt, occ, _, _ = ctx.autotune_launch(65536, stream=st)
         J = torch.empty(n, dtype=torch.float32, device=dev)
         F = torch.empty(3 * n, dtype=torch.float64, device=dev)
         for _ in range(3):
@@ -206,7 +206,7 @@ def time_evaluate(tr, torch, w, dev, steps: int, flush):
     ctx.close()
     ms = statistics.mean(ts)
     visits, acc, ent = (int(x) for x in tot)
-    return {"ms": ms, "cells": n, "npix": w.params["npix"], "warps_per_target": wpt,
+    return {"ms": ms, "cells": n, "npix": w.params["npix"], "warps_per_target": wpt, "occupancy_pct": occ,
             "ray_evals_per_s": n * w.params["npix"] / (ms * 1e-3),
             "node_stream_GBps": node_stream_bytes(visits, acc) / (ms * 1e-3) / 1e9,
             "walk": {"visits": visits, "accepted": acc, "alpha_entries": ent}}
@@ -248,7 +248,7 @@ def run_ours(args):
     # evaluate kernel's warps per target for this tree
     with torch.cuda.stream(st):
         ctx.build(w.box_cm, rho, td, n=w.uniform_n, star_pos=w.star_pos, star_lum=w.star_lum, stream=st)
-        best_wpt, tune_ms = ctx.autotune(65536, stream=st)
+        best_wpt, best_occ, tune_ms, tune_occ = ctx.autotune_launch(65536, stream=st)
 
     def step(ev=None):
         if ev:
@@ -368,6 +368,8 @@ def run_ours(args):
                                     "ms_radpressure_dust": statistics.mean(post_ms),
                                     "warps_per_target": best_wpt,
                                     "autotune_ms_wpt2_3_4_8": tune_ms,
+                                    "occupancy_pct": best_occ,
+                                    "autotune_ms_occupancy_100_75_50": tune_occ,
                                     "ms_evaluate_npix192": extra.get("turb128_npix192", {}).get("ms"),
                                     "ms_evaluate_amr_core": extra.get("amr_core_npix48", {}).get("ms"),
                                     "other_configs": extra}),
@@ -448,20 +450,32 @@ def cpu_baseline(w, seconds: float):
 
 
 def run_batch64(args):
-    """64 independent AMR boxes (12.3 M leaves): one batched persistent launch replayed as a
-    CUDA graph, against one evaluate launch per box. Prints one JSON line."""
+    """Independent boxes evaluated together: one batched persistent launch (per kernel
+    variant), also replayed as a CUDA graph, against one evaluate launch per box with each
+    box's autotuned team size. --batch64: 64 AMR boxes of 32^3-128^3 finest resolution
+    (12.3 M leaves); --batch512: 512 boxes of 16^3-32^3 (1-2 levels); --batch-tiny: 1024
+    boxes of 8^3, too small to fill the GPU one launch at a time. Prints one JSON line."""
     import torch
 
     import paper_2204_09072_gb300 as tr
     import synth
     dev = torch.device("cuda:0")
-    boxes = synth.batch_of_boxes(64, seed=5, npix=args.npix)
+    if args.batch_tiny:
+        boxes = synth.batch_of_tiny_boxes(1024, seed=10, npix=args.npix)
+        name = "batch1024_tiny8"
+    elif args.batch512:
+        boxes = synth.batch_of_small_boxes(512, seed=9, npix=args.npix)
+        name = "batch512_small"
+    else:
+        boxes = synth.batch_of_boxes(64, seed=5, npix=args.npix)
+        name = "batch64_amr"
     ctxs, Js, Fs = [], [], []
     t0 = time.perf_counter()
     for w in boxes:
         c = tr.Context(w.params)
         c.build(w.box_cm, torch.as_tensor(w.rho, device=dev), torch.as_tensor(w.td, device=dev),
                 blocks=w.blocks)
+        c.autotune_launch(min(65536, w.n_leaves))
         ctxs.append(c)
         Js.append(torch.empty(w.n_leaves, dtype=torch.float32, device=dev))
         Fs.append(torch.empty(3 * w.n_leaves, dtype=torch.float64, device=dev))
@@ -492,7 +506,8 @@ def run_batch64(args):
     ms_seq = timed(per_box, args.steps)
     for c in ctxs:
         c.check()
-    print(json.dumps({"metric": METRIC, "unit": UNIT, "workload": "batch64_amr",
+    print(json.dumps({"metric": METRIC, "unit": UNIT, "workload": name,
+                      "speedup_graph_vs_per_box": ms_seq / ms_graph,
                       "boxes": len(boxes), "cells": n, "npix": args.npix,
                       "value_batched_graph": n * args.npix / (ms_graph * 1e-3),
                       "value_batched_plain": n * args.npix / (ms_plain * 1e-3),
@@ -963,6 +978,8 @@ def main():
     ap.add_argument("--profile-wpt", type=int, default=3, choices=[2, 3, 4, 8],
                     help="warps per target of the profiled launches (thick trees run 3 as 4)")
     ap.add_argument("--batch64", action="store_true", help="64-box AMR batch: batched vs per-box launches")
+    ap.add_argument("--batch512", action="store_true", help="512 small boxes: batched vs per-box launches")
+    ap.add_argument("--batch-tiny", action="store_true", help="1024 boxes of 8^3: batched vs per-box launches")
     ap.add_argument("--sweep", action="store_true", help="N_pix x segments sweep with the autotuner")
     ap.add_argument("--warmstart", action="store_true", help="learned warm start of the T_d fixed point")
     ap.add_argument("--warm-n", type=int, default=256)
@@ -983,7 +1000,7 @@ def main():
         args.warmup = 3
     if args.profile_evaluate:
         run_profile(args)
-    elif args.batch64:
+    elif args.batch64 or args.batch512 or args.batch_tiny:
         run_batch64(args)
     elif args.sweep:
         run_sweep(args)

@@ -265,6 +265,25 @@ treeray_status treeray_fixed_point(treeray_t ctx, const float* Tgas, const float
 treeray_status treeray_autotune(treeray_t ctx, int64_t n_sample, int* best_wpt, float* ms,
                                 treeray_stream_t stream);
 
+/*
+ * The autotuner over both result-neutral launch choices of the evaluate kernel (no
+ * counterpart in the paper; the method's results do not depend on them): warps per target
+ * team as treeray_autotune does, then, for the fastest team size, the resident teams per SM
+ * launched (100, 75 or 50 % of those that fit; fewer teams share the L1 and L2 among fewer
+ * walks). best_wpt, best_occupancy_pct (host int), ms_wpt (host float[4], as for
+ * treeray_autotune) and ms_occupancy (host float[3], for 100, 75, 50 %) may be NULL.
+ * The choice is kept by the context and remembered for the process, keyed by the tree's
+ * shape (leaf count, depth, N_pix, segments, thin or thick tiles, kernel variant, AMR or
+ * uniform, device): a later treeray_build of a tree of the same shape, in any context,
+ * starts from it without timing. Synchronous.
+ */
+treeray_status treeray_autotune_launch(treeray_t ctx, int64_t n_sample, int* best_wpt, int* best_occupancy_pct,
+                                       float* ms_wpt, float* ms_occupancy, treeray_stream_t stream);
+/* The evaluate kernel's current launch choices (host ints, either may be NULL). */
+treeray_status treeray_get_launch_config(treeray_t ctx, int* wpt, int* occupancy_pct);
+/* Resident teams per SM launched by the evaluate kernel, in % of those that fit (1..100). */
+treeray_status treeray_set_occupancy(treeray_t ctx, int occupancy_pct);
+
 /* Set the evaluate kernel's warps per target (2, 3, 4 or 8) by hand; 4 is the default.
  * Trees with thick material run teams of 3 as teams of 4. */
 treeray_status treeray_set_warps_per_target(treeray_t ctx, int wpt);

@@ -98,6 +98,10 @@ def lib():
     L.treeray_morton_order_noalloc.argtypes = [C.POINTER(Grid), vp, vp, vp]
     L.treeray_kernel_launches.argtypes = [vp]
     L.treeray_set_walk_stack_limit.argtypes = [vp, C.c_int]
+    L.treeray_autotune_launch.argtypes = [vp, i64, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                          C.POINTER(C.c_float), C.POINTER(C.c_float), vp]
+    L.treeray_get_launch_config.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.treeray_set_occupancy.argtypes = [vp, C.c_int]
     L.treeray_inject_alloc_failure.argtypes = [vp, C.c_int]
     L.treeray_kernel_launches.restype = i64
     L.treeray_last_error.restype = C.c_char_p
@@ -112,7 +116,8 @@ def lib():
               "treeray_mlp_destroy", "treeray_mlp_set_params", "treeray_mlp_get_params",
               "treeray_mlp_fit_normalization", "treeray_mlp_train", "treeray_mlp_grad",
               "treeray_mlp_infer", "treeray_warm_start", "treeray_set_walk_stack_limit",
-              "treeray_inject_alloc_failure"):
+              "treeray_inject_alloc_failure", "treeray_autotune_launch", "treeray_get_launch_config",
+              "treeray_set_occupancy"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -293,6 +298,26 @@ class Context:
         ms = (C.c_float * 4)()
         _raise(lib().treeray_autotune(self.h, int(n_sample), C.byref(best), ms, _stream(stream)))
         return best.value, list(ms)
+
+    # -- C: treeray_autotune_launch
+    def autotune_launch(self, n_sample: int = 65536, stream=None):
+        """Team size, then resident teams per SM; returns (wpt, occupancy_pct, ms over
+        2/3/4/8 warps, ms over 100/75/50 % occupancy)."""
+        best, occ = C.c_int(0), C.c_int(0)
+        ms = (C.c_float * 4)()
+        mo = (C.c_float * 3)()
+        _raise(lib().treeray_autotune_launch(self.h, int(n_sample), C.byref(best), C.byref(occ), ms, mo,
+                                             _stream(stream)))
+        return best.value, occ.value, list(ms), list(mo)
+
+    # -- C: treeray_get_launch_config / treeray_set_occupancy
+    def launch_config(self):
+        w, o = C.c_int(0), C.c_int(0)
+        _raise(lib().treeray_get_launch_config(self.h, C.byref(w), C.byref(o)))
+        return w.value, o.value
+
+    def set_occupancy(self, pct: int):
+        _raise(lib().treeray_set_occupancy(self.h, int(pct)))
 
     # -- C: treeray_set_orientations
     def set_orientations(self, rot, orient=None):

@@ -781,7 +781,9 @@ treeray_status build_tree(treeray_ctx* c, const treeray_grid* gr, const float* r
     c->grid_n = gr->n;
     c->n_stars = n_stars;
     c->kin_given = kappa != nullptr;
-    return upload_tables(c, st);
+    const treeray_status rt = upload_tables(c, st);
+    if (rt == TREERAY_OK) apply_cached_launch_choice(c);
+    return rt;
 }
 
 // New dust temperatures on the same grid, densities, opacities and stars: leaf

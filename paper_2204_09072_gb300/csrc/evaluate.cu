@@ -19,8 +19,11 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <map>
 #include <memory>
+#include <mutex>
 #include <new>
+#include <tuple>
 #include <vector>
 
 #include "internal.h"
@@ -1103,11 +1106,11 @@ __global__ void __launch_bounds__(WPT * 32, min_warps_per_sm(NPIX, THICK) / WPT)
     evaluate_team<NPIX, THICK, WPT, GENERAL, false>(a, nullptr);
 }
 
-// batches run teams of 4 warps
-template <int NPIX, bool THICK, bool GENERAL>
-__global__ void __launch_bounds__(4 * 32, min_warps_per_sm(NPIX, THICK) / 4)
+// batches run teams of 3 (thin tiles) or 4 warps
+template <int NPIX, bool THICK, int WPT, bool GENERAL>
+__global__ void __launch_bounds__(WPT * 32, min_warps_per_sm(NPIX, THICK) / WPT)
     k_evaluate_batch(const __grid_constant__ BatchArgs p) {
-    evaluate_team<NPIX, THICK, 4, GENERAL, true>(p.launch, &p);
+    evaluate_team<NPIX, THICK, WPT, GENERAL, true>(p.launch, &p);
 }
 
 template <typename K>
@@ -1172,7 +1175,9 @@ treeray_status launch_team(treeray_ctx* c, const EvalArgs& a, const EvalArgs* bo
             set_error("evaluate: kernel does not fit on an SM");
             return TREERAY_EINVAL;
         }
-        blocks = std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * sms, n));
+        // the autotuner may launch fewer resident teams than fit (occ_pct of them, >= 1 per SM)
+        const int use = std::max(1, (per_sm * c->occ_pct + 50) / 100);
+        blocks = std::max<int64_t>(1, std::min<int64_t>((int64_t)use * sms, n));
         if (c->stack_scr_bytes < stack_bytes_for(WPT, layout_lmax, (int)blocks)) {
             const treeray_status rc = reserve_eval_stacks(c, layout_lmax, s);
             if (rc != TREERAY_OK) return rc;
@@ -1190,8 +1195,8 @@ treeray_status launch_team(treeray_ctx* c, const EvalArgs& a, const EvalArgs* bo
         c->launches += 1;
         TR_CUDA(cudaGetLastError());
     } else {
-        static_assert(WPT == 4, "batches run teams of 4 warps");
-        auto kern = k_evaluate_batch<NPIX, THICK, GENERAL>;
+        static_assert(WPT == 4 || (WPT == 3 && !THICK), "batches run teams of 3 (thin) or 4 warps");
+        auto kern = k_evaluate_batch<NPIX, THICK, WPT, GENERAL>;
         std::unique_ptr<BatchArgs> p(new (std::nothrow) BatchArgs());
         if (!p) {
             set_error("out of host memory");
@@ -1211,7 +1216,7 @@ treeray_status launch_team(treeray_ctx* c, const EvalArgs& a, const EvalArgs* bo
             if ((rc = grid_for(kern, p->launch.n, blocks)) != TREERAY_OK) return rc;
             p->launch.stack = c->stack_scr;
             TR_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), s));
-            kern<<<(int)blocks, 4 * 32, smem, s>>>(*p);
+            kern<<<(int)blocks, WPT * 32, smem, s>>>(*p);
             c->launches += 1;
             TR_CUDA(cudaGetLastError());
         }
@@ -1222,8 +1227,12 @@ treeray_status launch_team(treeray_ctx* c, const EvalArgs& a, const EvalArgs* bo
 template <int NPIX, bool THICK, bool GENERAL>
 treeray_status launch_wpt(treeray_ctx* c, int wpt, const EvalArgs& a, const EvalArgs* boxes,
                           const int64_t* box_start, int nbox, int layout_lmax, cudaStream_t s) {
-    // batches run teams of 4 warps
-    if (boxes) return launch_team<NPIX, THICK, 4, GENERAL, true>(c, a, boxes, box_start, nbox, layout_lmax, s);
+    // batches run teams of 3 warps (thin tiles, when that is the team size asked for) or 4
+    if (boxes) {
+        if constexpr (!THICK)
+            if (wpt == 3) return launch_team<NPIX, THICK, 3, GENERAL, true>(c, a, boxes, box_start, nbox, layout_lmax, s);
+        return launch_team<NPIX, THICK, 4, GENERAL, true>(c, a, boxes, box_start, nbox, layout_lmax, s);
+    }
     switch (wpt) {
         case 2: return launch_team<NPIX, THICK, 2, GENERAL, false>(c, a, nullptr, nullptr, 0, layout_lmax, s);
         case 3:  // thin tiles only; thick teams of three were slower than four
@@ -1409,7 +1418,33 @@ int64_t gcd64(int64_t a, int64_t b) {
 }
 }  // namespace
 
-treeray_status autotune(treeray_ctx* c, int64_t n_sample, int* best, float* ms, cudaStream_t s) {
+// Launch choices found by the autotuner, per tree shape (process-wide): a context that
+// builds a tree of a shape already tuned starts from that choice without timing.
+using ShapeKey = std::tuple<int64_t, int, int, int, bool, bool, bool, int>;
+struct LaunchChoice {
+    int wpt, occ_pct;
+};
+std::mutex g_choice_mutex;
+std::map<ShapeKey, LaunchChoice> g_choice;
+
+ShapeKey shape_key(const treeray_ctx* c) {
+    return ShapeKey(c->nleaves, c->lmax, c->p.npix, c->p.nbins, c->has_thick || c->force_thick, needs_general(c),
+                    c->amr, c->device);
+}
+
+void apply_cached_launch_choice(treeray_ctx* c) {
+    std::lock_guard<std::mutex> lock(g_choice_mutex);
+    const auto it = g_choice.find(shape_key(c));
+    if (it == g_choice.end()) return;
+    c->wpt = it->second.wpt;
+    c->occ_pct = it->second.occ_pct;
+}
+
+// Times the result-neutral launch choices of the evaluate kernel on a sample of targets:
+// warps per target (2, 3, 4, 8; 3 only for thin tiles) at full occupancy, then for the
+// fastest team size the resident teams per SM (100, 75, 50 % of those that fit).
+treeray_status autotune(treeray_ctx* c, int64_t n_sample, int* best, float* ms, int* best_occ, float* ms_occ,
+                        cudaStream_t s) {
     const int64_t N = c->nleaves;
     const int64_t n = std::max<int64_t>(1, std::min(n_sample, N));
     int64_t step = 1000003;
@@ -1432,38 +1467,41 @@ treeray_status autotune(treeray_ctx* c, int64_t n_sample, int* best, float* ms, 
             if (e1) cudaEventDestroy(e1);
         }
     } guard{t, J, F, e0, e1};
-    TR_CUDA(cudaMalloc(&t, sizeof(int32_t) * n));
-    TR_CUDA(cudaMalloc(&J, sizeof(float) * n));
-    TR_CUDA(cudaMalloc(&F, sizeof(double) * 3 * n));
+    treeray_status rc;
+    if ((rc = dev_alloc(c, (void**)&t, sizeof(int32_t) * n)) != TREERAY_OK) return rc;
+    if ((rc = dev_alloc(c, (void**)&J, sizeof(float) * n)) != TREERAY_OK) return rc;
+    if ((rc = dev_alloc(c, (void**)&F, sizeof(double) * 3 * n)) != TREERAY_OK) return rc;
     TR_CUDA(cudaEventCreate(&e0));
     TR_CUDA(cudaEventCreate(&e1));
     k_sample_targets<<<(int)((n + 255) / 256), 256, 0, s>>>(t, n, N, step);
     ++c->launches;
-    // teams of three warps exist for thin tiles only
     const bool thick = c->has_thick || c->force_thick;
+    auto time_once = [&](int wpt, float* out) -> treeray_status {
+        EvalArgs a = make_args(c, t, n);
+        a.J = J;
+        a.F = F;
+        for (int rep = 0; rep < 2; ++rep) {  // the second launch is timed
+            if (rep == 1) TR_CUDA(cudaEventRecord(e0, s));
+            const treeray_status r = dispatch_team(c, thick, needs_general(c), wpt, a, nullptr, nullptr, 1, c->lmax, s);
+            if (r != TREERAY_OK) return r;
+        }
+        TR_CUDA(cudaEventRecord(e1, s));
+        TR_CUDA(cudaEventSynchronize(e1));
+        TR_CUDA(cudaEventElapsedTime(out, e0, e1));
+        return TREERAY_OK;
+    };
     const int cand[4] = {2, 3, 4, 8};
     float bestt = 0.0f;
     int bw = c->wpt;
     bool first = true;
+    c->occ_pct = 100;
     for (int k = 0; k < 4; ++k) {
-        if (thick && cand[k] == 3) {
+        if (thick && cand[k] == 3) {  // teams of three warps exist for thin tiles only
             if (ms) ms[k] = -1.0f;
             continue;
         }
-        EvalArgs a = make_args(c, t, n);
-        a.J = J;
-        a.F = F;
-        treeray_status rc;
-        for (int rep = 0; rep < 2; ++rep) {  // the second launch is timed
-            if (rep == 1) TR_CUDA(cudaEventRecord(e0, s));
-            rc = dispatch_team(c, c->has_thick || c->force_thick, needs_general(c), cand[k], a, nullptr, nullptr, 1,
-                               c->lmax, s);
-            if (rc != TREERAY_OK) return rc;
-        }
-        TR_CUDA(cudaEventRecord(e1, s));
-        TR_CUDA(cudaEventSynchronize(e1));
         float t_ms = 0.0f;
-        TR_CUDA(cudaEventElapsedTime(&t_ms, e0, e1));
+        if ((rc = time_once(cand[k], &t_ms)) != TREERAY_OK) return rc;
         if (ms) ms[k] = t_ms;
         if (first || t_ms < bestt) {
             bestt = t_ms;
@@ -1471,8 +1509,29 @@ treeray_status autotune(treeray_ctx* c, int64_t n_sample, int* best, float* ms, 
             first = false;
         }
     }
+    const int occ[3] = {100, 75, 50};
+    int bo = 100;
+    if (ms_occ) ms_occ[0] = bestt;
+    for (int k = 1; k < 3; ++k) {
+        c->occ_pct = occ[k];
+        float t_ms = 0.0f;
+        rc = time_once(bw, &t_ms);
+        c->occ_pct = 100;
+        if (rc != TREERAY_OK) return rc;
+        if (ms_occ) ms_occ[k] = t_ms;
+        if (t_ms < bestt) {
+            bestt = t_ms;
+            bo = occ[k];
+        }
+    }
     c->wpt = bw;
+    c->occ_pct = bo;
     if (best) *best = bw;
+    if (best_occ) *best_occ = bo;
+    {
+        std::lock_guard<std::mutex> lock(g_choice_mutex);
+        g_choice[shape_key(c)] = LaunchChoice{bw, bo};
+    }
     return TREERAY_OK;
 }
 
@@ -1493,6 +1552,7 @@ struct treeray_batch {
     std::vector<treeray_t> ctx;
     Group g[2];
     std::vector<void*> lastJ, lastF;
+    int wpt_thin = 3;  // team size of the thin-tile launch (3 or 4 warps)
     cudaGraphExec_t graph = nullptr;
     cudaStream_t gstream = nullptr;
     cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -1526,6 +1586,11 @@ treeray_status treeray_batch_create(const treeray_t* ctxs, int n_boxes, treeray_
         return TREERAY_ENOMEM;
     }
     b->ctx.assign(ctxs, ctxs + n_boxes);
+    for (int k = 0; k < n_boxes; ++k)  // thin boxes run the team size of the first one's choice
+        if (!(ctxs[k]->has_thick || ctxs[k]->force_thick)) {
+            b->wpt_thin = ctxs[k]->wpt == 3 ? 3 : 4;
+            break;
+        }
     for (int k = 0; k < n_boxes; ++k) {
         treeray_t c = ctxs[k];
         treeray_batch::Group& g = b->g[(c->has_thick || c->force_thick) ? 1 : 0];
@@ -1581,7 +1646,8 @@ treeray_status batch_launch(treeray_batch_t b, cudaStream_t s) {
         a.targets = nullptr;
         a.skip = nullptr;
         const treeray_status rc =
-            dispatch_team(c0, t == 1, g.periodic, 4, a, g.desc.data(), g.start.data(), (int)g.box.size(), g.max_lmax, s);
+            dispatch_team(c0, t == 1, g.periodic, t == 0 ? b->wpt_thin : 4, a, g.desc.data(), g.start.data(),
+                          (int)g.box.size(), g.max_lmax, s);
         if (rc != TREERAY_OK) return rc;
     }
     return TREERAY_OK;
@@ -1659,7 +1725,39 @@ treeray_status treeray_autotune(treeray_t c, int64_t n_sample, int* best_wpt, fl
         set_error("autotune: n_sample >= 1");
         return TREERAY_EINVAL;
     }
-    return autotune(c, n_sample, best_wpt, ms, (cudaStream_t)stream);
+    return autotune(c, n_sample, best_wpt, ms, nullptr, nullptr, (cudaStream_t)stream);
+}
+
+treeray_status treeray_autotune_launch(treeray_t c, int64_t n_sample, int* best_wpt, int* best_occupancy_pct,
+                                       float* ms_wpt, float* ms_occupancy, treeray_stream_t stream) {
+    if (!c || !c->built) {
+        set_error("autotune_launch: no tree");
+        return c ? TREERAY_ENOTBUILT : TREERAY_EINVAL;
+    }
+    if (n_sample < 1) {
+        set_error("autotune_launch: n_sample >= 1");
+        return TREERAY_EINVAL;
+    }
+    return autotune(c, n_sample, best_wpt, ms_wpt, best_occupancy_pct, ms_occupancy, (cudaStream_t)stream);
+}
+
+treeray_status treeray_get_launch_config(treeray_t c, int* wpt, int* occupancy_pct) {
+    if (!c) {
+        set_error("get_launch_config: null context");
+        return TREERAY_EINVAL;
+    }
+    if (wpt) *wpt = c->wpt;
+    if (occupancy_pct) *occupancy_pct = c->occ_pct;
+    return TREERAY_OK;
+}
+
+treeray_status treeray_set_occupancy(treeray_t c, int occupancy_pct) {
+    if (!c || occupancy_pct < 1 || occupancy_pct > 100) {
+        set_error("set_occupancy: occupancy_pct in 1..100");
+        return TREERAY_EINVAL;
+    }
+    c->occ_pct = occupancy_pct;
+    return TREERAY_OK;
 }
 
 }  // extern "C"

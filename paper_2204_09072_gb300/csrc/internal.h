@@ -139,6 +139,7 @@ struct treeray_ctx {
     int64_t launches = 0;  // kernels launched by this context
     int wpt = 4;           // warps per target team of the evaluate kernel (autotuned)
     int tau_q = 0;         // thin tiles: fixed-point optical depth in units of 2^-tau_q (0: float)
+    int occ_pct = 100;     // evaluate: resident teams per SM launched, % of the maximum (autotuned)
     int stack_limit = 0;   // test hook: cap on the walk stack's entries (0: the full stack)
     int alloc_fail_at = 0; // test hook: the n-th device allocation from now fails (0: none)
     int alloc_count = 0;
@@ -156,6 +157,8 @@ treeray_status dev_alloc(treeray_ctx* c, void** p, size_t bytes);
 // Team-stack scratch of the evaluate kernel large enough for any team size on a tree of
 // `lmax` levels below the root; never allocates while `s` is being captured.
 treeray_status reserve_eval_stacks(treeray_ctx* c, int lmax, cudaStream_t s);
+// Apply the autotuner's choice cached for a tree of this context's shape, if any.
+void apply_cached_launch_choice(treeray_ctx* c);
 treeray_status build_tree(treeray_ctx* c, const treeray_grid* g, const float* rho, const float* Td,
                           const float* kappa, int n_stars, const double* star_pos,
                           const double* star_lum, cudaStream_t s);

@@ -370,6 +370,28 @@ def batch_of_boxes(count: int = 64, seed: int = 5, **pover):
     return out
 
 
+def batch_of_small_boxes(count: int = 512, seed: int = 9, **pover):
+    """Many small independent boxes: finest resolution 16 or 32 per axis, 1 or 2 AMR levels
+    (base grid >= 8 cells), own density seed, grey kappa ~ U[1, 10] (the batch workload in
+    which launch overheads and tails matter)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    while len(out) < count:
+        finest = int(rng.choice([16, 32]))
+        levels = int(rng.integers(1, 3))
+        kap = float(rng.uniform(1.0, 10.0))
+        out.append(amr_random(finest, levels, seed=int(rng.integers(1 << 30)), kappa=kap, **pover))
+    return out
+
+
+def batch_of_tiny_boxes(count: int = 1024, seed: int = 10, **pover):
+    """Many tiny independent boxes of 8^3 cells (512 targets each, too few to fill the GPU
+    in a launch of their own), own density seed, grey kappa ~ U[1, 10]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return [amr_random(8, 1, seed=int(rng.integers(1 << 30)), kappa=float(rng.uniform(1.0, 10.0)), **pover)
+            for _ in range(count)]
+
+
 def ionising_field(w: Workload, q_per_lsun: float = 1e44, e_photon_ev: float = 18.0,
                    sigma_d: float = 1.5e-21) -> Workload:
     """Attach a synthetic ionising photon flux and the UV heating it implies.

@@ -16,13 +16,16 @@ def _boxes():
             synth.point_source(8, kappa0=2.0, nbins=16)]
 
 
-@pytest.mark.parametrize("use_graph", [False, True])
-def test_batch_matches_single_and_oracle(orc, use_graph):
+@pytest.mark.parametrize("use_graph,thin_wpt", [(False, 4), (True, 4), (True, 3)])
+def test_batch_matches_single_and_oracle(orc, use_graph, thin_wpt):
+    """Thin boxes run teams of the first thin box's size (3 or 4 warps), thick boxes 4."""
     import torch
 
     import paper_2204_09072_gb300 as tr
     ws = _boxes()
     ctxs = [build_ctx(w)[0] for w in ws]
+    for c in ctxs:
+        c.set_warps_per_target(thin_wpt)
     singles = [evaluate(c) for c in ctxs]
     b = tr.Batch(ctxs)
     Js = [torch.empty(c.leaf_count, dtype=torch.float32, device="cuda:0") for c in ctxs]
