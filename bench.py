@@ -703,6 +703,20 @@ def _cloud(n, seed, sigma, n_stars, npix, uv_heating=False):
     return w
 
 
+def _clump(n, seed, npix):
+    """The Gaussian clump (config 1) with a seeded gas temperature, a Planck-mean opacity
+    (so that T_d feeds back on the field) and no stars or ionising flux."""
+    import synth
+    w = synth.gaussian_clump(n, npix=npix)
+    w.params = dict(w.params, kappa_model=1)
+    w = synth.with_gas(w, seed=seed, tgas_lo=10.0, tgas_hi=100.0)
+    w.phi = np.zeros(w.n_leaves, np.float32)
+    w.heat_extra = np.zeros(w.n_leaves, np.float32)
+    w.star_pos = np.zeros((0, 3))
+    w.star_lum = np.zeros(0)
+    return w
+
+
 def run_warmstart(args):
     import numpy as np  # noqa: F401  (used by _cloud)
     """Learned warm start of the dust-temperature fixed point.
@@ -733,8 +747,10 @@ def run_warmstart(args):
     solves = [(128, 101, 1.5, 1), (128, 102, 2.0, 2), (128, 103, 1.5, 4), (128, 104, 2.0, 3), (128, 105, 2.0, 4),
               (128, 106, 2.0, 4), (128, 107, 1.5, 2)]
     solves += [(args.warm_n, 200 + k, 2.0, 4) for k in range(args.warm_train_big)]
+    # the 32^3 Gaussian clump (sigma 0: no turbulence) with gas temperatures of several seeds
+    solves += [(32, 300 + k, 0.0, 0) for k in range(4)]
     for k, (nn, seed, sig, ns) in enumerate(solves):
-        w = _cloud(nn, seed, sig, ns, args.npix)
+        w = _cloud(nn, seed, sig, ns, args.npix) if sig > 0 else _clump(nn, seed, args.npix)
         c, tg, he, ph = make(w)
         c.refresh(torch.full((w.n_leaves,), args.warm_feature_td, device=dev))
         X = c.features(tg, phi=ph)[0].clone()
@@ -756,46 +772,53 @@ def run_warmstart(args):
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
 
-    w = _cloud(args.warm_n, 777, 2.0, 4, args.npix)
-    c, tg, he, ph = make(w)
-    td0 = torch.as_tensor(w.td, device=dev)
-    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    td_plain = td0.clone()
-    torch.cuda.synchronize()
-    e[0].record()
-    it_plain = c.fixed_point(tg, td_plain, heat_extra=he, tol=1e-4, max_iter=60, raise_on_noconv=False)
-    e[1].record()
-    torch.cuda.synchronize()
-    td_warm = td0.clone()
-    torch.cuda.synchronize()
-    e[2].record()
-    c.refresh(torch.full_like(td0, args.warm_feature_td))
-    Xw = c.features(tg, phi=ph)[0]
-    c.warm_start(net, Xw.reshape(-1).contiguous(), td_warm)
-    guess = td_warm.clone()
-    it_warm = c.fixed_point(tg, td_warm, heat_extra=he, tol=1e-4, max_iter=60, raise_on_noconv=False)
-    e[3].record()
-    torch.cuda.synchronize()
-    c.check()
-    ms_plain = e[0].elapsed_time(e[1])
-    ms_warm = e[2].elapsed_time(e[3])
-    gerr = (guess / td_plain - 1).abs()
-    ferr = (td_warm / td_plain - 1).abs()
-    gq = torch.quantile(gerr[torch.randperm(gerr.numel(), device=gerr.device)[:1 << 22]],
-                        torch.tensor([0.5, 0.9, 0.99, 0.999], device=gerr.device)).tolist()
+    per_seed = []
+    for seed in args.warm_test_seeds:
+        w = _cloud(args.warm_n, seed, 2.0, 4, args.npix)
+        c, tg, he, ph = make(w)
+        td0 = torch.as_tensor(w.td, device=dev)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        td_plain = td0.clone()
+        torch.cuda.synchronize()
+        e[0].record()
+        it_plain = c.fixed_point(tg, td_plain, heat_extra=he, tol=1e-4, max_iter=60, raise_on_noconv=False)
+        e[1].record()
+        torch.cuda.synchronize()
+        td_warm = td0.clone()
+        torch.cuda.synchronize()
+        e[2].record()
+        c.refresh(torch.full_like(td0, args.warm_feature_td))
+        Xw = c.features(tg, phi=ph)[0]
+        c.warm_start(net, Xw.reshape(-1).contiguous(), td_warm)
+        guess = td_warm.clone()
+        it_warm = c.fixed_point(tg, td_warm, heat_extra=he, tol=1e-4, max_iter=60, raise_on_noconv=False)
+        e[3].record()
+        torch.cuda.synchronize()
+        c.check()
+        ms_plain = e[0].elapsed_time(e[1])
+        ms_warm = e[2].elapsed_time(e[3])
+        gerr = (guess / td_plain - 1).abs()
+        ferr = (td_warm / td_plain - 1).abs()
+        gq = torch.quantile(gerr[torch.randperm(gerr.numel(), device=gerr.device)[:1 << 22]],
+                            torch.tensor([0.5, 0.9, 0.99, 0.999], device=gerr.device)).tolist()
+        per_seed.append({
+            "seed": seed, "iterations_plain": it_plain, "iterations_warm": it_warm,
+            "evaluations_plain": it_plain, "evaluations_warm": it_warm + 1,
+            "evaluation_ratio": it_plain / (it_warm + 1), "iteration_ratio": it_plain / max(it_warm, 1),
+            "ms_fixed_point_plain": ms_plain, "ms_warm_total": ms_warm, "speedup": ms_plain / ms_warm,
+            "guess_rel_err_p50_p90_p99_p999": gq, "guess_rel_err_max": float(gerr.max()),
+            "final_rel_diff_max": float(ferr.max())})
+        c.close()
     print(json.dumps({
-        "workload": f"learned warm start, test cloud {args.warm_n}^3 sigma_lnrho 2, 4 stars, ionising flux "
+        "workload": f"learned warm start, test clouds {args.warm_n}^3 sigma_lnrho 2, 4 stars, ionising flux "
                     f"as a feature (no UV dust heating); features at uniform T_d = {args.warm_feature_td} K",
         "train_samples": int(y.numel()), "train_solves_iterations": its, "train_steps": len(hist) + len(hist2),
         "train_loss_first_last": [float(hist[:20].mean()), float(hist2[-50:].mean())],
-        "s_training_data": t_data, "s_training": t_train,
-        "iterations_plain": it_plain, "iterations_warm": it_warm, "warm_extra_evaluations": 1,
-        "iteration_ratio": it_plain / max(it_warm, 1),
-        "evaluation_ratio": it_plain / (it_warm + 1),
-        "ms_fixed_point_plain": ms_plain, "ms_warm_total": ms_warm, "speedup": ms_plain / ms_warm,
-        "guess_rel_err_max": float(gerr.max()), "guess_rel_err_median": float(gerr.median()),
-        "guess_rel_err_p50_p90_p99_p999": gq, "training_solves": [list(x) for x in solves],
-        "final_rel_diff_max": float(ferr.max())}))
+        "s_training_data": t_data, "s_training": t_train, "training_solves": [list(x) for x in solves],
+        "evaluations_note": "warm path = feature pass (one evaluation) + fixed-point iterations",
+        "per_seed": per_seed,
+        "evaluation_ratio_min": min(p["evaluation_ratio"] for p in per_seed),
+        "final_rel_diff_max": max(p["final_rel_diff_max"] for p in per_seed)}))
 
 
 def run_amr_core(args):
@@ -983,6 +1006,7 @@ def main():
     ap.add_argument("--sweep", action="store_true", help="N_pix x segments sweep with the autotuner")
     ap.add_argument("--warmstart", action="store_true", help="learned warm start of the T_d fixed point")
     ap.add_argument("--warm-n", type=int, default=256)
+    ap.add_argument("--warm-test-seeds", type=int, nargs="+", default=[777, 778, 779])
     ap.add_argument("--train-steps", type=int, default=4000)
     ap.add_argument("--warm-feature-td", type=float, default=20.0,
                     help="uniform T_d of the feature pass (training and test)")
