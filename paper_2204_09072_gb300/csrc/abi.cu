@@ -237,8 +237,8 @@ treeray_status treeray_create(const treeray_params* p, treeray_t* out) {
         return TREERAY_EINVAL;
     }
     *out = nullptr;
-    if (p->npix != 12 && p->npix != 48 && p->npix != 192) {
-        set_error("npix must be 12, 48 or 192");
+    if (p->npix != 12 && p->npix != 48 && p->npix != 192 && p->npix != 768) {
+        set_error("npix must be 12, 48, 192 or 768");
         return TREERAY_EINVAL;
     }
     if (p->nbins < 1 || p->nbins > kMaxBins) {
@@ -310,6 +310,7 @@ treeray_status treeray_destroy(treeray_t c) {
     if (c->fp_F) cudaFree(c->fp_F);
     if (c->fp_flags) cudaFree(c->fp_flags);
     if (c->stack_scr) cudaFree(c->stack_scr);
+    if (c->gtile) cudaFree(c->gtile);
     if (c->orient) cudaFree(c->orient);
     if (c->fp_stream) cudaStreamDestroy(c->fp_stream);
     for (cudaEvent_t e : c->fp_ev)

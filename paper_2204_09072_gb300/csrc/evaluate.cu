@@ -66,6 +66,8 @@ struct __align__(16) EvalArgs {
     unsigned long long* stats;  // accepted-list mode: totals of visits, accepted, entries
     const int* skip;            // fixed-point mode: return at once when *skip != 0
     int* stack;                 // team stacks: stack_cap ints per block of the launch
+    float* gtile;               // 768 rays: the teams' (segment x ray) tiles in global memory
+    int64_t gtile_stride;       // floats per team in gtile (tile, then merge flags)
     int acc_cap;
     int64_t n;
     int64_t nleaves;
@@ -423,6 +425,42 @@ __global__ void __launch_bounds__(256) k_walk_list(EvalArgs a) {
 // the static shared memory and the per-block reservation (measured: 8 teams at 192)
 __host__ __device__ constexpr int owner_cap(bool thick) { return thick ? 160 : 256; }
 
+// 768 rays (N_side 8): a (segment x ray) tile of 20 segments takes 123 KB thin and 369 KB
+// thick, so each team keeps it in a slice of global memory (L2-resident for the teams of one
+// launch) instead of shared memory; deposits are L2 reductions (red.global.add.f32, native
+// for FP32, unlike shared-memory FP32 adds) and the tile is read through L2 (ld.global.cg)
+// after the team barrier. Teams of 8 warps, owner bytes for 2048 entries per warp pass.
+template <int NPIX>
+struct GlobalTile {
+    static constexpr bool on = NPIX > 192;
+};
+__host__ __device__ constexpr int owner_cap_for(int npix, bool thick) { return npix > 192 ? 2048 : owner_cap(thick); }
+template <bool G>
+__device__ __forceinline__ float tld(const float* p) {
+    if constexpr (G) return __ldcg(p);
+    else return *p;
+}
+template <bool G>
+__device__ __forceinline__ void tst(float* p, float v) {
+    if constexpr (G) __stcg(p, v);
+    else *p = v;
+}
+template <bool G>
+__device__ __forceinline__ unsigned tldu(const unsigned* p) {
+    if constexpr (G) return __ldcg(p);
+    else return *p;
+}
+template <bool G>
+__device__ __forceinline__ unsigned long long tld64(const unsigned long long* p) {
+    if constexpr (G) return __ldcg(p);
+    else return *p;
+}
+template <bool G>
+__device__ __forceinline__ void tst64(unsigned long long* p, unsigned long long v) {
+    if constexpr (G) __stcg(p, v);
+    else *p = v;
+}
+
 // Row stride of the (segment x ray) tile in shared memory: a few words more than the rays,
 // so that the same ray in nearby segments (a common pair among the entries of one deposit
 // pass) falls into different banks (48 rays: 48 x 2 = 0 mod 32 banks). Thin tiles: 4 more
@@ -552,7 +590,8 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
     //         per warp entry owners u8[owner_cap] (16-byte aligned parts)
     // The team's stack of child groups is this block's slice of a global scratch array:
     // it stays in L1, and leaving it out of shared memory lets more teams share an SM.
-    float* tL = reinterpret_cast<float*>(smem);
+    constexpr bool GT = GlobalTile<NPIX>::on;
+    float* tL = GT ? a.gtile + (size_t)blockIdx.x * a.gtile_stride : reinterpret_cast<float*>(smem);
     float* tA = tL + cells;
     unsigned* tT = reinterpret_cast<unsigned*>(tA);  // fixed-point tiles: segment optical depth
     constexpr bool FIXT = FixedTau<THICK, GENERAL>::on;
@@ -560,11 +599,13 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
     float* tAk = tLk + cells;
     float* tVk = tAk + cells;
     float* tQk = tVk + cells;
-    unsigned long long* flags = reinterpret_cast<unsigned long long*>(smem + align16((size_t)nq * cells * 4));
+    unsigned long long* flags = reinterpret_cast<unsigned long long*>(
+        (GT ? reinterpret_cast<unsigned char*>(tL) : smem) + align16((size_t)nq * cells * 4));
     // each entry's node data comes from the owner lane by shuffles (fewer shared-memory
     // operations and registers than a per-warp node buffer, and smaller thick teams)
-    constexpr int OCAP = owner_cap(THICK);
-    unsigned char* owner = smem + align16(align16((size_t)nq * cells * 4) + (THICK ? NPIX * 8 : 0)) + warp * OCAP;
+    constexpr int OCAP = owner_cap_for(NPIX, THICK);
+    unsigned char* owner =
+        smem + (GT ? 0 : align16(align16((size_t)nq * cells * 4) + (THICK ? NPIX * 8 : 0))) + warp * OCAP;
     const int stack_cap = a.stack_cap;
     int* stack = a.stack + (size_t)blockIdx.x * stack_cap;
     __shared__ int s_sp, s_overflow;
@@ -628,9 +669,9 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
         const float* R2 = A.R2 + (int64_t)tl * nb;
         const float2 lp = __ldg(A.lvlp + tl);
 
-        for (int i = tid; i < nq * cells; i += NT) tL[i] = 0.0f;
+        for (int i = tid; i < nq * cells; i += NT) tst<GT>(tL + i, 0.0f);
         if (THICK)
-            for (int h = tid; h < NPIX; h += NT) flags[h] = 0ull;
+            for (int h = tid; h < NPIX; h += NT) tst64<GT>(flags + h, 0ull);
         if (tid == 0) {
             s_overflow = 0;
             s_sp = 0;
@@ -913,14 +954,15 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
             }
             const float w = 1.0f / NPIX;
             for (int h = tid; h < NPIX; h += NT) {
-                tL[h] += w * v0.x;
-                if constexpr (!FIXT) tA[h] += w * v0.y;  // fixed-point tiles: segment 0 holds no depth
+                tst<GT>(tL + h, tld<GT>(tL + h) + w * v0.x);
+                // fixed-point tiles: segment 0 holds no depth
+                if constexpr (!FIXT) tst<GT>(tA + h, tld<GT>(tA + h) + w * v0.y);
                 if (THICK && v1.w > 0.0f) {
-                    tLk[h] += w * v1.y;
-                    tAk[h] += v1.z;
-                    tVk[h] += w * v1.w;
-                    tQk[h] += w * v1.w;
-                    flags[h] |= fmask;
+                    tst<GT>(tLk + h, tld<GT>(tLk + h) + w * v1.y);
+                    tst<GT>(tAk + h, tld<GT>(tAk + h) + v1.z);
+                    tst<GT>(tVk + h, tld<GT>(tVk + h) + w * v1.w);
+                    tst<GT>(tQk + h, tld<GT>(tQk + h) + w * v1.w);
+                    tst64<GT>(flags + h, tld64<GT>(flags + h) | fmask);
                 }
             }
         }
@@ -935,29 +977,29 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
         auto segments = [&](int h, int i0, int i1, float& Fp, float& thi, float& tlo, float& ek) {
             for (int i = i0; i < i1; ++i) {
                 const int ci = i * ROW + h;
-                const float Lth = tL[ci];
+                const float Lth = tld<GT>(tL + ci);
                 const float R2i = __ldg(R2 + i);
                 const float inv_R2 = 1.0f / R2i;
                 float Ath, tth;
                 if constexpr (FIXT) {
-                    Ath = (float)tT[ci];
+                    Ath = (float)tldu<GT>(tT + ci);
                     tth = Ath * (1.0f / A.tau_scale);  // a power of two: exact scaling
                 } else {
-                    Ath = tA[ci];
+                    Ath = tld<GT>(tA + ci);
                     tth = i == 0 ? 0.0f : Ath * inv_R2 * (1.0f / omega);
                 }
-                const float Vk = THICK ? tVk[ci] : 0.0f;
+                const float Vk = THICK ? tld<GT>(tVk + ci) : 0.0f;
                 if (Lth == 0.0f && Ath == 0.0f && Vk == 0.0f) continue;  // empty segment
                 float f = 0.0f, Fk = 0.0f, Akv = 0.0f, tk = 0.0f;
                 if constexpr (THICK) {
                     if (Vk > 0.0f) {
                         const float cb = cbrtf(Vk);
-                        float wk = (tQk[ci] / Vk) * (cb * cb) * inv_R2;
+                        float wk = (tld<GT>(tQk + ci) / Vk) * (cb * cb) * inv_R2;
                         wk = fminf(wk, omega);
                         f = wk / omega;
-                        Akv = tAk[ci];
+                        Akv = tld<GT>(tAk + ci);
                         tk = (i == 0 || wk == 0.0f) ? 0.0f : Akv / (wk * R2i);
-                        Fk = wk * tLk[ci] / Vk;
+                        Fk = wk * tld<GT>(tLk + ci) / Vk;
                     }
                 }
                 const float g = tth < 1e-4f ? 1.0f : -expm1f(-tth) / tth;
@@ -1001,9 +1043,9 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
                 segments(h, i0, i1, Fp, thi, tlo, ek);
                 // every part has >= 2 segments: its first two cells of ray h, read only by
                 // this thread, now hold (Fp, thi) and tlo
-                tL[i0 * ROW + h] = Fp;
-                tA[i0 * ROW + h] = thi;
-                tL[(i0 + 1) * ROW + h] = tlo;
+                tst<GT>(tL + i0 * ROW + h, Fp);
+                tst<GT>(tA + i0 * ROW + h, thi);
+                tst<GT>(tL + (i0 + 1) * ROW + h, tlo);
             }
             __syncthreads();
             if (tid < NPIX) {
@@ -1012,27 +1054,27 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
                 for (int p = 0; p < P; ++p) {
                     const int i0 = p * nb / P;
                     const float eps = expf(-chi) * (1.0f - clo);
-                    Fh += eps * tL[i0 * ROW + h];
-                    add_pair(chi, clo, tA[i0 * ROW + h], tL[(i0 + 1) * ROW + h]);
+                    Fh += eps * tld<GT>(tL + i0 * ROW + h);
+                    add_pair(chi, clo, tld<GT>(tA + i0 * ROW + h), tld<GT>(tL + (i0 + 1) * ROW + h));
                 }
                 ray_done(h, Fh, chi + clo);
             }
         } else {
             for (int h = tid; h < NPIX; h += NT) {
                 if (THICK) {
-                    const unsigned long long fl = flags[h];
+                    const unsigned long long fl = tld64<GT>(flags + h);
                     if (fl)
                         for (int i = nb - 2; i >= 0; --i) {
                             if (!((fl >> i) & 1ull)) continue;
                             const int c0 = i * ROW + h, c1 = (i + 1) * ROW + h;
                             const float T = __ldg(R2 + i) / __ldg(R2 + i + 1);
-                            tL[c0] += T * tL[c1];
-                            tA[c0] += T * tA[c1];
-                            tQk[c0] += T * tQk[c1];
-                            tLk[c0] += tLk[c1];
-                            tAk[c0] += tAk[c1];
-                            tVk[c0] += tVk[c1];
-                            tL[c1] = tA[c1] = tQk[c1] = tLk[c1] = tAk[c1] = tVk[c1] = 0.0f;
+                            tst<GT>(tL + c0, tld<GT>(tL + c0) + T * tld<GT>(tL + c1));
+                            tst<GT>(tA + c0, tld<GT>(tA + c0) + T * tld<GT>(tA + c1));
+                            tst<GT>(tQk + c0, tld<GT>(tQk + c0) + T * tld<GT>(tQk + c1));
+                            tst<GT>(tLk + c0, tld<GT>(tLk + c0) + tld<GT>(tLk + c1));
+                            tst<GT>(tAk + c0, tld<GT>(tAk + c0) + tld<GT>(tAk + c1));
+                            tst<GT>(tVk + c0, tld<GT>(tVk + c0) + tld<GT>(tVk + c1));
+                            for (float* q : {tL, tA, tQk, tLk, tAk, tVk}) tst<GT>(q + c1, 0.0f);
                         }
                 }
                 float Fh = 0.0f, thi = 0.0f, tlo = 0.0f, ek = 1.0f;
@@ -1144,6 +1186,28 @@ treeray_status launch_persistent(treeray_ctx* c, K kern, size_t per_warp, int ma
     return TREERAY_OK;
 }
 
+// global-memory tiles of one launch are kept within this many bytes (L2 129 MB)
+constexpr size_t kGlobalTileBudget = (size_t)96 << 20;
+
+treeray_status reserve_global_tiles(treeray_ctx* c, size_t bytes, cudaStream_t s) {
+    if (c->gtile_bytes >= bytes) return TREERAY_OK;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    TR_CUDA(cudaStreamIsCapturing(s, &cs));
+    if (cs != cudaStreamCaptureStatusNone) {
+        set_error("evaluate: 768-ray tiles must be reserved before stream capture (evaluate once first)");
+        return TREERAY_EINVAL;
+    }
+    if (c->gtile) {
+        TR_CUDA(cudaFree(c->gtile));  // waits for launches that may still use it
+        c->gtile = nullptr;
+        c->gtile_bytes = 0;
+    }
+    const treeray_status rc = dev_alloc(c, (void**)&c->gtile, bytes);
+    if (rc != TREERAY_OK) return rc;
+    c->gtile_bytes = bytes;
+    return TREERAY_OK;
+}
+
 size_t stack_bytes_for(int wpt, int lmax, int blocks) {
     // the team stack holds at most one batch of pushes (32 WPT groups) per level
     return (size_t)blocks * (size_t)(32 * wpt * (lmax + 1) + 64) * sizeof(int);
@@ -1157,8 +1221,9 @@ treeray_status launch_team(treeray_ctx* c, const EvalArgs& a, const EvalArgs* bo
     EvalArgs b = a;
     b.stack_cap = (int)(stack_bytes_for(WPT, layout_lmax, 1) / sizeof(int));
     if (c->stack_limit > 0) b.stack_cap = std::min(b.stack_cap, c->stack_limit);  // test hook
-    const size_t smem = align16(align16((size_t)nq * a.nbins * tile_row(NPIX, THICK) * 4) + (THICK ? NPIX * 8 : 0)) +
-                        (size_t)WPT * owner_cap(THICK);
+    constexpr bool GT = GlobalTile<NPIX>::on;
+    const size_t tile_bytes = align16(align16((size_t)nq * a.nbins * tile_row(NPIX, THICK) * 4) + (THICK ? NPIX * 8 : 0));
+    const size_t smem = (GT ? 0 : tile_bytes) + (size_t)WPT * owner_cap_for(NPIX, THICK);
     int smem_optin = 0, sms = 0;
     TR_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
     TR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
@@ -1178,6 +1243,12 @@ treeray_status launch_team(treeray_ctx* c, const EvalArgs& a, const EvalArgs* bo
         // the autotuner may launch fewer resident teams than fit (occ_pct of them, >= 1 per SM)
         const int use = std::max(1, (per_sm * c->occ_pct + 50) / 100);
         blocks = std::max<int64_t>(1, std::min<int64_t>((int64_t)use * sms, n));
+        if constexpr (GT) {  // global tiles: as many teams as keep them within the L2 budget
+            blocks = std::max<int64_t>(1, std::min<int64_t>(
+                                              blocks, std::max<int64_t>(sms, (int64_t)(kGlobalTileBudget / tile_bytes))));
+            const treeray_status rg = reserve_global_tiles(c, (size_t)blocks * tile_bytes, s);
+            if (rg != TREERAY_OK) return rg;
+        }
         if (c->stack_scr_bytes < stack_bytes_for(WPT, layout_lmax, (int)blocks)) {
             const treeray_status rc = reserve_eval_stacks(c, layout_lmax, s);
             if (rc != TREERAY_OK) return rc;
@@ -1190,6 +1261,8 @@ treeray_status launch_team(treeray_ctx* c, const EvalArgs& a, const EvalArgs* bo
         auto kern = k_evaluate<NPIX, THICK, WPT, GENERAL>;
         if ((rc = grid_for(kern, a.n, blocks)) != TREERAY_OK) return rc;
         b.stack = c->stack_scr;
+        b.gtile = c->gtile;
+        b.gtile_stride = (int64_t)(tile_bytes / sizeof(float));
         TR_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), s));
         kern<<<(int)blocks, WPT * 32, smem, s>>>(b);
         c->launches += 1;
@@ -1227,6 +1300,13 @@ treeray_status launch_team(treeray_ctx* c, const EvalArgs& a, const EvalArgs* bo
 template <int NPIX, bool THICK, bool GENERAL>
 treeray_status launch_wpt(treeray_ctx* c, int wpt, const EvalArgs& a, const EvalArgs* boxes,
                           const int64_t* box_start, int nbox, int layout_lmax, cudaStream_t s) {
+    if constexpr (GlobalTile<NPIX>::on) {  // 768 rays: teams of 8 warps, no batches
+        if (boxes) {
+            set_error("batch: 768 rays are evaluated one box at a time");
+            return TREERAY_EINVAL;
+        }
+        return launch_team<NPIX, THICK, 8, GENERAL, false>(c, a, nullptr, nullptr, 0, layout_lmax, s);
+    } else {
     // batches run teams of 3 warps (thin tiles, when that is the team size asked for) or 4
     if (boxes) {
         if constexpr (!THICK)
@@ -1240,6 +1320,7 @@ treeray_status launch_wpt(treeray_ctx* c, int wpt, const EvalArgs& a, const Eval
             return launch_team<NPIX, THICK, 4, GENERAL, false>(c, a, nullptr, nullptr, 0, layout_lmax, s);
         case 8: return launch_team<NPIX, THICK, 8, GENERAL, false>(c, a, nullptr, nullptr, 0, layout_lmax, s);
         default: return launch_team<NPIX, THICK, 4, GENERAL, false>(c, a, nullptr, nullptr, 0, layout_lmax, s);
+    }
     }
 }
 
@@ -1263,8 +1344,9 @@ treeray_status dispatch_team(treeray_ctx* c, bool thick, bool periodic, int wpt,
         case 12: return launch_kind<12>(c, thick, periodic, wpt, a, boxes, box_start, nbox, layout_lmax, s);
         case 48: return launch_kind<48>(c, thick, periodic, wpt, a, boxes, box_start, nbox, layout_lmax, s);
         case 192: return launch_kind<192>(c, thick, periodic, wpt, a, boxes, box_start, nbox, layout_lmax, s);
+        case 768: return launch_kind<768>(c, thick, periodic, wpt, a, boxes, box_start, nbox, layout_lmax, s);
     }
-    set_error("evaluate: npix must be 12, 48 or 192");
+    set_error("evaluate: npix must be 12, 48, 192 or 768");
     return TREERAY_EINVAL;
 }
 

@@ -131,6 +131,8 @@ struct treeray_ctx {
     cudaEvent_t fp_ev[2] = {nullptr, nullptr};
     int* stack_scr = nullptr;    // evaluate: team stacks (global scratch, grow-only)
     size_t stack_scr_bytes = 0;
+    float* gtile = nullptr;      // evaluate at 768 rays: the teams' tiles (global scratch, grow-only)
+    size_t gtile_bytes = 0;
     // several HEALPix orientations (Sec. 7.6)
     std::vector<double> rot;     // [k][9] row-major rotations; empty: the single unturned ray set
     uint8_t* orient = nullptr;   // device [orient_n]: orientation of each leaf (caller order)

@@ -177,7 +177,7 @@ bool build_alpha_table(HostTables& t, double theta, int lmax, bool amr, bool col
     int64_t D = (int64_t)std::ceil(8.0 * reach) + 1 + extra;
     const int64_t cap = 8 * ((int64_t)1 << lmax) + 1 + extra;
     D = std::min(D, cap);
-    D = std::min<int64_t>(D, 128 + extra);
+    D = std::min<int64_t>(D, 160 + extra);  // covers the ray-matched angle at 768 rays (D = 133)
     t.D = (int)D;
     const auto key = std::make_tuple(t.npix, t.s, theta, D, amr, col, rot);
     {
