@@ -821,6 +821,62 @@ def run_warmstart(args):
         "final_rel_diff_max": max(p["final_rel_diff_max"] for p in per_seed)}))
 
 
+def run_rays_study(args):
+    """The paper's ray-count study (Sec. 7.6) on the collapsing-core AMR grid: evaluate cost at
+    48, 192 and 768 rays with the opening angle matched to the ray size (theta = sqrt(4 pi /
+    N_pix): the paper opens nodes further as the rays get finer), and the residual of the
+    radiation temperature T_J = (pi J / sigma)^(1/4) (eq. radtemp) of 48 and 192 rays against
+    768 rays, as mean +- standard deviation over the cells of the central half of the domain
+    (the half-width cube) and of the whole domain. Same T_d field for all ray counts (T_d =
+    20 K inside, as generated). Prints one JSON line."""
+    import numpy as np
+    import torch
+
+    import paper_2204_09072_gb300 as tr
+    import synth
+    dev = torch.device("cuda:0")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    w0 = synth.amr_core() if args.rays_workload == "amr_core" else synth.turbulent_cloud(128)
+    sig = 5.670374419e-5
+    res, T = {}, {}
+    for npix in (48, 192, 768):
+        w = w0
+        w.params = dict(w0.params, npix=npix, theta=-1.0)
+        t0 = time.perf_counter()
+        r = time_evaluate(tr, torch, w, dev, args.steps, flush)
+        r["s_setup_and_timing"] = time.perf_counter() - t0
+        ctx = tr.Context(w.params)
+        ctx.build(w.box_cm, torch.as_tensor(w.rho, device=dev), torch.as_tensor(w.td, device=dev),
+                  n=w.uniform_n, blocks=w.blocks, star_pos=w.star_pos, star_lum=w.star_lum)
+        n = w.n_leaves
+        J = torch.empty(n, dtype=torch.float32, device=dev)
+        F = torch.empty(3 * n, dtype=torch.float64, device=dev)
+        ctx.evaluate(J, F)
+        ctx.check()
+        T[npix] = (np.pi * J.double().cpu().numpy() / sig) ** 0.25
+        ctx.close()
+        res[npix] = r
+    cen = (w0.leaf_ijk.astype(np.float64) + 0.5) / (2.0 ** w0.leaf_level)[:, None]  # in box units
+    half = (np.abs(cen - 0.5) < 0.25).all(axis=1)
+    out = {}
+    for npix in (48, 192):
+        d = T[npix] / T[768] - 1
+        out[f"residual_{npix}_vs_768"] = {
+            "half_domain_mean_std_pct": [100 * float(d[half].mean()), 100 * float(d[half].std())],
+            "full_domain_mean_std_pct": [100 * float(d.mean()), 100 * float(d.std())]}
+    base = res[48]["ms"]
+    print(json.dumps({"workload": f"{args.rays_workload}, ray-matched opening angle", "cells": int(w0.n_leaves),
+                      "cells_half_domain": int(half.sum()),
+                      "ms_evaluate": {k: v["ms"] for k, v in res.items()},
+                      "cost_ratio_48_192_768": [1.0, res[192]["ms"] / base, res[768]["ms"] / base],
+                      "paper_cost_ratio": [1.0, 4.39, 15.98],
+                      "walk": {k: v["walk"] for k, v in res.items()},
+                      "warps_per_target": {k: v["warps_per_target"] for k, v in res.items()},
+                      "paper_residuals_pct": {"48_half": [-15.4, 14.0], "192_half": [-3.77, 5.31],
+                                              "48_full": [-31.0, 17.9], "192_full": [-13.2, 10.5]},
+                      **out}))
+
+
 def run_amr_core(args):
     """Collapsing-core AMR grid (~1.9 M leaves of 8^3 blocks on levels 5-9, 10 stars of
     1e2-1e5 Lsun, optically thick centre): evaluation throughput with the step as in the
@@ -1003,6 +1059,9 @@ def main():
     ap.add_argument("--batch64", action="store_true", help="64-box AMR batch: batched vs per-box launches")
     ap.add_argument("--batch512", action="store_true", help="512 small boxes: batched vs per-box launches")
     ap.add_argument("--batch-tiny", action="store_true", help="1024 boxes of 8^3: batched vs per-box launches")
+    ap.add_argument("--rays-study", action="store_true",
+                    help="cost and T_J residuals at 48 / 192 / 768 rays, ray-matched opening angle")
+    ap.add_argument("--rays-workload", default="amr_core", choices=["amr_core", "turb128"])
     ap.add_argument("--sweep", action="store_true", help="N_pix x segments sweep with the autotuner")
     ap.add_argument("--warmstart", action="store_true", help="learned warm start of the T_d fixed point")
     ap.add_argument("--warm-n", type=int, default=256)
@@ -1024,6 +1083,8 @@ def main():
         args.warmup = 3
     if args.profile_evaluate:
         run_profile(args)
+    elif args.rays_study:
+        run_rays_study(args)
     elif args.batch64 or args.batch512 or args.batch_tiny:
         run_batch64(args)
     elif args.sweep:
