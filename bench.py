@@ -932,7 +932,7 @@ def run_amr_core(args):
     ms_step = statistics.mean(e[0].elapsed_time(e[3]) for e in ev)
     ms_eval = statistics.mean(e[1].elapsed_time(e[2]) for e in ev)
     visits, acc, ent = (int(x) for x in tot)
-    alg = BYTES_VISIT * visits + BYTES_ACCEPT * (acc - n) + BYTES_ENTRY * ent + BYTES_TARGET * n
+    alg = node_stream_bytes(visits, acc)
     peak, kind = measured_peak()
     # plain GPU fixed point (graph of unrolled iterations)
     ctx.refresh(td0)
@@ -950,24 +950,35 @@ def run_amr_core(args):
         "s_generate": t_gen, "warps_per_target": best, "autotune_ms_wpt2_3_4_8": tune,
         "ms_per_step": ms_step, "ms_evaluate": ms_eval,
         "ray_evals_per_s": n * npix / (ms_step * 1e-3), "ray_evals_per_s_evaluate": n * npix / (ms_eval * 1e-3),
-        "roofline": {"bound": "hbm", "achieved": alg / (ms_eval * 1e-3) / 1e9, "peak": peak, "peak_kind": kind,
-                     "frac": alg / (ms_eval * 1e-3) / 1e9 / peak, "algorithmic_bytes_per_launch": alg},
+        "roofline": {"bound": "l1", "achieved": alg / (ms_eval * 1e-3) / 1e9, "peak": peak, "peak_kind": kind,
+                     "frac": alg / (ms_eval * 1e-3) / 1e9 / peak, "algorithmic_bytes_per_launch": alg,
+                     "bytes_model": f"{NODE_BYTES_VISIT} B per visited node + {NODE_BYTES_ACCEPT} B per accepted node"},
         "walk": {"visits": visits, "accepted": acc, "alpha_entries": ent},
         "fixed_point": {"tol": 1e-4, "iterations": it, "converged": it > 0, "ms": ms_fp,
                         "Td_min": float(td.min()), "Td_max": float(td.max())},
     }
     if it <= 0:
-        # one iteration at a time: the largest relative change and where it sits
+        # one iteration at a time: the largest relative change and where it sits, and how many
+        # cells still change by more than the tolerance, thin and thick (the class of the
+        # iteration's T_d) and per refinement level
         ctx.refresh(td0)
         td = td0.clone()
-        hist = []
+        hist, above = [], []
+        lev = torch.as_tensor(np.asarray(w.leaf_level), device=dev)
+        levels = sorted(set(np.asarray(w.leaf_level).tolist()))
         for _ in range(args.fp_diag_iter):
             prev = td.clone()
             ctx.fixed_point(tgas, td, tol=1e-30, max_iter=1, unroll=0, raise_on_noconv=False)
             ch = (td / prev - 1).abs()
             k = int(torch.argmax(ch))
             hist.append([float(ch[k]), k, float(prev[k]), float(td[k]), float(rho[k])])
+            thick = torch.as_tensor(ctx.leaf_export()["thick"], device=dev) != 0
+            big = ch > 1e-4
+            above.append({"above_tol": int(big.sum()), "thick": int((big & thick).sum()),
+                          "thin": int((big & ~thick).sum()), "thick_cells": int(thick.sum()),
+                          "by_level": {int(L): int((big & (lev == L)).sum()) for L in levels}})
         out["fixed_point"]["history_max_change_cell_T_before_after_rho"] = hist
+        out["fixed_point"]["history_cells_above_tol"] = above
     ctx.close()
     print(json.dumps(out))
 
@@ -999,6 +1010,46 @@ def run_profile(args):
                       "warps_per_target": args.profile_wpt,
                       "J_mean": float(J.double().mean())}))
     ctx.close()
+
+
+def run_profile_others(args):
+    """Profiling driver for ncu: every kernel of the path other than the evaluate kernel on
+    the 128^3 cloud, twice (a warm-up pass, then the captured one): tree build (leaf
+    quantities, Morton keys and radix sort, levels, moments, records), radiation pressure,
+    dust temperature, warm-start features, network inference and training steps."""
+    import torch
+
+    import paper_2204_09072_gb300 as tr
+    w = workload(args.npix)
+    n = w.n_leaves
+    dev = torch.device("cuda:0")
+    ctx = tr.Context(w.params)
+    rho = torch.as_tensor(w.rho, device=dev)
+    td = torch.as_tensor(w.td, device=dev)
+    tg = torch.as_tensor(w.tgas, device=dev)
+    J = torch.empty(n, dtype=torch.float32, device=dev)
+    F = torch.empty(3 * n, dtype=torch.float64, device=dev)
+    u, Td = torch.empty(n, device=dev), torch.empty(n, device=dev)
+    a_rp, force, p_src = torch.empty(3 * n, device=dev), torch.empty(3 * n, device=dev), torch.empty(n, device=dev)
+    net = tr.MLP(seed=1)
+    for rep in range(2):
+        ctx.build(w.box_cm, rho, td, n=w.uniform_n, star_pos=w.star_pos, star_lum=w.star_lum)
+        ctx.evaluate(J, F)
+        ctx.radpressure(J, F, u, a_rp, force, p_src)
+        ctx.dust_temperature(tg, J, Td)
+        X = ctx.features(tg)[0].reshape(-1).contiguous()
+        y = torch.log10(Td)
+        if rep == 0:
+            net.fit_normalization(X, y)
+        net.train(X, y, steps=4, batch=8192, lr=1e-3, seed=rep)
+        guess = torch.empty(n, device=dev)
+        ctx.warm_start(net, X, guess)
+        ctx.check()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": "others", "workload": f"turb128_npix{args.npix}", "cells": n,
+                      "Td_mean": float(Td.double().mean()), "guess_mean": float(guess.double().mean())}))
+    ctx.close()
+    net.close()
 
 
 def run_reference(args):
@@ -1053,6 +1104,8 @@ def main():
     ap.add_argument("--profile-evaluate", action="store_true",
                     help="ncu driver: evaluate kernel only, on --profile-targets cells")
     ap.add_argument("--profile-targets", type=int, default=262144)
+    ap.add_argument("--profile-others", action="store_true",
+                    help="ncu driver: every kernel but the evaluate kernel, on the 128^3 cloud")
     ap.add_argument("--profile-workload", default="turb128", choices=["turb128", "amr_core"])
     ap.add_argument("--profile-wpt", type=int, default=3, choices=[2, 3, 4, 8],
                     help="warps per target of the profiled launches (thick trees run 3 as 4)")
@@ -1083,6 +1136,8 @@ def main():
         args.warmup = 3
     if args.profile_evaluate:
         run_profile(args)
+    elif args.profile_others:
+        run_profile_others(args)
     elif args.rays_study:
         run_rays_study(args)
     elif args.batch64 or args.batch512 or args.batch_tiny:

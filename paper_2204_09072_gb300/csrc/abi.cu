@@ -324,6 +324,7 @@ treeray_status treeray_destroy(treeray_t c) {
 treeray_status treeray_build(treeray_t c, const treeray_grid* g, const float* rho, const float* Td,
                              const float* kappa, int n_stars, const double* star_pos,
                              const double* star_lum, treeray_stream_t stream) {
+    NvtxRange nvtx_("treeray_build");
     treeray_status rc = check_ctx(c, false);
     if (rc != TREERAY_OK) return rc;
     if (!g) {
@@ -338,6 +339,7 @@ treeray_status treeray_build(treeray_t c, const treeray_grid* g, const float* rh
 }
 
 treeray_status treeray_set_orientations(treeray_t c, int k, const double* rot, const uint8_t* orient) {
+    NvtxRange nvtx_("treeray_set_orientations");
     treeray_status rc = check_ctx(c, orient != nullptr);
     if (rc != TREERAY_OK) return rc;
     if (k < 0 || k > kMaxOrientations || (k > 0 && !rot) || (k == 0 && orient)) {
@@ -391,6 +393,7 @@ treeray_status treeray_set_orientations(treeray_t c, int k, const double* rot, c
 
 treeray_status treeray_evaluate(treeray_t c, const int32_t* targets, int64_t n, float* J, double* F,
                                 treeray_stream_t stream) {
+    NvtxRange nvtx_("treeray_evaluate");
     treeray_status rc = check_ctx(c, true);
     if (rc != TREERAY_OK) return rc;
     if (n == 0 && targets == nullptr && c->nleaves != 0) return TREERAY_OK;  // an empty target list
@@ -404,6 +407,7 @@ treeray_status treeray_evaluate(treeray_t c, const int32_t* targets, int64_t n, 
 
 treeray_status treeray_radpressure(treeray_t c, const float* J, const double* F, float* u, float* a_rp,
                                    float* force, float* p_src, treeray_stream_t stream) {
+    NvtxRange nvtx_("treeray_radpressure");
     treeray_status rc = check_ctx(c, true);
     if (rc != TREERAY_OK) return rc;
     if (!J || !F) {
@@ -415,6 +419,7 @@ treeray_status treeray_radpressure(treeray_t c, const float* J, const double* F,
 
 treeray_status treeray_uv_radpressure(treeray_t c, const float* nph, const float* uph, const float* x_ion,
                                       float* a_uv, float* force_uv, treeray_stream_t stream) {
+    NvtxRange nvtx_("treeray_uv_radpressure");
     treeray_status rc = check_ctx(c, true);
     if (rc != TREERAY_OK) return rc;
     if (!nph || !uph) {
@@ -426,6 +431,7 @@ treeray_status treeray_uv_radpressure(treeray_t c, const float* nph, const float
 
 treeray_status treeray_dust_temperature(treeray_t c, const float* Tgas, const float* heat_extra,
                                         const float* J, float* Td, treeray_stream_t stream) {
+    NvtxRange nvtx_("treeray_dust_temperature");
     treeray_status rc = check_ctx(c, true);
     if (rc != TREERAY_OK) return rc;
     if (!Tgas || !J || !Td) {
@@ -436,6 +442,7 @@ treeray_status treeray_dust_temperature(treeray_t c, const float* Tgas, const fl
 }
 
 treeray_status treeray_refresh(treeray_t c, const float* Td, treeray_stream_t stream) {
+    NvtxRange nvtx_("treeray_refresh");
     treeray_status rc = check_ctx(c, true);
     if (rc != TREERAY_OK) return rc;
     if (!Td) {
@@ -462,6 +469,7 @@ treeray_status fp_iteration(treeray_t c, const float* Tgas, const float* heat, f
 treeray_status treeray_fixed_point(treeray_t c, const float* Tgas, const float* heat_extra, float* Td,
                                    int max_iter, double tol, int unroll, int* iters,
                                    treeray_stream_t stream) {
+    NvtxRange nvtx_("treeray_fixed_point");
     treeray_status rc = check_ctx(c, true);
     if (rc != TREERAY_OK) return rc;
     if (!Tgas || !Td || max_iter < 1 || !(tol > 0.0) || unroll < 0 || unroll > 64) {
@@ -538,6 +546,7 @@ treeray_status treeray_fixed_point(treeray_t c, const float* Tgas, const float* 
 }
 
 treeray_status treeray_check(treeray_t c, treeray_stream_t stream) {
+    NvtxRange nvtx_("treeray_check");
     treeray_status rc = check_ctx(c, false);
     if (rc != TREERAY_OK) return rc;
     TR_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
@@ -563,6 +572,7 @@ int64_t treeray_node_count(treeray_t c) { return c && c->built ? c->nnodes : 0; 
 
 treeray_status treeray_tree_export(treeray_t c, int32_t* level, int32_t* leaf, int32_t* child0,
                                    int64_t* centre, double* vals, treeray_stream_t stream) {
+    NvtxRange nvtx_("treeray_tree_export");
     treeray_status rc = check_ctx(c, true);
     if (rc != TREERAY_OK) return rc;
     const int64_t nn = c->nnodes;
@@ -592,6 +602,7 @@ treeray_status treeray_tree_export(treeray_t c, int32_t* level, int32_t* leaf, i
 
 treeray_status treeray_leaf_export(treeray_t c, double* kappa, double* tau, double* jsrc, double* psrc,
                                    int32_t* thick, treeray_stream_t stream) {
+    NvtxRange nvtx_("treeray_leaf_export");
     treeray_status rc = check_ctx(c, true);
     if (rc != TREERAY_OK) return rc;
     cudaStream_t s = (cudaStream_t)stream;
@@ -607,6 +618,7 @@ treeray_status treeray_leaf_export(treeray_t c, double* kappa, double* tau, doub
 
 treeray_status treeray_accepted(treeray_t c, const int32_t* targets, int64_t n, int32_t cap,
                                 int32_t* counts, int32_t* ids, treeray_stream_t stream) {
+    NvtxRange nvtx_("treeray_accepted");
     treeray_status rc = check_ctx(c, true);
     if (rc != TREERAY_OK) return rc;
     if (n == 0 && cap >= 1) return TREERAY_OK;  // an empty target list
@@ -619,6 +631,7 @@ treeray_status treeray_accepted(treeray_t c, const int32_t* targets, int64_t n, 
 
 treeray_status treeray_walk_stats(treeray_t c, const int32_t* targets, int64_t n, int64_t* totals,
                                   treeray_stream_t stream) {
+    NvtxRange nvtx_("treeray_walk_stats");
     treeray_status rc = check_ctx(c, true);
     if (rc != TREERAY_OK) return rc;
     if (n == 0 && targets == nullptr && c->nleaves != 0) return TREERAY_OK;  // an empty target list

@@ -1738,6 +1738,7 @@ treeray_status batch_launch(treeray_batch_t b, cudaStream_t s) {
 
 treeray_status treeray_batch_evaluate(treeray_batch_t b, float* const* J, double* const* F, int use_graph,
                                       treeray_stream_t stream) {
+    NvtxRange nvtx_("treeray_batch_evaluate");
     if (!b || !J || !F) {
         set_error("batch_evaluate: batch, J and F required");
         return TREERAY_EINVAL;
@@ -1799,6 +1800,7 @@ treeray_status treeray_set_warps_per_target(treeray_t c, int wpt) {
 
 treeray_status treeray_autotune(treeray_t c, int64_t n_sample, int* best_wpt, float* ms,
                                 treeray_stream_t stream) {
+    NvtxRange nvtx_("treeray_autotune");
     if (!c || !c->built) {
         set_error("autotune: no tree");
         return c ? TREERAY_ENOTBUILT : TREERAY_EINVAL;
@@ -1812,6 +1814,7 @@ treeray_status treeray_autotune(treeray_t c, int64_t n_sample, int* best_wpt, fl
 
 treeray_status treeray_autotune_launch(treeray_t c, int64_t n_sample, int* best_wpt, int* best_occupancy_pct,
                                        float* ms_wpt, float* ms_occupancy, treeray_stream_t stream) {
+    NvtxRange nvtx_("treeray_autotune_launch");
     if (!c || !c->built) {
         set_error("autotune_launch: no tree");
         return c ? TREERAY_ENOTBUILT : TREERAY_EINVAL;

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <string>
@@ -34,6 +35,15 @@ enum : unsigned {
 };
 
 void set_error(const std::string& msg);
+
+// An NVTX range named after the ABI call for the scope of one call (a no-op unless a
+// profiler such as Nsight Systems or Nsight Compute with --nvtx listens).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Host-built tables (FP64 on the host, fixed per context and grid shape).
 struct HostTables {

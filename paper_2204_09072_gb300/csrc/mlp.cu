@@ -538,6 +538,7 @@ treeray_status treeray_mlp_grad(treeray_mlp_t m, const float* X, const float* y,
 treeray_status treeray_mlp_train(treeray_mlp_t m, const float* X, const float* y, int64_t n, int batch,
                                  int steps, float lr, uint64_t seed, float* loss_history,
                                  treeray_stream_t stream) {
+    NvtxRange nvtx_("treeray_mlp_train");
     if (!m || !X || !y || n < 1 || batch < 1 || batch > (1 << 20) || steps < 0 || !(lr >= 0.0f) || seed == 0) {
         set_error("mlp_train: network, X, y, n >= 1, 1 <= batch <= 2^20, steps >= 0, lr >= 0, seed != 0");
         return TREERAY_EINVAL;
@@ -567,6 +568,7 @@ treeray_status treeray_mlp_train(treeray_mlp_t m, const float* X, const float* y
 }
 
 treeray_status treeray_mlp_infer(treeray_mlp_t m, const float* X, int64_t n, float* y, treeray_stream_t stream) {
+    NvtxRange nvtx_("treeray_mlp_infer");
     if (!m || !X || !y || n < 0) {
         set_error("mlp_infer: network, X and y required");
         return TREERAY_EINVAL;
@@ -584,6 +586,7 @@ treeray_status treeray_mlp_infer(treeray_mlp_t m, const float* X, int64_t n, flo
 
 treeray_status treeray_features(treeray_t c, const float* Tgas, const float* phi, float* X, float* J, double* F,
                                 float* tau_mean, float* tau_min, treeray_stream_t stream) {
+    NvtxRange nvtx_("treeray_features");
     if (!c || !c->built) {
         set_error("features: no tree");
         return c ? TREERAY_ENOTBUILT : TREERAY_EINVAL;
@@ -600,6 +603,7 @@ treeray_status treeray_features(treeray_t c, const float* Tgas, const float* phi
 
 treeray_status treeray_warm_start(treeray_t c, treeray_mlp_t m, const float* X, float* Td,
                                   treeray_stream_t stream) {
+    NvtxRange nvtx_("treeray_warm_start");
     if (!c || !m || !X || !Td || !c->built) {
         set_error("warm_start: built context, network, features and Td required");
         return TREERAY_EINVAL;
