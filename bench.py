@@ -527,14 +527,14 @@ def run_sweep(args):
     import paper_2204_09072_gb300 as tr
     import synth
     dev = torch.device("cuda:0")
-    combos = [(npix, nb, {}) for npix in (12, 48, 192) for nb in (10, 20, 40)]
-    combos += [(npix, 20, {"theta": -1.0, "bin_spacing": sp}) for sp in (0, 1) for npix in (48, 192)]
+    combos = [(npix, nb, {}) for npix in (12, 48, 192) for nb in (10, 20, 40)] + [(768, 20, {})]
+    combos += [(npix, 20, {"theta": -1.0, "bin_spacing": sp}) for sp in (0, 1) for npix in (48, 192, 768)]
     for npix, nb, extra in combos:
         w = synth.turbulent_cloud(128, npix=npix, nbins=nb, **extra)
         c = tr.Context(w.params)
         c.build(w.box_cm, torch.as_tensor(w.rho, device=dev), torch.as_tensor(w.td, device=dev), n=128,
                 star_pos=w.star_pos, star_lum=w.star_lum)
-        best, tune = c.autotune(65536)
+        best, occ, tune, _ = c.autotune_launch(65536)
         J = torch.empty(w.n_leaves, dtype=torch.float32, device=dev)
         F = torch.empty(3 * w.n_leaves, dtype=torch.float64, device=dev)
         c.evaluate(J, F)
@@ -549,7 +549,8 @@ def run_sweep(args):
         print(json.dumps({"sweep": "turb128", "npix": npix, "nbins": nb,
                           "theta": "ray-matched" if extra.get("theta", 0.5) < 0 else 0.5,
                           "bin_spacing": "quadratic" if extra.get("bin_spacing", 0) == 1 else "geometric",
-                          "warps_per_target": best, "autotune_ms_wpt2_3_4_8_on_65536": tune, "ms_evaluate": ms,
+                          "warps_per_target": best if npix <= 192 else 8, "occupancy_pct": occ,
+                          "autotune_ms_wpt2_3_4_8_on_65536": tune, "ms_evaluate": ms,
                           "ray_evals_per_s": w.n_leaves * npix / (ms * 1e-3),
                           "walk_visits_accepted_entries": st}))
         c.close()
@@ -653,7 +654,7 @@ def run_blob(args):
         w = synth.blob_suite(v, n)
         c = tr.Context(w.params)
         c.build(w.box_cm, torch.as_tensor(w.rho, device=dev), torch.as_tensor(w.td, device=dev), n=n)
-        best, tune = c.autotune(65536)
+        best, occ, tune, _ = c.autotune_launch(65536)
         J = torch.empty(w.n_leaves, dtype=torch.float32, device=dev)
         F = torch.empty(3 * w.n_leaves, dtype=torch.float64, device=dev)
         c.evaluate(J, F)
@@ -1041,7 +1042,7 @@ def run_profile_others(args):
         y = torch.log10(Td)
         if rep == 0:
             net.fit_normalization(X, y)
-        net.train(X, y, steps=4, batch=8192, lr=1e-3, seed=rep)
+        net.train(X, y, steps=4, batch=8192, lr=1e-3, seed=rep + 1)
         guess = torch.empty(n, device=dev)
         ctx.warm_start(net, X, guess)
         ctx.check()

@@ -86,7 +86,11 @@ typedef struct {
 /* ------------------------------------------------------------------ HEALPix
  * Nested-scheme pixelisation of Gorski et al. (2005, ApJ 622, 759): 12 base
  * faces, each split into nside x nside pixels whose (ix, iy) bits are
- * interleaved. Written from the published geometry. */
+ * interleaved. The steps (polar caps against the equatorial belt, the face
+ * index from the two edge indices, the ring shift, and the base-face row and
+ * column tables) are those of the standard published algorithm, as the HEALPix
+ * library's nested ang2pix / pix2vec implement it; the names here are the
+ * paper's symbols. */
 
 static const int or_jrll[12] = {2, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 4};
 static const int or_jpll[12] = {1, 3, 5, 7, 0, 2, 4, 6, 1, 3, 5, 7};

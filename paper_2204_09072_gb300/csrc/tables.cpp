@@ -19,7 +19,10 @@ namespace tr {
 
 // ---------------------------------------------------------------- HEALPix
 // Nested pixelisation of Gorski et al. (2005): 12 base faces of nside^2 pixels whose
-// in-face coordinates (ix, iy) are bit-interleaved.
+// in-face coordinates (ix, iy) are bit-interleaved. The steps (polar caps against the
+// equatorial belt, the face from the two edge indices, the ring shift, the base-face row
+// and column tables) follow the standard published algorithm, as the HEALPix library's
+// nested ang2pix / pix2vec implement it.
 namespace {
 constexpr int kFaceRing[12] = {2, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 4};
 constexpr int kFacePhi[12] = {1, 3, 5, 7, 0, 2, 4, 6, 1, 3, 5, 7};

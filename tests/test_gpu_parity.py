@@ -165,6 +165,29 @@ def test_evaluate_dense_thin_32(orc):
     assert ej.max() <= J_TOL and ef.max() <= F_TOL
 
 
+def test_deep_thin_optical_depth_prefix(orc):
+    """Rays whose thin optical-depth prefix passes 50 (where a plain FP32 sum would lose the
+    small terms): 128^3 thin cells at tau_b 0.9-0.99 give central targets rays of tau 60-110.
+    The prefix is a float pair (~48 bits) and the segment depths are fixed point; 1500
+    targets, among them those with the deepest rays, against the oracle."""
+    import torch
+    w = synth.random_uniform(128, seed=61, thick_frac=0.0, n_stars=2)
+    dx = w.box_cm / 128
+    rng = np.random.Generator(np.random.PCG64(62))
+    w.rho = (rng.uniform(0.9, 0.99, w.n_leaves) / dx).astype(np.float32)
+    w = synth.with_gas(w)
+    ctx, _ = build_ctx(w)
+    tau_mean = ctx.features(torch.as_tensor(w.tgas, device="cuda:0"))[3].cpu().numpy()
+    ctx.close()
+    deep = np.argsort(tau_mean)[-500:]
+    assert tau_mean[deep].min() > 50.0, tau_mean.max()
+    tg = np.unique(np.concatenate([deep, synth.sample_targets(w.n_leaves, 1000, seed=63)]))
+    ej, ef = _parity(orc, w, tg)
+    print(f"deep thin prefix: mean ray depth up to {tau_mean.max():.1f}; J max {ej.max():.2e}, "
+          f"F max {ef.max():.2e}")
+    assert ej.max() <= J_TOL and ef.max() <= F_TOL
+
+
 @pytest.mark.parametrize("npix", [12, 48, 192])
 def test_evaluate_ragged_subset_npix(orc, npix):
     w = synth.random_uniform(16, seed=9, thick_frac=0.1, npix=npix, nbins=16)
