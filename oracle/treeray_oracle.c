@@ -42,13 +42,16 @@
  * against direct sums; dust temperature against T_J in the radiative limit and its
  * fixed point; the quarter-turn symmetry of turned HEALPix ray sets; the thick blob's
  * far field (V^(2/3) scaling), plateau and ambient level (Sec. 5.2); the Stroemgren
- * balance of the UV radiation pressure (App. C).
+ * balance of the UV radiation pressure (App. C); values evaluated by hand outside the
+ * oracle for J_src, P_src and the escaping S of a star (eqs. jsrc, psrc), the Planck-mean
+ * opacity law (Sec. 2), the gas-dust coupling coefficient (App. D) and a segment merge
+ * with thick content (Sec. 4.3).
  *
  * Parity unpinned: the readings of the thick path where the paper leaves the choice
- * open (the full A~ of every thick node touching a ray segment, which quantities a
- * segment merge scales, the blend of thin and thick flux when neither weighs) are pinned
- * only through their limits (deep-thick plateau, compact thick body, blob far field and
- * plateau), not against an independent transfer solution.
+ * open (the full A~ of every thick node touching a ray segment, the blend of thin and
+ * thick flux when neither weighs) are pinned only through their limits (deep-thick
+ * plateau, compact thick body, blob far field and plateau) and the merge through one
+ * hand-evaluated case, not against an independent transfer solution.
  */
 #include <math.h>
 #include <stdint.h>
