@@ -669,7 +669,13 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
         const float* R2 = A.R2 + (int64_t)tl * nb;
         const float2 lp = __ldg(A.lvlp + tl);
 
-        for (int i = tid; i < nq * cells; i += NT) tst<GT>(tL + i, 0.0f);
+        if constexpr (!GT) {  // the tile starts 16-byte aligned in shared memory
+            float4* t4 = reinterpret_cast<float4*>(tL);
+            for (int i = tid; i < nq * cells / 4; i += NT) t4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int i = (nq * cells / 4) * 4 + tid; i < nq * cells; i += NT) tL[i] = 0.0f;
+        } else {
+            for (int i = tid; i < nq * cells; i += NT) tst<GT>(tL + i, 0.0f);
+        }
         if (THICK)
             for (int h = tid; h < NPIX; h += NT) tst64<GT>(flags + h, 0ull);
         if (tid == 0) {
@@ -770,7 +776,9 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
                     Ky = alpha_key(oy, elog);
                     Kz = alpha_key(oz, elog);
                 }
-                const float beta = __ldg(R2 + i) / (rx * rx + ry * ry + rz * rz);
+                // one approximate reciprocal per node (MUFU, ~1 ulp) serves beta and the depth
+                const float inv_r2 = __fdividef(1.0f, rx * rx + ry * ry + rz * rz);
+                const float beta = __ldg(R2 + i) * inv_r2;
                 if (abs(Kx) > A.D || abs(Ky) > A.D || abs(Kz) > A.D) {
                     atomicOr(A.err, kErrAlphaKey);
                 } else {
@@ -787,7 +795,7 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
                     // fixed-point tiles carry the optical depth per sample, A~ / (s^3 omega r^2) in
                     // units of 2^-Q (beta / R_i^2 = 1 / r^2); segment 0 never extinguishes
                     bA = FIXT ? (i == 0 ? 0.0f
-                                        : v0.y * A.inv_s3 * A.tau_scale / (omega * (rx * rx + ry * ry + rz * rz)))
+                                        : v0.y * A.inv_s3 * A.tau_scale * (1.0f / omega) * inv_r2)
                               : beta * v0.y * A.inv_s3;
                     if (THICK && v1.w > 0.0f) {
                         int ilo = cilo, ihi = cihi;
