@@ -669,7 +669,8 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
         const float* R2 = A.R2 + (int64_t)tl * nb;
         const float2 lp = __ldg(A.lvlp + tl);
 
-        if constexpr (!GT) {  // the tile starts 16-byte aligned in shared memory
+        if constexpr (!GT && !THICK) {  // thin tiles start 16-byte aligned in shared memory
+            // (vector stores measured faster for thin tiles, slower for the 49-word thick rows)
             float4* t4 = reinterpret_cast<float4*>(tL);
             for (int i = tid; i < nq * cells / 4; i += NT) t4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
             for (int i = (nq * cells / 4) * 4 + tid; i < nq * cells; i += NT) tL[i] = 0.0f;
