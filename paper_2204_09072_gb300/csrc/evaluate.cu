@@ -983,12 +983,12 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
         //
         // Segments i0 <= i < i1 of ray h with a local prefix starting at zero:
         //   Fp = sum_i eps_i F*_i,  (thi, tlo) = sum_i tau_thin,i,  ek = prod_i thick transmission.
-        auto segments = [&](int h, int i0, int i1, float& Fp, float& thi, float& tlo, float& ek) {
+        auto segments = [&](int h, int i0, int i1, float& Fp, float& et, float& ek, float& ts) {
             for (int i = i0; i < i1; ++i) {
                 const int ci = i * ROW + h;
                 const float Lth = tld<GT>(tL + ci);
                 const float R2i = __ldg(R2 + i);
-                const float inv_R2 = 1.0f / R2i;
+                const float inv_R2 = __fdividef(1.0f, R2i);
                 float Ath, tth;
                 if constexpr (FIXT) {
                     Ath = (float)tldu<GT>(tT + ci);
@@ -1011,7 +1011,18 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
                         Fk = wk * tld<GT>(tLk + ci) / Vk;
                     }
                 }
-                const float g = tth < 1e-4f ? 1.0f : -expm1f(-tth) / tth;
+                // g = (1 - e^-tau) / tau (eq. fthin, the escape fraction of the segment's own
+                // emission) and its transmission e^-tau = 1 - tau g: a series below 1/16
+                // (truncation below 2e-9), exp above
+                float g, eth;
+                if (tth < 0.0625f) {
+                    g = fmaf(tth, fmaf(tth, fmaf(tth, fmaf(tth, 1.0f / 120.0f, -1.0f / 24.0f), 1.0f / 6.0f), -0.5f),
+                             1.0f);
+                    eth = fmaf(-tth, g, 1.0f);
+                } else {
+                    eth = expf(-tth);
+                    g = (1.0f - eth) * __fdividef(1.0f, tth);
+                }
                 const float Fth = g * Lth * inv_R2 * (float)(1.0 / (4.0 * kPi));
                 // eq. fcombined; without thick material the blend is F*_thin itself
                 float Fs = Fth;
@@ -1019,10 +1030,12 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
                     const float den = Ath + f * Akv;
                     Fs = den > 0.0f ? (Fth * Ath + Fk * f * Akv) / den : Fth + Fk;
                 }
-                // exp(-(thi + tlo)) with |tlo| far below one unit of thi
-                const float eps = expf(-thi) * (1.0f - tlo) * ek;
-                Fp += eps * Fs;
-                two_sum_into(thi, tlo, tth);
+                // eq. ext inner: the segments inside attenuate by the product of their thin
+                // transmissions (each e^-tau to FP32 rounding, so the product keeps its relative
+                // precision at any depth) and of their thick ones
+                Fp += et * ek * Fs;
+                ts += tth;
+                et *= eth;
                 if (THICK && f > 0.0f) ek *= (1.0f - f) + f * expf(-tk);
             }
         };
@@ -1041,32 +1054,32 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
             add_product(Fzh, Fzl, -Fh, __ldg(nh + 3 * h + 2));
         };
         // thin tiles with spare threads: the segments of a ray are cut into P consecutive
-        // parts, one thread each; a part's result is carried outward by the transmission
-        // exp(-tau) of the parts inside it
+        // parts, one thread each; a part's result is carried outward by the transmission of
+        // the parts inside it
         constexpr int P = THICK ? 1 : (NT >= 4 * NPIX ? 4 : (NT >= 2 * NPIX ? 2 : 1));
         if (P > 1 && nb >= 2 * P) {
             if (tid < P * NPIX) {
                 const int h = tid % NPIX, p = tid / NPIX;
                 const int i0 = p * nb / P, i1 = (p + 1) * nb / P;
-                float Fp = 0.0f, thi = 0.0f, tlo = 0.0f, ek = 1.0f;
-                segments(h, i0, i1, Fp, thi, tlo, ek);
+                float Fp = 0.0f, et = 1.0f, ek = 1.0f, ts = 0.0f;
+                segments(h, i0, i1, Fp, et, ek, ts);
                 // every part has >= 2 segments: its first two cells of ray h, read only by
-                // this thread, now hold (Fp, thi) and tlo
+                // this thread, now hold (Fp, transmission) and the part's optical depth
                 tst<GT>(tL + i0 * ROW + h, Fp);
-                tst<GT>(tA + i0 * ROW + h, thi);
-                tst<GT>(tL + (i0 + 1) * ROW + h, tlo);
+                tst<GT>(tA + i0 * ROW + h, et);
+                tst<GT>(tL + (i0 + 1) * ROW + h, ts);
             }
             __syncthreads();
             if (tid < NPIX) {
                 const int h = tid;
-                float Fh = 0.0f, chi = 0.0f, clo = 0.0f;
+                float Fh = 0.0f, tr = 1.0f, ts = 0.0f;
                 for (int p = 0; p < P; ++p) {
                     const int i0 = p * nb / P;
-                    const float eps = expf(-chi) * (1.0f - clo);
-                    Fh += eps * tld<GT>(tL + i0 * ROW + h);
-                    add_pair(chi, clo, tld<GT>(tA + i0 * ROW + h), tld<GT>(tL + (i0 + 1) * ROW + h));
+                    Fh += tr * tld<GT>(tL + i0 * ROW + h);
+                    tr *= tld<GT>(tA + i0 * ROW + h);
+                    ts += tld<GT>(tL + (i0 + 1) * ROW + h);
                 }
-                ray_done(h, Fh, chi + clo);
+                ray_done(h, Fh, ts);
             }
         } else {
             for (int h = tid; h < NPIX; h += NT) {
@@ -1086,10 +1099,10 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
                             for (float* q : {tL, tA, tQk, tLk, tAk, tVk}) tst<GT>(q + c1, 0.0f);
                         }
                 }
-                float Fh = 0.0f, thi = 0.0f, tlo = 0.0f, ek = 1.0f;
-                segments(h, 0, nb, Fh, thi, tlo, ek);
-                // optical depth of the whole ray: thin prefix plus thick transmission
-                ray_done(h, Fh, (thi + tlo) + (THICK && ek < 1.0f ? -__logf(ek) : 0.0f));
+                float Fh = 0.0f, et = 1.0f, ek = 1.0f, ts = 0.0f;
+                segments(h, 0, nb, Fh, et, ek, ts);
+                // optical depth of the whole ray: thin depths plus thick transmission
+                ray_done(h, Fh, ts + (THICK && ek < 1.0f ? -__logf(ek) : 0.0f));
             }
         }
         // ---- team reduction (only warps that hold rays contribute)
