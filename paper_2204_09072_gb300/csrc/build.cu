@@ -464,16 +464,18 @@ __global__ void k_pack(const int4* geo, const double* mom, int64_t nn, double u,
                        float4* thin, float4* thick, const int* skip) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= nn || (skip && *skip)) return;
-    const double Ls = scal[0];
-    const double u2 = u * u, u3 = u2 * u;
+    // the FP32 walk records: scaled by reciprocals (the GB300's FP64 division is slow; the
+    // scaled values differ from quotients by at most an FP64 rounding before the FP32 one,
+    // and 1 / L_scale is exact, L_scale being a power of two)
+    const double iLs = 1.0 / scal[0];
+    const double iu = 1.0 / u, iu2 = iu * iu, iu3 = iu2 * iu;
     const int4 g = geo[i];
     const double ox = mom[8 * nn + i] - (double)g.x;
     const double oy = mom[9 * nn + i] - (double)g.y;
     const double oz = mom[10 * nn + i] - (double)(g.z & 0xffffff);
-    thin[i] = make_float4((float)(mom[0 * nn + i] / Ls), (float)(mom[1 * nn + i] / u2), (float)ox,
-                          (float)oy);
-    thick[i] = make_float4((float)oz, (float)(mom[3 * nn + i] / (Ls * u)),
-                           (float)(mom[4 * nn + i] / u2), (float)(mom[5 * nn + i] / u3));
+    thin[i] = make_float4((float)(mom[0 * nn + i] * iLs), (float)(mom[1 * nn + i] * iu2), (float)ox, (float)oy);
+    thick[i] = make_float4((float)oz, (float)((mom[3 * nn + i] * iLs) * iu), (float)(mom[4 * nn + i] * iu2),
+                           (float)(mom[5 * nn + i] * iu3));
 }
 
 inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
