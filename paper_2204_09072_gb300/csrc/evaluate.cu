@@ -976,13 +976,33 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
             }
         }
         __syncthreads();
+        // eq. merge (Sec. 4.3): a flagged boundary between segments i and i+1 lies inside a thick
+        // node, so segment i+1 folds into i (thin content and Q^_thick scaled by R_i^2/R_(i+1)^2,
+        // the other thick sums added), from the outside in; one thread per ray
+        auto merge_flagged = [&](int h) {
+            const unsigned long long fl = tld64<GT>(flags + h);
+            if (fl)
+                for (int i = nb - 2; i >= 0; --i) {
+                    if (!((fl >> i) & 1ull)) continue;
+                    const int c0 = i * ROW + h, c1 = (i + 1) * ROW + h;
+                    const float T = __ldg(R2 + i) / __ldg(R2 + i + 1);
+                    tst<GT>(tL + c0, tld<GT>(tL + c0) + T * tld<GT>(tL + c1));
+                    tst<GT>(tA + c0, tld<GT>(tA + c0) + T * tld<GT>(tA + c1));
+                    tst<GT>(tQk + c0, tld<GT>(tQk + c0) + T * tld<GT>(tQk + c1));
+                    tst<GT>(tLk + c0, tld<GT>(tLk + c0) + tld<GT>(tLk + c1));
+                    tst<GT>(tAk + c0, tld<GT>(tAk + c0) + tld<GT>(tAk + c1));
+                    tst<GT>(tVk + c0, tld<GT>(tVk + c0) + tld<GT>(tVk + c1));
+                    for (float* q : {tL, tA, tQk, tLk, tAk, tVk}) tst<GT>(q + c1, 0.0f);
+                }
+        };
         // ---- integrate each ray from the inside out
         // J sums positive FP32 terms. The flux vector cancels between opposite rays, so each
         // product F^h n^h is split exactly into a float pair and summed with error-free
-        // transformations; the optical-depth prefix is such a pair too. No FP64 on the way.
+        // transformations. No FP64 on the way.
         //
-        // Segments i0 <= i < i1 of ray h with a local prefix starting at zero:
-        //   Fp = sum_i eps_i F*_i,  (thi, tlo) = sum_i tau_thin,i,  ek = prod_i thick transmission.
+        // Segments i0 <= i < i1 of ray h, attenuated only by the segments of the range inside them:
+        //   Fp = sum_i eps_i F*_i,  et = prod_i e^-tau_thin,i,  ek = prod_i thick transmission,
+        //   ts = sum_i tau_thin,i.
         auto segments = [&](int h, int i0, int i1, float& Fp, float& et, float& ek, float& ts) {
             for (int i = i0; i < i1; ++i) {
                 const int ci = i * ROW + h;
@@ -1053,10 +1073,18 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
             add_product(Fyh, Fyl, -Fh, __ldg(nh + 3 * h + 1));
             add_product(Fzh, Fzl, -Fh, __ldg(nh + 3 * h + 2));
         };
-        // thin tiles with spare threads: the segments of a ray are cut into P consecutive
-        // parts, one thread each; a part's result is carried outward by the transmission of
-        // the parts inside it
-        constexpr int P = THICK ? 1 : (NT >= 4 * NPIX ? 4 : (NT >= 2 * NPIX ? 2 : 1));
+        // tiles with spare threads: the segments of a ray are cut into P consecutive parts, one
+        // thread each; a part's result is carried outward by the transmission of the parts
+        // inside it
+        constexpr int P = NT >= 4 * NPIX ? 4 : (NT >= 2 * NPIX ? 2 : 1);
+        if constexpr (THICK && P > 1) {
+            // thick tiles split too: the merges of straddled boundaries first (Sec. 4.3), one
+            // thread per ray; a part then hands on its total transmission, thin times thick
+            if (nb >= 2 * P) {
+                for (int h = tid; h < NPIX; h += NT) merge_flagged(h);
+                __syncthreads();
+            }
+        }
         if (P > 1 && nb >= 2 * P) {
             if (tid < P * NPIX) {
                 const int h = tid % NPIX, p = tid / NPIX;
@@ -1066,8 +1094,8 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
                 // every part has >= 2 segments: its first two cells of ray h, read only by
                 // this thread, now hold (Fp, transmission) and the part's optical depth
                 tst<GT>(tL + i0 * ROW + h, Fp);
-                tst<GT>(tA + i0 * ROW + h, et);
-                tst<GT>(tL + (i0 + 1) * ROW + h, ts);
+                tst<GT>(tA + i0 * ROW + h, et * ek);
+                tst<GT>(tL + (i0 + 1) * ROW + h, ts + (THICK && ek < 1.0f ? -__logf(ek) : 0.0f));
             }
             __syncthreads();
             if (tid < NPIX) {
@@ -1083,22 +1111,7 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
             }
         } else {
             for (int h = tid; h < NPIX; h += NT) {
-                if (THICK) {
-                    const unsigned long long fl = tld64<GT>(flags + h);
-                    if (fl)
-                        for (int i = nb - 2; i >= 0; --i) {
-                            if (!((fl >> i) & 1ull)) continue;
-                            const int c0 = i * ROW + h, c1 = (i + 1) * ROW + h;
-                            const float T = __ldg(R2 + i) / __ldg(R2 + i + 1);
-                            tst<GT>(tL + c0, tld<GT>(tL + c0) + T * tld<GT>(tL + c1));
-                            tst<GT>(tA + c0, tld<GT>(tA + c0) + T * tld<GT>(tA + c1));
-                            tst<GT>(tQk + c0, tld<GT>(tQk + c0) + T * tld<GT>(tQk + c1));
-                            tst<GT>(tLk + c0, tld<GT>(tLk + c0) + tld<GT>(tLk + c1));
-                            tst<GT>(tAk + c0, tld<GT>(tAk + c0) + tld<GT>(tAk + c1));
-                            tst<GT>(tVk + c0, tld<GT>(tVk + c0) + tld<GT>(tVk + c1));
-                            for (float* q : {tL, tA, tQk, tLk, tAk, tVk}) tst<GT>(q + c1, 0.0f);
-                        }
-                }
+                if (THICK) merge_flagged(h);
                 float Fh = 0.0f, et = 1.0f, ek = 1.0f, ts = 0.0f;
                 segments(h, 0, nb, Fh, et, ek, ts);
                 // optical depth of the whole ray: thin depths plus thick transmission
