@@ -248,7 +248,14 @@ def run_ours(args):
     # evaluate kernel's warps per target for this tree
     with torch.cuda.stream(st):
         ctx.build(w.box_cm, rho, td, n=w.uniform_n, star_pos=w.star_pos, star_lum=w.star_lum, stream=st)
-        best_wpt, best_occ, tune_ms, tune_occ = ctx.autotune_launch(65536, stream=st)
+        if args.wpt:
+            # a fixed team size: under a profiler the autotuner's timings are serialised and
+            # cold-cache, so a capture pins the choice that the plain run made
+            ctx.set_warps_per_target(args.wpt)
+            ctx.set_occupancy(100)
+            best_wpt, best_occ, tune_ms, tune_occ = args.wpt, 100, None, None
+        else:
+            best_wpt, best_occ, tune_ms, tune_occ = ctx.autotune_launch(65536, stream=st)
 
     def step(ev=None):
         if ev:
@@ -1100,6 +1107,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-sample", type=int, default=16384)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--wpt", type=int, default=0, choices=[0, 2, 3, 4, 8],
+                    help="headline step: fixed warps per target instead of the autotuner (0)")
     ap.add_argument("--no-extra-configs", action="store_true",
                     help="skip the 192-ray and collapsing-core evaluate timings")
     ap.add_argument("--profile-evaluate", action="store_true",

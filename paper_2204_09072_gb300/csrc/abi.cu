@@ -334,6 +334,7 @@ treeray_status treeray_build(treeray_t c, const treeray_grid* g, const float* rh
     rc = build_tree(c, g, rho, Td, kappa, n_stars, star_pos, star_lum, (cudaStream_t)stream);
     if (rc != TREERAY_OK) return rc;
     rc = reserve_eval_stacks(c, c->lmax, (cudaStream_t)stream);
+    if (rc == TREERAY_OK) rc = reserve_team_tiles(c, c->nleaves, (cudaStream_t)stream);
     if (rc != TREERAY_OK) c->built = false;  // a failed build leaves no usable tree
     return rc;
 }

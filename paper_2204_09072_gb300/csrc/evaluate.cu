@@ -141,9 +141,10 @@ __device__ __forceinline__ int fixup_r2(int g, float x2, const float* __restrict
 }
 // Thin tiles of the isolated, centre-mapped kernels keep each segment's optical depth as an
 // unsigned fixed-point number (unit 2^-Q): the deposits are then integer shared-memory atomics,
-// which cost a third of an FP32 one and barely slow down when lanes hit the same cell. Each
-// deposit is rounded to the nearest unit; Q is chosen on the host so that no segment's optical
-// depth can reach 2^32 units (tau_fixed_point_q in abi.cu).
+// which are native (an FP32 addition to shared memory is a compare-and-swap loop) and barely
+// slow down when lanes hit the same cell. Each deposit is rounded to the nearest unit; Q is
+// chosen on the host so that no segment's optical depth can reach 2^32 units
+// (tau_fixed_point_q in abi.cu).
 __device__ __forceinline__ unsigned tau_units(float y) {  // round y >= 0 to the nearest integer
     return y < 8388608.0f ? __float_as_uint(y + 8388608.0f) - 0x4B000000u : __float2uint_rn(y);
 }
@@ -420,21 +421,31 @@ __global__ void __launch_bounds__(256) k_walk_list(EvalArgs a) {
     }
 }
 
-// entries per warp and walk step spread one per lane (more go through a serial fallback);
-// thick teams keep fewer so that nine of them fit an SM at 48 rays and 20 segments with
-// the static shared memory and the per-block reservation (measured: 8 teams at 192)
+// entries per warp and walk step spread one per lane (more go through a serial fallback)
 __host__ __device__ constexpr int owner_cap(bool thick) { return thick ? 160 : 256; }
 
-// 768 rays (N_side 8): a (segment x ray) tile of 20 segments takes 123 KB thin and 369 KB
-// thick, so each team keeps it in a slice of global memory (L2-resident for the teams of one
-// launch) instead of shared memory; deposits are L2 reductions (red.global.add.f32, native
-// for FP32, unlike shared-memory FP32 adds) and the tile is read through L2 (ld.global.cg)
-// after the team barrier. Teams of 8 warps, owner bytes for 2048 entries per warp pass.
+// Where a team's (segment x ray) tile lives. On sm_103a an FP32 addition to shared memory is
+// a compare-and-swap loop through the SM's load/store data pipe, while an FP32 reduction to
+// global memory (red.global.add.f32) is native in L2 and costs the SM one fire-and-forget
+// request. So every team keeps the FP32 quantities of its tile in its own slice of global
+// memory (L2-resident: the slices of one launch take 20-100 MB) and reads them back through
+// L2 (ld.global.cg) after the team barrier. The fixed-point optical depth of thin tiles,
+// whose integer atomics are native in shared memory, stays there up to 192 rays (768-ray
+// depth tiles of 61 KB go to global memory too).
+template <int NPIX, bool THICK, bool GENERAL>
+struct TileSpace {
+    static constexpr bool tau_shared = FixedTau<THICK, GENERAL>::on && NPIX <= 192;
+    static constexpr int nq_global = (THICK ? 6 : 2) - (tau_shared ? 1 : 0);  // quantities in global memory
+};
+// 768 rays (N_side 8): teams of 8 warps, owner bytes for 2048 entries per warp pass
 template <int NPIX>
-struct GlobalTile {
+struct WideRays {
     static constexpr bool on = NPIX > 192;
 };
 __host__ __device__ constexpr int owner_cap_for(int npix, bool thick) { return npix > 192 ? 2048 : owner_cap(thick); }
+__device__ __forceinline__ float gld(const float* p) { return __ldcg(p); }
+__device__ __forceinline__ void gst(float* p, float v) { __stcg(p, v); }
+// tile accessors: G selects global memory (through L2), else shared memory
 template <bool G>
 __device__ __forceinline__ float tld(const float* p) {
     if constexpr (G) return __ldcg(p);
@@ -461,18 +472,18 @@ __device__ __forceinline__ void tst64(unsigned long long* p, unsigned long long 
     else *p = v;
 }
 
-// Row stride of the (segment x ray) tile in shared memory: a few words more than the rays,
-// so that the same ray in nearby segments (a common pair among the entries of one deposit
-// pass) falls into different banks (48 rays: 48 x 2 = 0 mod 32 banks). Thin tiles: 4 more
-// (measured best); thick tiles: 1 more, which keeps 8 six-quantity tiles of 20 segments
-// per SM.
+// Row stride of the (segment x ray) tile: a few words more than the rays, so that in the
+// shared-memory depth tile the same ray in nearby segments (a common pair among the entries of
+// one deposit pass) falls into different banks (48 rays: 48 x 2 = 0 mod 32 banks). Thin tiles:
+// 4 more (measured best); thick tiles, all in global memory: 1 more.
 __host__ __device__ constexpr int tile_row(int npix, bool thick) { return npix + (thick ? 1 : 4); }
 __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-// Warps resident per SM that the register budget is cut for: thin tiles at N_pix <= 48 are
-// small enough for 64 warps per SM; larger thin tiles are limited by shared memory anyway;
-// thick kernels (six-quantity tiles) fit 32 warps without spilling.
-constexpr int min_warps_per_sm(int npix, bool thick) { return thick ? 36 : (npix <= 48 ? 64 : 48); }
+// Warps resident per SM that the register budget is cut for: with the FP32 tiles in global
+// memory no kernel is limited by shared memory, and a full SM (64 warps, 32 registers with
+// a few spills) measured fastest for thin and thick tiles alike (collapsing core, thick:
+// 103.6 ms at 36 warps, 93.3 at 48, 76.6 at 64).
+constexpr int min_warps_per_sm(int, bool) { return 64; }
 
 // Deposit of an accepted node whose closest periodic copies are tied (it lies exactly half
 // a box away on a periodic axis): every closest copy, with weight 1/2 per tied axis, by the
@@ -585,27 +596,30 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
     const int nb = a.nbins;
     constexpr int ROW = tile_row(NPIX, THICK);
     const int cells = nb * ROW;
-    constexpr int nq = THICK ? 6 : 2;
-    // layout: tile [nq][nb][ROW] f32 | THICK: flags [NPIX] u64 | THICK: per warp node
-    //         per warp entry owners u8[owner_cap] (16-byte aligned parts)
+    // layout of the team's slice of global memory (16-byte aligned parts):
+    //   L^_thin [nb][ROW] f32 | A^_thin, unless in shared memory | THICK: L^, A^, V^, Q^ thick,
+    //   then the merge flags [NPIX] u64
+    // shared memory: the fixed-point depth tile [nb][ROW] u32 (thin, up to 192 rays) | per
+    //   warp entry owners u8[owner_cap]
     // The team's stack of child groups is this block's slice of a global scratch array:
     // it stays in L1, and leaving it out of shared memory lets more teams share an SM.
-    constexpr bool GT = GlobalTile<NPIX>::on;
-    float* tL = GT ? a.gtile + (size_t)blockIdx.x * a.gtile_stride : reinterpret_cast<float*>(smem);
-    float* tA = tL + cells;
-    unsigned* tT = reinterpret_cast<unsigned*>(tA);  // fixed-point tiles: segment optical depth
     constexpr bool FIXT = FixedTau<THICK, GENERAL>::on;
-    float* tLk = tA + cells;
+    constexpr bool TS = TileSpace<NPIX, THICK, GENERAL>::tau_shared;
+    constexpr bool GA = !TS;  // the depth tile in global memory
+    constexpr int nqg = TileSpace<NPIX, THICK, GENERAL>::nq_global;
+    float* tL = a.gtile + (size_t)blockIdx.x * a.gtile_stride;
+    float* tA = TS ? reinterpret_cast<float*>(smem) : tL + cells;
+    unsigned* tT = reinterpret_cast<unsigned*>(tA);  // fixed-point tiles: segment optical depth
+    float* tLk = tA + cells;  // thick tiles: all quantities in global memory
     float* tAk = tLk + cells;
     float* tVk = tAk + cells;
     float* tQk = tVk + cells;
-    unsigned long long* flags = reinterpret_cast<unsigned long long*>(
-        (GT ? reinterpret_cast<unsigned char*>(tL) : smem) + align16((size_t)nq * cells * 4));
+    unsigned long long* flags =
+        reinterpret_cast<unsigned long long*>(reinterpret_cast<unsigned char*>(tL) + align16((size_t)nqg * cells * 4));
     // each entry's node data comes from the owner lane by shuffles (fewer shared-memory
-    // operations and registers than a per-warp node buffer, and smaller thick teams)
+    // operations and registers than a per-warp node buffer)
     constexpr int OCAP = owner_cap_for(NPIX, THICK);
-    unsigned char* owner =
-        smem + (GT ? 0 : align16(align16((size_t)nq * cells * 4) + (THICK ? NPIX * 8 : 0))) + warp * OCAP;
+    unsigned char* owner = smem + (TS ? align16((size_t)cells * 4) : 0) + warp * OCAP;
     const int stack_cap = a.stack_cap;
     int* stack = a.stack + (size_t)blockIdx.x * stack_cap;
     __shared__ int s_sp, s_overflow;
@@ -669,16 +683,20 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
         const float* R2 = A.R2 + (int64_t)tl * nb;
         const float2 lp = __ldg(A.lvlp + tl);
 
-        if constexpr (!GT && !THICK) {  // thin tiles start 16-byte aligned in shared memory
-            // (vector stores measured faster for thin tiles, slower for the 49-word thick rows)
-            float4* t4 = reinterpret_cast<float4*>(tL);
-            for (int i = tid; i < nq * cells / 4; i += NT) t4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-            for (int i = (nq * cells / 4) * 4 + tid; i < nq * cells; i += NT) tL[i] = 0.0f;
-        } else {
-            for (int i = tid; i < nq * cells; i += NT) tst<GT>(tL + i, 0.0f);
+        {  // zero the tile: 16-byte stores (both parts start 16-byte aligned), then the tails
+            const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            float4* g4 = reinterpret_cast<float4*>(tL);
+            const int ng = nqg * cells;
+            for (int i = tid; i < ng / 4; i += NT) __stcg(g4 + i, z4);
+            for (int i = (ng / 4) * 4 + tid; i < ng; i += NT) gst(tL + i, 0.0f);
+            if constexpr (TS) {
+                float4* t4 = reinterpret_cast<float4*>(tA);
+                for (int i = tid; i < cells / 4; i += NT) t4[i] = z4;
+                for (int i = (cells / 4) * 4 + tid; i < cells; i += NT) tA[i] = 0.0f;
+            }
         }
         if (THICK)
-            for (int h = tid; h < NPIX; h += NT) tst64<GT>(flags + h, 0ull);
+            for (int h = tid; h < NPIX; h += NT) tst64<true>(flags + h, 0ull);
         if (tid == 0) {
             s_overflow = 0;
             s_sp = 0;
@@ -963,15 +981,15 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
             }
             const float w = 1.0f / NPIX;
             for (int h = tid; h < NPIX; h += NT) {
-                tst<GT>(tL + h, tld<GT>(tL + h) + w * v0.x);
+                gst(tL + h, gld(tL + h) + w * v0.x);
                 // fixed-point tiles: segment 0 holds no depth
-                if constexpr (!FIXT) tst<GT>(tA + h, tld<GT>(tA + h) + w * v0.y);
+                if constexpr (!FIXT) tst<GA>(tA + h, tld<GA>(tA + h) + w * v0.y);
                 if (THICK && v1.w > 0.0f) {
-                    tst<GT>(tLk + h, tld<GT>(tLk + h) + w * v1.y);
-                    tst<GT>(tAk + h, tld<GT>(tAk + h) + v1.z);
-                    tst<GT>(tVk + h, tld<GT>(tVk + h) + w * v1.w);
-                    tst<GT>(tQk + h, tld<GT>(tQk + h) + w * v1.w);
-                    tst64<GT>(flags + h, tld64<GT>(flags + h) | fmask);
+                    gst(tLk + h, gld(tLk + h) + w * v1.y);
+                    gst(tAk + h, gld(tAk + h) + v1.z);
+                    gst(tVk + h, gld(tVk + h) + w * v1.w);
+                    gst(tQk + h, gld(tQk + h) + w * v1.w);
+                    tst64<true>(flags + h, tld64<true>(flags + h) | fmask);
                 }
             }
         }
@@ -980,19 +998,19 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
         // node, so segment i+1 folds into i (thin content and Q^_thick scaled by R_i^2/R_(i+1)^2,
         // the other thick sums added), from the outside in; one thread per ray
         auto merge_flagged = [&](int h) {
-            const unsigned long long fl = tld64<GT>(flags + h);
+            const unsigned long long fl = tld64<true>(flags + h);
             if (fl)
                 for (int i = nb - 2; i >= 0; --i) {
                     if (!((fl >> i) & 1ull)) continue;
                     const int c0 = i * ROW + h, c1 = (i + 1) * ROW + h;
                     const float T = __ldg(R2 + i) / __ldg(R2 + i + 1);
-                    tst<GT>(tL + c0, tld<GT>(tL + c0) + T * tld<GT>(tL + c1));
-                    tst<GT>(tA + c0, tld<GT>(tA + c0) + T * tld<GT>(tA + c1));
-                    tst<GT>(tQk + c0, tld<GT>(tQk + c0) + T * tld<GT>(tQk + c1));
-                    tst<GT>(tLk + c0, tld<GT>(tLk + c0) + tld<GT>(tLk + c1));
-                    tst<GT>(tAk + c0, tld<GT>(tAk + c0) + tld<GT>(tAk + c1));
-                    tst<GT>(tVk + c0, tld<GT>(tVk + c0) + tld<GT>(tVk + c1));
-                    for (float* q : {tL, tA, tQk, tLk, tAk, tVk}) tst<GT>(q + c1, 0.0f);
+                    gst(tL + c0, gld(tL + c0) + T * gld(tL + c1));
+                    gst(tA + c0, gld(tA + c0) + T * gld(tA + c1));
+                    gst(tQk + c0, gld(tQk + c0) + T * gld(tQk + c1));
+                    gst(tLk + c0, gld(tLk + c0) + gld(tLk + c1));
+                    gst(tAk + c0, gld(tAk + c0) + gld(tAk + c1));
+                    gst(tVk + c0, gld(tVk + c0) + gld(tVk + c1));
+                    for (float* q : {tL, tA, tQk, tLk, tAk, tVk}) gst(q + c1, 0.0f);
                 }
         };
         // ---- integrate each ray from the inside out
@@ -1006,29 +1024,29 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
         auto segments = [&](int h, int i0, int i1, float& Fp, float& et, float& ek, float& ts) {
             for (int i = i0; i < i1; ++i) {
                 const int ci = i * ROW + h;
-                const float Lth = tld<GT>(tL + ci);
+                const float Lth = gld(tL + ci);
                 const float R2i = __ldg(R2 + i);
                 const float inv_R2 = __fdividef(1.0f, R2i);
                 float Ath, tth;
                 if constexpr (FIXT) {
-                    Ath = (float)tldu<GT>(tT + ci);
+                    Ath = (float)tldu<GA>(tT + ci);
                     tth = Ath * (1.0f / A.tau_scale);  // a power of two: exact scaling
                 } else {
-                    Ath = tld<GT>(tA + ci);
+                    Ath = tld<GA>(tA + ci);
                     tth = i == 0 ? 0.0f : Ath * inv_R2 * (1.0f / omega);
                 }
-                const float Vk = THICK ? tld<GT>(tVk + ci) : 0.0f;
+                const float Vk = THICK ? gld(tVk + ci) : 0.0f;
                 if (Lth == 0.0f && Ath == 0.0f && Vk == 0.0f) continue;  // empty segment
                 float f = 0.0f, Fk = 0.0f, Akv = 0.0f, tk = 0.0f;
                 if constexpr (THICK) {
                     if (Vk > 0.0f) {
                         const float cb = cbrtf(Vk);
-                        float wk = (tld<GT>(tQk + ci) / Vk) * (cb * cb) * inv_R2;
+                        float wk = (gld(tQk + ci) / Vk) * (cb * cb) * inv_R2;
                         wk = fminf(wk, omega);
                         f = wk / omega;
-                        Akv = tld<GT>(tAk + ci);
+                        Akv = gld(tAk + ci);
                         tk = (i == 0 || wk == 0.0f) ? 0.0f : Akv / (wk * R2i);
-                        Fk = wk * tld<GT>(tLk + ci) / Vk;
+                        Fk = wk * gld(tLk + ci) / Vk;
                     }
                 }
                 // g = (1 - e^-tau) / tau (eq. fthin, the escape fraction of the segment's own
@@ -1093,9 +1111,9 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
                 segments(h, i0, i1, Fp, et, ek, ts);
                 // every part has >= 2 segments: its first two cells of ray h, read only by
                 // this thread, now hold (Fp, transmission) and the part's optical depth
-                tst<GT>(tL + i0 * ROW + h, Fp);
-                tst<GT>(tA + i0 * ROW + h, et * ek);
-                tst<GT>(tL + (i0 + 1) * ROW + h, ts + (THICK && ek < 1.0f ? -__logf(ek) : 0.0f));
+                gst(tL + i0 * ROW + h, Fp);
+                tst<GA>(tA + i0 * ROW + h, et * ek);
+                gst(tL + (i0 + 1) * ROW + h, ts + (THICK && ek < 1.0f ? -__logf(ek) : 0.0f));
             }
             __syncthreads();
             if (tid < NPIX) {
@@ -1103,9 +1121,9 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
                 float Fh = 0.0f, tr = 1.0f, ts = 0.0f;
                 for (int p = 0; p < P; ++p) {
                     const int i0 = p * nb / P;
-                    Fh += tr * tld<GT>(tL + i0 * ROW + h);
-                    tr *= tld<GT>(tA + i0 * ROW + h);
-                    ts += tld<GT>(tL + (i0 + 1) * ROW + h);
+                    Fh += tr * gld(tL + i0 * ROW + h);
+                    tr *= tld<GA>(tA + i0 * ROW + h);
+                    ts += gld(tL + (i0 + 1) * ROW + h);
                 }
                 ray_done(h, Fh, ts);
             }
@@ -1224,12 +1242,25 @@ treeray_status launch_persistent(treeray_ctx* c, K kern, size_t per_warp, int ma
 // global-memory tiles of one launch are kept within this many bytes (L2 129 MB)
 constexpr size_t kGlobalTileBudget = (size_t)96 << 20;
 
+// Bytes of one team's slice of global memory (see TileSpace), 16-byte aligned.
+size_t team_tile_bytes(int npix, int nbins, bool thick, bool general) {
+    const bool tau_shared = !thick && !general && npix <= 192;
+    const int nqg = (thick ? 6 : 2) - (tau_shared ? 1 : 0);
+    return align16(align16((size_t)nqg * nbins * tile_row(npix, thick) * 4) + (thick ? (size_t)npix * 8 : 0));
+}
+
+// Teams of a launch: those asked for, at most as many as keep their tiles within the L2
+// budget (but one per SM).
+int64_t tile_blocks(size_t tile_bytes, int64_t want, int sms) {
+    return std::max<int64_t>(1, std::min<int64_t>(want, std::max<int64_t>(sms, (int64_t)(kGlobalTileBudget / tile_bytes))));
+}
+
 treeray_status reserve_global_tiles(treeray_ctx* c, size_t bytes, cudaStream_t s) {
     if (c->gtile_bytes >= bytes) return TREERAY_OK;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     TR_CUDA(cudaStreamIsCapturing(s, &cs));
     if (cs != cudaStreamCaptureStatusNone) {
-        set_error("evaluate: 768-ray tiles must be reserved before stream capture (evaluate once first)");
+        set_error("evaluate: team tiles must be reserved before stream capture (build or evaluate first)");
         return TREERAY_EINVAL;
     }
     if (c->gtile) {
@@ -1252,13 +1283,13 @@ template <int NPIX, bool THICK, int WPT, bool GENERAL, bool BATCH>
 treeray_status launch_team(treeray_ctx* c, const EvalArgs& a, const EvalArgs* boxes,
                            const int64_t* box_start, int nbox, int layout_lmax, cudaStream_t s) {
     // batch: boxes and box_start are HOST arrays of the boxes' descriptors and first targets
-    constexpr int nq = THICK ? 6 : 2;
     EvalArgs b = a;
     b.stack_cap = (int)(stack_bytes_for(WPT, layout_lmax, 1) / sizeof(int));
     if (c->stack_limit > 0) b.stack_cap = std::min(b.stack_cap, c->stack_limit);  // test hook
-    constexpr bool GT = GlobalTile<NPIX>::on;
-    const size_t tile_bytes = align16(align16((size_t)nq * a.nbins * tile_row(NPIX, THICK) * 4) + (THICK ? NPIX * 8 : 0));
-    const size_t smem = (GT ? 0 : tile_bytes) + (size_t)WPT * owner_cap_for(NPIX, THICK);
+    constexpr bool TS = TileSpace<NPIX, THICK, GENERAL>::tau_shared;
+    const size_t tile_bytes = team_tile_bytes(NPIX, a.nbins, THICK, GENERAL);
+    const size_t smem = (TS ? align16((size_t)a.nbins * tile_row(NPIX, THICK) * 4) : 0) +
+                        (size_t)WPT * owner_cap_for(NPIX, THICK);
     int smem_optin = 0, sms = 0;
     TR_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
     TR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
@@ -1277,13 +1308,9 @@ treeray_status launch_team(treeray_ctx* c, const EvalArgs& a, const EvalArgs* bo
         }
         // the autotuner may launch fewer resident teams than fit (occ_pct of them, >= 1 per SM)
         const int use = std::max(1, (per_sm * c->occ_pct + 50) / 100);
-        blocks = std::max<int64_t>(1, std::min<int64_t>((int64_t)use * sms, n));
-        if constexpr (GT) {  // global tiles: as many teams as keep them within the L2 budget
-            blocks = std::max<int64_t>(1, std::min<int64_t>(
-                                              blocks, std::max<int64_t>(sms, (int64_t)(kGlobalTileBudget / tile_bytes))));
-            const treeray_status rg = reserve_global_tiles(c, (size_t)blocks * tile_bytes, s);
-            if (rg != TREERAY_OK) return rg;
-        }
+        blocks = tile_blocks(tile_bytes, std::min<int64_t>((int64_t)use * sms, n), sms);
+        const treeray_status rg = reserve_global_tiles(c, (size_t)blocks * tile_bytes, s);
+        if (rg != TREERAY_OK) return rg;
         if (c->stack_scr_bytes < stack_bytes_for(WPT, layout_lmax, (int)blocks)) {
             const treeray_status rc = reserve_eval_stacks(c, layout_lmax, s);
             if (rc != TREERAY_OK) return rc;
@@ -1323,6 +1350,8 @@ treeray_status launch_team(treeray_ctx* c, const EvalArgs& a, const EvalArgs* bo
             if (p->launch.n == 0) continue;
             if ((rc = grid_for(kern, p->launch.n, blocks)) != TREERAY_OK) return rc;
             p->launch.stack = c->stack_scr;
+            p->launch.gtile = c->gtile;
+            p->launch.gtile_stride = (int64_t)(tile_bytes / sizeof(float));
             TR_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), s));
             kern<<<(int)blocks, WPT * 32, smem, s>>>(*p);
             c->launches += 1;
@@ -1335,7 +1364,7 @@ treeray_status launch_team(treeray_ctx* c, const EvalArgs& a, const EvalArgs* bo
 template <int NPIX, bool THICK, bool GENERAL>
 treeray_status launch_wpt(treeray_ctx* c, int wpt, const EvalArgs& a, const EvalArgs* boxes,
                           const int64_t* box_start, int nbox, int layout_lmax, cudaStream_t s) {
-    if constexpr (GlobalTile<NPIX>::on) {  // 768 rays: teams of 8 warps, no batches
+    if constexpr (WideRays<NPIX>::on) {  // 768 rays: teams of 8 warps, no batches
         if (boxes) {
             set_error("batch: 768 rays are evaluated one box at a time");
             return TREERAY_EINVAL;
@@ -1474,6 +1503,22 @@ treeray_status reserve_eval_stacks(treeray_ctx* c, int lmax, cudaStream_t s) {
     }
     c->stack_scr_bytes = need;
     return TREERAY_OK;
+}
+
+// The teams' tiles for up to n targets, for every kind of tile a launch of this context can
+// use (thin or thick, fixed-point or float depth: the fixed point may switch kinds) and any
+// team size, so that launches captured in a CUDA graph find them reserved.
+treeray_status reserve_team_tiles(treeray_ctx* c, int64_t n, cudaStream_t s) {
+    int sms = 0;
+    TR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+    size_t need = 0;
+    for (bool thick : {false, true})
+        for (bool general : {false, true}) {
+            const size_t tb = team_tile_bytes(c->p.npix, c->p.nbins, thick, general);
+            // at most 2048 threads, i.e. 32 teams of 2 warps, per SM
+            need = std::max(need, tb * (size_t)tile_blocks(tb, std::min<int64_t>(std::max<int64_t>(n, 1), 32LL * sms), sms));
+        }
+    return reserve_global_tiles(c, need, s);
 }
 
 treeray_status launch_evaluate(treeray_ctx* c, const int32_t* targets, int64_t n, float* J, double* F,
@@ -1729,6 +1774,8 @@ treeray_status treeray_batch_create(const treeray_t* ctxs, int n_boxes, treeray_
         // deepest tree of the group
         const treeray_status rs = reserve_eval_stacks(b->ctx[g.box[0]], g.max_lmax, nullptr);
         if (rs != TREERAY_OK) return fail(rs);
+        const treeray_status rt = reserve_team_tiles(b->ctx[g.box[0]], g.start.back(), nullptr);
+        if (rt != TREERAY_OK) return fail(rt);
         if (cudaMalloc(&g.d_queue, sizeof(unsigned long long)) != cudaSuccess) {
             set_error("batch_create: device allocation failed");
             return fail(TREERAY_ENOMEM);
