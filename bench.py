@@ -556,7 +556,7 @@ def run_sweep(args):
         print(json.dumps({"sweep": "turb128", "npix": npix, "nbins": nb,
                           "theta": "ray-matched" if extra.get("theta", 0.5) < 0 else 0.5,
                           "bin_spacing": "quadratic" if extra.get("bin_spacing", 0) == 1 else "geometric",
-                          "warps_per_target": best if npix <= 192 else 8, "occupancy_pct": occ,
+                          "warps_per_target": best, "occupancy_pct": occ,
                           "autotune_ms_wpt2_3_4_8_on_65536": tune, "ms_evaluate": ms,
                           "ray_evals_per_s": w.n_leaves * npix / (ms * 1e-3),
                           "walk_visits_accepted_entries": st}))

@@ -164,7 +164,9 @@ treeray_status treeray_set_orientations(treeray_t ctx, int k, const double* rot,
  * e^(-tau_b/2); J_src = (1 - e^(-tau_b/2)) L_src / dx^2 (eq. jsrc);
  * P_src = (1 - e^(-tau_b/2)) L_src / (c dx^2) (eq. psrc).
  * The call synchronizes the stream once (to size the tree) and returns after the
- * build is enqueued. Inputs may be freed after the stream has finished.
+ * build is enqueued. Inputs may be freed after the stream has finished. It also reserves
+ * the evaluation scratch for up to N targets (team stacks, and the teams' ray tiles in
+ * global memory: at most 96 MB), so that evaluations can be captured in a CUDA graph.
  */
 treeray_status treeray_build(treeray_t ctx, const treeray_grid* grid, const float* rho,
                              const float* Td, const float* kappa, int n_stars,
@@ -180,6 +182,9 @@ treeray_status treeray_build(treeray_t ctx, const treeray_grid* grid, const floa
  *            an empty list: nothing is launched or written.
  *  J         device float[n], mean intensity (erg/s/cm^2/sr).
  *  F         device double[3n], flux vector xyz interleaved (erg/s/cm^2).
+ * A target list longer than the leaf count may need more scratch than the build
+ * reserved: outside a stream capture it is grown, inside one the call returns
+ * TREERAY_EINVAL.
  */
 treeray_status treeray_evaluate(treeray_t ctx, const int32_t* targets, int64_t n, float* J,
                                 double* F, treeray_stream_t stream);
@@ -256,7 +261,8 @@ treeray_status treeray_fixed_point(treeray_t ctx, const float* Tgas, const float
 /*
  * Warps per target for the evaluate kernel, chosen by timing (autotuner): the evaluate
  * kernel runs a team of 2, 3, 4 or 8 warps per target sharing one walk stack and one ray
- * tile (3 only for trees without thick material); each choice is launched twice on
+ * tile (3 only for trees without thick material below 768 rays; elsewhere a request for 3
+ * runs teams of 4); each choice is launched twice on
  * n_sample targets of the current tree (a fixed stride permutation of the leaves) and the
  * second launch is timed. The fastest choice is kept by the context. best_wpt (host int)
  * and ms (host float[4], times for 2, 3, 4, 8; -1 for a choice not tried) may be NULL.

@@ -66,7 +66,7 @@ struct __align__(16) EvalArgs {
     unsigned long long* stats;  // accepted-list mode: totals of visits, accepted, entries
     const int* skip;            // fixed-point mode: return at once when *skip != 0
     int* stack;                 // team stacks: stack_cap ints per block of the launch
-    float* gtile;               // 768 rays: the teams' (segment x ray) tiles in global memory
+    float* gtile;               // the teams' (segment x ray) tiles in global memory
     int64_t gtile_stride;       // floats per team in gtile (tile, then merge flags)
     int acc_cap;
     int64_t n;
@@ -437,7 +437,7 @@ struct TileSpace {
     static constexpr bool tau_shared = FixedTau<THICK, GENERAL>::on && NPIX <= 192;
     static constexpr int nq_global = (THICK ? 6 : 2) - (tau_shared ? 1 : 0);  // quantities in global memory
 };
-// 768 rays (N_side 8): teams of 8 warps, owner bytes for 2048 entries per warp pass
+// 768 rays (N_side 8): owner bytes for 2048 entries per warp pass, no batches
 template <int NPIX>
 struct WideRays {
     static constexpr bool on = NPIX > 192;
@@ -1240,8 +1240,11 @@ treeray_status launch_persistent(treeray_ctx* c, K kern, size_t per_warp, int ma
     return TREERAY_OK;
 }
 
-// global-memory tiles of one launch are kept within this many bytes (L2 129 MB)
-constexpr size_t kGlobalTileBudget = (size_t)96 << 20;
+// Global-memory tiles of one launch are kept within this many bytes. Tiles beyond the 129 MB
+// L2 go through HBM, which costs less than teams left unlaunched: 768 rays on the collapsing
+// core (thick tiles of 369 KB) took 5577 ms with one launch's tiles capped at 96 MB and 2525
+// ms at 1 GB (192 rays: 436 -> 408 ms).
+constexpr size_t kGlobalTileBudget = (size_t)1 << 30;
 
 // Bytes of one team's slice of global memory (see TileSpace), 16-byte aligned.
 size_t team_tile_bytes(int npix, int nbins, bool thick, bool general) {
@@ -1365,12 +1368,14 @@ treeray_status launch_team(treeray_ctx* c, const EvalArgs& a, const EvalArgs* bo
 template <int NPIX, bool THICK, bool GENERAL>
 treeray_status launch_wpt(treeray_ctx* c, int wpt, const EvalArgs& a, const EvalArgs* boxes,
                           const int64_t* box_start, int nbox, int layout_lmax, cudaStream_t s) {
-    if constexpr (WideRays<NPIX>::on) {  // 768 rays: teams of 8 warps, no batches
+    if constexpr (WideRays<NPIX>::on) {  // 768 rays: teams of 2, 4 or 8 warps, no batches
         if (boxes) {
             set_error("batch: 768 rays are evaluated one box at a time");
             return TREERAY_EINVAL;
         }
-        return launch_team<NPIX, THICK, 8, GENERAL, false>(c, a, nullptr, nullptr, 0, layout_lmax, s);
+        if (wpt == 2) return launch_team<NPIX, THICK, 2, GENERAL, false>(c, a, nullptr, nullptr, 0, layout_lmax, s);
+        if (wpt == 8) return launch_team<NPIX, THICK, 8, GENERAL, false>(c, a, nullptr, nullptr, 0, layout_lmax, s);
+        return launch_team<NPIX, THICK, 4, GENERAL, false>(c, a, nullptr, nullptr, 0, layout_lmax, s);
     } else {
     // batches run teams of 3 warps (thin tiles, when that is the team size asked for) or 4
     if (boxes) {
@@ -1506,20 +1511,30 @@ treeray_status reserve_eval_stacks(treeray_ctx* c, int lmax, cudaStream_t s) {
     return TREERAY_OK;
 }
 
-// The teams' tiles for up to n targets, for every kind of tile a launch of this context can
-// use (thin or thick, fixed-point or float depth: the fixed point may switch kinds) and any
-// team size, so that launches captured in a CUDA graph find them reserved.
-treeray_status reserve_team_tiles(treeray_ctx* c, int64_t n, cudaStream_t s) {
+// The teams' tiles for up to n targets, for each kind of tile (thin or thick, fixed-point or
+// float depth) a launch of this context can use and any team size, so that launches
+// captured in a CUDA graph find them reserved.
+treeray_status reserve_team_tiles_kind(treeray_ctx* c, int64_t n, bool thick, bool general, cudaStream_t s) {
     int sms = 0;
     TR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
-    size_t need = 0;
-    for (bool thick : {false, true})
-        for (bool general : {false, true}) {
-            const size_t tb = team_tile_bytes(c->p.npix, c->p.nbins, thick, general);
-            // at most 2048 threads, i.e. 32 teams of 2 warps, per SM
-            need = std::max(need, tb * (size_t)tile_blocks(tb, std::min<int64_t>(std::max<int64_t>(n, 1), 32LL * sms), sms));
-        }
-    return reserve_global_tiles(c, need, s);
+    const size_t tb = team_tile_bytes(c->p.npix, c->p.nbins, thick, general);
+    // at most 2048 threads, i.e. 32 teams of 2 warps, per SM
+    const int64_t teams = tile_blocks(tb, std::min<int64_t>(std::max<int64_t>(n, 1), 32LL * sms), sms);
+    return reserve_global_tiles(c, tb * (size_t)teams, s);
+}
+
+treeray_status reserve_team_tiles(treeray_ctx* c, int64_t n, cudaStream_t s) {
+    // thick tiles for trees with thick material, thin tiles for trees without; both where a
+    // refresh can change the classes (temperature-dependent opacity)
+    for (bool thick : {false, true}) {
+        const bool tdep = c->p.kappa_model == 1;
+        const bool possible = thick ? (c->has_thick || c->force_thick || tdep) : (!c->has_thick || tdep);
+        if (!possible) continue;
+        const bool general = c->p.periodic != 0 || c->p.col_mapping != 0 || (!thick && c->tau_q == 0);
+        const treeray_status rc = reserve_team_tiles_kind(c, n, thick, general, s);
+        if (rc != TREERAY_OK) return rc;
+    }
+    return TREERAY_OK;
 }
 
 treeray_status launch_evaluate(treeray_ctx* c, const int32_t* targets, int64_t n, float* J, double* F,
@@ -1659,7 +1674,8 @@ treeray_status autotune(treeray_ctx* c, int64_t n_sample, int* best, float* ms, 
     bool first = true;
     c->occ_pct = 100;
     for (int k = 0; k < 4; ++k) {
-        if (thick && cand[k] == 3) {  // teams of three warps exist for thin tiles only
+        // teams of three warps exist for thin tiles below 768 rays only
+        if (cand[k] == 3 && (thick || c->p.npix > 192)) {
             if (ms) ms[k] = -1.0f;
             continue;
         }
@@ -1775,7 +1791,8 @@ treeray_status treeray_batch_create(const treeray_t* ctxs, int n_boxes, treeray_
         // deepest tree of the group
         const treeray_status rs = reserve_eval_stacks(b->ctx[g.box[0]], g.max_lmax, nullptr);
         if (rs != TREERAY_OK) return fail(rs);
-        const treeray_status rt = reserve_team_tiles(b->ctx[g.box[0]], g.start.back(), nullptr);
+        const treeray_status rt =
+            reserve_team_tiles_kind(b->ctx[g.box[0]], g.start.back(), &g == &b->g[1], g.periodic, nullptr);
         if (rt != TREERAY_OK) return fail(rt);
         if (cudaMalloc(&g.d_queue, sizeof(unsigned long long)) != cudaSuccess) {
             set_error("batch_create: device allocation failed");

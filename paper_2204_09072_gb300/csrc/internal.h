@@ -170,6 +170,7 @@ treeray_status dev_alloc(treeray_ctx* c, void** p, size_t bytes);
 // `lmax` levels below the root; never allocates while `s` is being captured.
 treeray_status reserve_eval_stacks(treeray_ctx* c, int lmax, cudaStream_t s);
 treeray_status reserve_team_tiles(treeray_ctx* c, int64_t n, cudaStream_t s);
+treeray_status reserve_team_tiles_kind(treeray_ctx* c, int64_t n, bool thick, bool general, cudaStream_t s);
 // Apply the autotuner's choice cached for a tree of this context's shape, if any.
 void apply_cached_launch_choice(treeray_ctx* c);
 treeray_status build_tree(treeray_ctx* c, const treeray_grid* g, const float* rho, const float* Td,

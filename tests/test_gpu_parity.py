@@ -133,9 +133,10 @@ def test_col_mapping_decisions_agree(orc, name):
 
 @pytest.mark.parametrize("case", ["thin_theta05", "thick_theta05", "thick_raymatched", "amr_raymatched"])
 def test_evaluate_768_rays(orc, case):
-    """768 rays (N_side 8), the paper's third ray count (Sec. 7.6): the teams' (segment x ray)
-    tiles live in global memory and take L2 reductions; every target against the oracle,
-    at theta 0.5 and at the ray-matched angle sqrt(4 pi / 768) = 0.128."""
+    """768 rays (N_side 8), the paper's third ray count (Sec. 7.6): every quantity of the
+    teams' (segment x ray) tiles lives in global memory and takes L2 reductions; every target
+    against the oracle with teams of 2, 4 and 8 warps, at theta 0.5 and at the ray-matched
+    angle sqrt(4 pi / 768) = 0.128."""
     if case == "thin_theta05":
         w = synth.random_uniform(16, seed=51, thick_frac=0.0, n_stars=2, npix=768)
     elif case == "thick_theta05":
@@ -145,9 +146,14 @@ def test_evaluate_768_rays(orc, case):
     else:
         w = synth.amr_core(n_base_blocks=2, max_level=1, target_leaves=16 * 512, n_stars=3, npix=768,
                            theta=-1.0)
-    ej, ef = _parity(orc, w)
-    print(f"768 rays {case}: {w.n_leaves} targets, J max {ej.max():.2e}, F max {ef.max():.2e}")
-    assert ej.max() <= J_TOL and ef.max() <= F_TOL
+    Jr, Fr = _oracle(orc, w).evaluate(None)
+    ctx, _ = build_ctx(w)
+    for wpt in (2, 4, 8):  # every team size the 768-ray kernels offer
+        ctx.set_warps_per_target(wpt)
+        J, F = evaluate(ctx, None)
+        ej, ef = np.abs(J / Jr - 1), flux_err(F, Fr, Jr)
+        print(f"768 rays {case}, {wpt} warps: {w.n_leaves} targets, J max {ej.max():.2e}, F max {ef.max():.2e}")
+        assert ej.max() <= J_TOL and ef.max() <= F_TOL
 
 
 def test_evaluate_dense_thin_32(orc):
