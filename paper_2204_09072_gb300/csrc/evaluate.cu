@@ -1202,7 +1202,7 @@ __global__ void __launch_bounds__(WPT * 32, min_warps_per_sm(NPIX, THICK) / WPT)
     evaluate_team<NPIX, THICK, WPT, GENERAL, false>(a, nullptr);
 }
 
-// batches run teams of 3 (thin tiles) or 4 warps
+// batches run teams of 2 or 3 (thin tiles) or 4 warps
 template <int NPIX, bool THICK, int WPT, bool GENERAL>
 __global__ void __launch_bounds__(WPT * 32, min_warps_per_sm(NPIX, THICK) / WPT)
     k_evaluate_batch(const __grid_constant__ BatchArgs p) {
@@ -1334,7 +1334,7 @@ treeray_status launch_team(treeray_ctx* c, const EvalArgs& a, const EvalArgs* bo
         c->launches += 1;
         TR_CUDA(cudaGetLastError());
     } else {
-        static_assert(WPT == 4 || (WPT == 3 && !THICK), "batches run teams of 3 (thin) or 4 warps");
+        static_assert(WPT == 4 || ((WPT == 2 || WPT == 3) && !THICK), "batches run teams of 2, 3 (thin) or 4 warps");
         auto kern = k_evaluate_batch<NPIX, THICK, WPT, GENERAL>;
         std::unique_ptr<BatchArgs> p(new (std::nothrow) BatchArgs());
         if (!p) {
@@ -1377,10 +1377,12 @@ treeray_status launch_wpt(treeray_ctx* c, int wpt, const EvalArgs& a, const Eval
         if (wpt == 8) return launch_team<NPIX, THICK, 8, GENERAL, false>(c, a, nullptr, nullptr, 0, layout_lmax, s);
         return launch_team<NPIX, THICK, 4, GENERAL, false>(c, a, nullptr, nullptr, 0, layout_lmax, s);
     } else {
-    // batches run teams of 3 warps (thin tiles, when that is the team size asked for) or 4
+    // batches run teams of 2 or 3 warps (thin tiles, when that is the team size asked for) or 4
     if (boxes) {
-        if constexpr (!THICK)
+        if constexpr (!THICK) {
+            if (wpt == 2) return launch_team<NPIX, THICK, 2, GENERAL, true>(c, a, boxes, box_start, nbox, layout_lmax, s);
             if (wpt == 3) return launch_team<NPIX, THICK, 3, GENERAL, true>(c, a, boxes, box_start, nbox, layout_lmax, s);
+        }
         return launch_team<NPIX, THICK, 4, GENERAL, true>(c, a, boxes, box_start, nbox, layout_lmax, s);
     }
     switch (wpt) {
@@ -1731,7 +1733,7 @@ struct treeray_batch {
     std::vector<treeray_t> ctx;
     Group g[2];
     std::vector<void*> lastJ, lastF;
-    int wpt_thin = 3;  // team size of the thin-tile launch (3 or 4 warps)
+    int wpt_thin = 3;  // team size of the thin-tile launch (2, 3 or 4 warps)
     cudaGraphExec_t graph = nullptr;
     cudaStream_t gstream = nullptr;
     cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -1767,7 +1769,7 @@ treeray_status treeray_batch_create(const treeray_t* ctxs, int n_boxes, treeray_
     b->ctx.assign(ctxs, ctxs + n_boxes);
     for (int k = 0; k < n_boxes; ++k)  // thin boxes run the team size of the first one's choice
         if (!(ctxs[k]->has_thick || ctxs[k]->force_thick)) {
-            b->wpt_thin = ctxs[k]->wpt == 3 ? 3 : 4;
+            b->wpt_thin = (ctxs[k]->wpt == 2 || ctxs[k]->wpt == 3) ? ctxs[k]->wpt : 4;
             break;
         }
     for (int k = 0; k < n_boxes; ++k) {

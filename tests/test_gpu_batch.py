@@ -16,9 +16,9 @@ def _boxes():
             synth.point_source(8, kappa0=2.0, nbins=16)]
 
 
-@pytest.mark.parametrize("use_graph,thin_wpt", [(False, 4), (True, 4), (True, 3)])
+@pytest.mark.parametrize("use_graph,thin_wpt", [(False, 4), (True, 4), (True, 3), (True, 2), (False, 2)])
 def test_batch_matches_single_and_oracle(orc, use_graph, thin_wpt):
-    """Thin boxes run teams of the first thin box's size (3 or 4 warps), thick boxes 4."""
+    """Thin boxes run teams of the first thin box's size (2, 3 or 4 warps), thick boxes 4."""
     import torch
 
     import paper_2204_09072_gb300 as tr
