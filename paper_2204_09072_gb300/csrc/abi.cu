@@ -90,35 +90,6 @@ treeray_status ensure_orient_map(treeray_ctx* c, cudaStream_t s) {
     return TREERAY_OK;
 }
 
-// Fixed-point unit 2^-Q of the thin tiles' segment optical depth (0: keep float tiles).
-// Without thick material every leaf has tau_b < 1, so the A~ of a node is below V / dx_min
-// (dx_min = 2 half-cells). An accepted node whose centre lies in segment [R_i, R_i+1) has
-// edge E < theta d, so it lies within R_i+1 (1 + sqrt(3)/2 theta) of the target and its COL
-// at least d (1 - sqrt(3)/2 theta) away: beta = R_i^2 / r^2 <= beta_max (leaves: <= 1). The
-// sampled volume of all nodes of one segment inside one ray's cone of solid angle omega is
-// at most omega b^3 / 3 with b = R_i+1 (1 + sqrt(3)/2 theta), so one cell's optical depth
-// A^ / (omega R_i^2) stays below beta_max b^3 / (3 R_i^2 dx_min). Q is the largest value
-// (at most 20) for which three times that bound (the sampling's cone edges, and margin)
-// stays below 2^32 units; below 2^-18 per unit the tiles stay in float.
-int tau_fixed_point_q(const treeray_ctx* c) {
-    const double th = c->p.theta, h = 0.5 * std::sqrt(3.0) * th;
-    if (!(h < 0.95)) return 0;
-    const double beta_max = std::max(1.0, 1.0 / ((1.0 - h) * (1.0 - h)));
-    const int L = c->lmax, nb = c->p.nbins;
-    std::vector<double> R(nb + 1);
-    double bound = 0.0;
-    for (int lt = 0; lt <= L; ++lt) {
-        radii(nb, L, c->p.periodic, c->p.bin_spacing, (int64_t)2 << (L - lt), R.data());
-        for (int i = 1; i < nb; ++i) {
-            const double b = R[i + 1] * (1.0 + h);
-            bound = std::max(bound, beta_max * b * b * b / (3.0 * R[i] * R[i] * 2.0));
-        }
-    }
-    if (bound <= 0.0) return 20;  // one segment: no optical depth is ever used
-    const int q = (int)std::floor(32.0 - std::log2(3.0 * bound));
-    return q >= 18 ? std::min(q, 20) : 0;
-}
-
 // Per-grid tables: the alpha table (cached by grid shape) and, for every target level,
 // the integer thresholds of the walk's decisions:
 //   bin i      : d^2 >= ceil(R_i^2)                      (segment index, i >= 1)
@@ -144,7 +115,6 @@ treeray_status upload_tables(treeray_ctx* c, cudaStream_t s) {
         if ((rc = upload(c, &c->dt.alpha_off, c->ht.alpha_off, s)) != TREERAY_OK) return rc;
         if ((rc = upload(c, &c->dt.alpha_ent, c->ht.alpha_ent, s)) != TREERAY_OK) return rc;
     }
-    c->tau_q = tau_fixed_point_q(c);
     std::vector<int64_t> thr((size_t)(L + 1) * nb), omax(L + 1);
     std::vector<float> R2((size_t)(L + 1) * nb), Rh((size_t)(L + 1) * nb);
     std::vector<double> Rd((size_t)(L + 1) * nb);

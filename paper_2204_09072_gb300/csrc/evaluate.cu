@@ -75,8 +75,6 @@ struct __align__(16) EvalArgs {
     int periodic;     // bit a: axis a periodic (closest copies)
     int col_mapping;  // map accepted nodes at their centre of luminosity
     float inv_s3;  // 1 / alpha_s^3: weight of one sub-cube sample of the angular kernel
-    float tau_scale;  // thin tiles of the isolated, centre-mapped kernels: 2^Q, the fixed-point
-                      // unit of the segment optical depth (0: float tiles)
     double u;
     double inv_u2;  // 1 / u^2: flux unit = L_scale / u^2 (L_scale a power of two)
 };
@@ -139,20 +137,6 @@ __device__ __forceinline__ int fixup_r2(int g, float x2, const float* __restrict
     while (g > 0 && x2 < __ldg(R2 + g)) --g;
     return g;
 }
-// Thin tiles of the isolated, centre-mapped kernels keep each segment's optical depth as an
-// unsigned fixed-point number (unit 2^-Q): the deposits are then integer shared-memory atomics,
-// which are native (an FP32 addition to shared memory is a compare-and-swap loop) and barely
-// slow down when lanes hit the same cell. Each deposit is rounded to the nearest unit; Q is
-// chosen on the host so that no segment's optical depth can reach 2^32 units
-// (tau_fixed_point_q in abi.cu).
-__device__ __forceinline__ unsigned tau_units(float y) {  // round y >= 0 to the nearest integer
-    return y < 8388608.0f ? __float_as_uint(y + 8388608.0f) - 0x4B000000u : __float2uint_rn(y);
-}
-template <bool THICK, bool GENERAL>
-struct FixedTau {
-    static constexpr bool on = !THICK && !GENERAL;
-};
-
 // Squared length in FP32, evaluated in a fixed order and never fused, as the oracle does.
 __device__ __forceinline__ float sq3_rn(float x, float y, float z) {
     return __fadd_rn(__fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y)), __fmul_rn(z, z));
@@ -427,16 +411,12 @@ __host__ __device__ constexpr int owner_cap(bool thick) { return thick ? 160 : 2
 // Where a team's (segment x ray) tile lives. On sm_103a an FP32 addition to shared memory is
 // a compare-and-swap loop through the SM's load/store data pipe, while an FP32 reduction to
 // global memory (red.global.add.f32) is native in L2 and costs the SM one fire-and-forget
-// request. So every team keeps the FP32 quantities of its tile in its own slice of global
-// memory (L2-resident: the slices of one launch take 20-100 MB) and reads them back through
-// L2 (ld.global.cg) after the team barrier. The fixed-point optical depth of thin tiles,
-// whose integer atomics are native in shared memory, stays there up to 192 rays (768-ray
-// depth tiles of 61 KB go to global memory too).
-template <int NPIX, bool THICK, bool GENERAL>
-struct TileSpace {
-    static constexpr bool tau_shared = FixedTau<THICK, GENERAL>::on && NPIX <= 192;
-    static constexpr int nq_global = (THICK ? 6 : 2) - (tau_shared ? 1 : 0);  // quantities in global memory
-};
+// request. So every team keeps its tile in its own slice of global memory (L2-resident: the
+// slices of one launch take 20-60 MB at 48 rays) and reads it back through L2
+// (ld.global.cg) after the team barrier. Thin tiles interleave each cell's L^ and A^, so
+// that one vector reduction (red.global.add.v2.f32) deposits both; thick tiles keep six
+// arrays (interleaving their four thick quantities into one vector reduction measured
+// slower at 48 rays).
 // 768 rays (N_side 8): owner bytes for 2048 entries per warp pass, no batches
 template <int NPIX>
 struct WideRays {
@@ -445,38 +425,27 @@ struct WideRays {
 __host__ __device__ constexpr int owner_cap_for(int npix, bool thick) { return npix > 192 ? 2048 : owner_cap(thick); }
 __device__ __forceinline__ float gld(const float* p) { return __ldcg(p); }
 __device__ __forceinline__ void gst(float* p, float v) { __stcg(p, v); }
-// tile accessors: G selects global memory (through L2), else shared memory
-template <bool G>
-__device__ __forceinline__ float tld(const float* p) {
-    if constexpr (G) return __ldcg(p);
-    else return *p;
+// p[0] += a, p[1] += b in L2 (p 8-byte aligned), one request
+__device__ __forceinline__ void red_add_v2(float* p, float a, float b) {
+    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(a), "f"(b) : "memory");
 }
-template <bool G>
-__device__ __forceinline__ void tst(float* p, float v) {
-    if constexpr (G) __stcg(p, v);
-    else *p = v;
+// thin deposit of cell c: L^ += l, A^ += ar (thin tiles: one interleaved pair)
+template <bool THICK>
+__device__ __forceinline__ void deposit_thin(float* tL, float* tA, int c, float l, float ar) {
+    if constexpr (THICK) {
+        atomicAdd(tL + c, l);
+        atomicAdd(tA + c, ar);
+    } else {
+        red_add_v2(tL + 2 * c, l, ar);
+    }
 }
-template <bool G>
-__device__ __forceinline__ unsigned tldu(const unsigned* p) {
-    if constexpr (G) return __ldcg(p);
-    else return *p;
-}
-template <bool G>
-__device__ __forceinline__ unsigned long long tld64(const unsigned long long* p) {
-    if constexpr (G) return __ldcg(p);
-    else return *p;
-}
-template <bool G>
-__device__ __forceinline__ void tst64(unsigned long long* p, unsigned long long v) {
-    if constexpr (G) __stcg(p, v);
-    else *p = v;
-}
+__device__ __forceinline__ unsigned long long gld64(const unsigned long long* p) { return __ldcg(p); }
+__device__ __forceinline__ void gst64(unsigned long long* p, unsigned long long v) { __stcg(p, v); }
 
-// Row stride of the (segment x ray) tile. Thin tiles: 4 words more than the rays, so that in
-// the shared-memory depth tile the same ray in nearby segments (a common pair among the
-// entries of one deposit pass) falls into different banks (48 rays: 48 x 2 = 0 mod 32
-// banks; 4 measured best). Thick tiles, all in global memory, are not padded (a smaller
-// footprint in L2: collapsing core 76.6 -> 74.6 ms against one word more).
+// Row stride of the (segment x ray) tile, in cells. Thin tiles: 4 cells more than the rays
+// (128^3 cloud at 48 rays: 42.3 ms against 42.5 unpadded; 192 rays: 69.2 against 68.6).
+// Thick tiles are not padded (a smaller footprint in L2: collapsing core 76.6 -> 74.6 ms
+// against one word more).
 __host__ __device__ constexpr int tile_row(int npix, bool thick) { return npix + (thick ? 0 : 4); }
 __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
@@ -488,7 +457,7 @@ constexpr int min_warps_per_sm(int, bool) { return 64; }
 
 // Deposit of an accepted node whose closest periodic copies are tied (it lies exactly half
 // a box away on a periodic axis): every closest copy, with weight 1/2 per tied axis, by the
-// node's own thread with shared-memory atomics. The copies share |offset| per axis, hence
+// node's own thread with atomics. The copies share |offset| per axis, hence
 // d^2, the segment and the straddled boundaries; alpha and beta differ. Such nodes lie on
 // the planes half a box from the target, so this path is rare.
 template <int NPIX, bool THICK>
@@ -558,8 +527,7 @@ __device__ __noinline__ void deposit_tied_copies(const EvalArgs& A, const int32_
             const int h = (int)(ent & 0xffffu);
             const int c = i * tile_row(NPIX, THICK) + h;
             const float w = count_to_float(ent >> 16);
-            atomicAdd(tL + c, w * bL);
-            atomicAdd(tA + c, w * bA);
+            deposit_thin<THICK>(tL, tA, c, w * bL, w * bA);
             if (thick) {
                 const float wn = w * inv_s3;
                 atomicAdd(tLk + c, wn * v1.y * wt);
@@ -598,29 +566,26 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
     constexpr int ROW = tile_row(NPIX, THICK);
     const int cells = nb * ROW;
     // layout of the team's slice of global memory (16-byte aligned parts):
-    //   L^_thin [nb][ROW] f32 | A^_thin, unless in shared memory | THICK: L^, A^, V^, Q^ thick,
-    //   then the merge flags [NPIX] u64
-    // shared memory: the fixed-point depth tile [nb][ROW] u32 (thin, up to 192 rays) | per
-    //   warp entry owners u8[owner_cap]
+    //   thin: (L^, A^) pairs [nb][ROW][2] f32
+    //   thick: L^, A^ thin, L^, A^, V^, Q^ thick [nb][ROW] f32 each, then the merge flags
+    //   [NPIX] u64
+    // shared memory: per warp entry owners u8[owner_cap]
     // The team's stack of child groups is this block's slice of a global scratch array:
     // it stays in L1, and leaving it out of shared memory lets more teams share an SM.
-    constexpr bool FIXT = FixedTau<THICK, GENERAL>::on;
-    constexpr bool TS = TileSpace<NPIX, THICK, GENERAL>::tau_shared;
-    constexpr bool GA = !TS;  // the depth tile in global memory
-    constexpr int nqg = TileSpace<NPIX, THICK, GENERAL>::nq_global;
+    constexpr int nq = THICK ? 6 : 2;
+    constexpr int LS = THICK ? 1 : 2;  // stride of a cell's L^ and A^ (thin: interleaved)
     float* tL = a.gtile + (size_t)blockIdx.x * a.gtile_stride;
-    float* tA = TS ? reinterpret_cast<float*>(smem) : tL + cells;
-    unsigned* tT = reinterpret_cast<unsigned*>(tA);  // fixed-point tiles: segment optical depth
-    float* tLk = tA + cells;  // thick tiles: all quantities in global memory
+    float* tA = THICK ? tL + cells : tL + 1;
+    float* tLk = tL + 2 * cells;  // thick tiles only
     float* tAk = tLk + cells;
     float* tVk = tAk + cells;
     float* tQk = tVk + cells;
     unsigned long long* flags =
-        reinterpret_cast<unsigned long long*>(reinterpret_cast<unsigned char*>(tL) + align16((size_t)nqg * cells * 4));
+        reinterpret_cast<unsigned long long*>(reinterpret_cast<unsigned char*>(tL) + align16((size_t)nq * cells * 4));
     // each entry's node data comes from the owner lane by shuffles (fewer shared-memory
     // operations and registers than a per-warp node buffer)
     constexpr int OCAP = owner_cap_for(NPIX, THICK);
-    unsigned char* owner = smem + (TS ? align16((size_t)cells * 4) : 0) + warp * OCAP;
+    unsigned char* owner = smem + warp * OCAP;
     const int stack_cap = a.stack_cap;
     int* stack = a.stack + (size_t)blockIdx.x * stack_cap;
     __shared__ int s_sp, s_overflow;
@@ -684,20 +649,15 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
         const float* R2 = A.R2 + (int64_t)tl * nb;
         const float2 lp = __ldg(A.lvlp + tl);
 
-        {  // zero the tile: 16-byte stores (both parts start 16-byte aligned), then the tails
+        {  // zero the tile: 16-byte stores (it starts 16-byte aligned), then the tail
             const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
             float4* g4 = reinterpret_cast<float4*>(tL);
-            const int ng = nqg * cells;
+            const int ng = nq * cells;
             for (int i = tid; i < ng / 4; i += NT) __stcg(g4 + i, z4);
             for (int i = (ng / 4) * 4 + tid; i < ng; i += NT) gst(tL + i, 0.0f);
-            if constexpr (TS) {
-                float4* t4 = reinterpret_cast<float4*>(tA);
-                for (int i = tid; i < cells / 4; i += NT) t4[i] = z4;
-                for (int i = (cells / 4) * 4 + tid; i < cells; i += NT) tA[i] = 0.0f;
-            }
         }
         if (THICK)
-            for (int h = tid; h < NPIX; h += NT) tst64<true>(flags + h, 0ull);
+            for (int h = tid; h < NPIX; h += NT) gst64(flags + h, 0ull);
         if (tid == 0) {
             s_overflow = 0;
             s_sp = 0;
@@ -812,11 +772,7 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
                     ebase = e0;
                     cbase = i * ROW;
                     bL = beta * v0.x * A.inv_s3;
-                    // fixed-point tiles carry the optical depth per sample, A~ / (s^3 omega r^2) in
-                    // units of 2^-Q (beta / R_i^2 = 1 / r^2); segment 0 never extinguishes
-                    bA = FIXT ? (i == 0 ? 0.0f
-                                        : v0.y * A.inv_s3 * A.tau_scale * (1.0f / omega) * inv_r2)
-                              : beta * v0.y * A.inv_s3;
+                    bA = beta * v0.y * A.inv_s3;
                     if (THICK && v1.w > 0.0f) {
                         int ilo = cilo, ihi = cihi;
                         if (!colmap) {
@@ -874,24 +830,12 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
                         if (r < tw) {
                             const int c = nd.x + (int)(ent & 0xffffu);
                             const float w = count_to_float(ent >> 16);
-                            atomicAdd(tL + c, w * __int_as_float(nd.z));
-                            if constexpr (FIXT) {
-                                const unsigned v = tau_units(w * __int_as_float(nd.w));
-                                if (v) atomicAdd(tT + c, v);
-                            } else {
-                                atomicAdd(tA + c, w * __int_as_float(nd.w));
-                            }
+                            deposit_thin<THICK>(tL, tA, c, w * __int_as_float(nd.z), w * __int_as_float(nd.w));
                         }
                         if (r2 < tw) {
                             const int c2 = nd2.x + (int)(ent2 & 0xffffu);
                             const float w2 = count_to_float(ent2 >> 16);
-                            atomicAdd(tL + c2, w2 * __int_as_float(nd2.z));
-                            if constexpr (FIXT) {
-                                const unsigned v = tau_units(w2 * __int_as_float(nd2.w));
-                                if (v) atomicAdd(tT + c2, v);
-                            } else {
-                                atomicAdd(tA + c2, w2 * __int_as_float(nd2.w));
-                            }
+                            deposit_thin<THICK>(tL, tA, c2, w2 * __int_as_float(nd2.z), w2 * __int_as_float(nd2.w));
                         }
                     }
                     __syncwarp();
@@ -900,13 +844,7 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
                         const uint32_t ent = __ldg(A.aent + e);
                         const int c = cbase + (int)(ent & 0xffffu);
                         const float w = count_to_float(ent >> 16);
-                        atomicAdd(tL + c, w * bL);
-                        if constexpr (FIXT) {
-                            const unsigned v = tau_units(w * bA);
-                            if (v) atomicAdd(tT + c, v);
-                        } else {
-                            atomicAdd(tA + c, w * bA);
-                        }
+                        deposit_thin<THICK>(tL, tA, c, w * bL, w * bA);
                     }
                 }
             }
@@ -982,15 +920,14 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
             }
             const float w = 1.0f / NPIX;
             for (int h = tid; h < NPIX; h += NT) {
-                gst(tL + h, gld(tL + h) + w * v0.x);
-                // fixed-point tiles: segment 0 holds no depth
-                if constexpr (!FIXT) tst<GA>(tA + h, tld<GA>(tA + h) + w * v0.y);
+                gst(tL + LS * h, gld(tL + LS * h) + w * v0.x);
+                gst(tA + LS * h, gld(tA + LS * h) + w * v0.y);
                 if (THICK && v1.w > 0.0f) {
                     gst(tLk + h, gld(tLk + h) + w * v1.y);
                     gst(tAk + h, gld(tAk + h) + v1.z);
                     gst(tVk + h, gld(tVk + h) + w * v1.w);
                     gst(tQk + h, gld(tQk + h) + w * v1.w);
-                    tst64<true>(flags + h, tld64<true>(flags + h) | fmask);
+                    gst64(flags + h, gld64(flags + h) | fmask);
                 }
             }
         }
@@ -999,7 +936,7 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
         // node, so segment i+1 folds into i (thin content and Q^_thick scaled by R_i^2/R_(i+1)^2,
         // the other thick sums added), from the outside in; one thread per ray
         auto merge_flagged = [&](int h) {
-            const unsigned long long fl = tld64<true>(flags + h);
+            const unsigned long long fl = gld64(flags + h);
             if (fl)
                 for (int i = nb - 2; i >= 0; --i) {
                     if (!((fl >> i) & 1ull)) continue;
@@ -1025,17 +962,11 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
         auto segments = [&](int h, int i0, int i1, float& Fp, float& et, float& ek, float& ts) {
             for (int i = i0; i < i1; ++i) {
                 const int ci = i * ROW + h;
-                const float Lth = gld(tL + ci);
+                const float Lth = gld(tL + LS * ci);
                 const float R2i = __ldg(R2 + i);
                 const float inv_R2 = __fdividef(1.0f, R2i);
-                float Ath, tth;
-                if constexpr (FIXT) {
-                    Ath = (float)tldu<GA>(tT + ci);
-                    tth = Ath * (1.0f / A.tau_scale);  // a power of two: exact scaling
-                } else {
-                    Ath = tld<GA>(tA + ci);
-                    tth = i == 0 ? 0.0f : Ath * inv_R2 * (1.0f / omega);
-                }
+                const float Ath = gld(tA + LS * ci);
+                const float tth = i == 0 ? 0.0f : Ath * inv_R2 * (1.0f / omega);  // eq. tauthin
                 const float Vk = THICK ? gld(tVk + ci) : 0.0f;
                 if (Lth == 0.0f && Ath == 0.0f && Vk == 0.0f) continue;  // empty segment
                 float f = 0.0f, Fk = 0.0f, Akv = 0.0f, tk = 0.0f;
@@ -1112,9 +1043,9 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
                 segments(h, i0, i1, Fp, et, ek, ts);
                 // every part has >= 2 segments: its first two cells of ray h, read only by
                 // this thread, now hold (Fp, transmission) and the part's optical depth
-                gst(tL + i0 * ROW + h, Fp);
-                tst<GA>(tA + i0 * ROW + h, et * ek);
-                gst(tL + (i0 + 1) * ROW + h, ts + (THICK && ek < 1.0f ? -__logf(ek) : 0.0f));
+                gst(tL + LS * (i0 * ROW + h), Fp);
+                gst(tA + LS * (i0 * ROW + h), et * ek);
+                gst(tL + LS * ((i0 + 1) * ROW + h), ts + (THICK && ek < 1.0f ? -__logf(ek) : 0.0f));
             }
             __syncthreads();
             if (tid < NPIX) {
@@ -1122,9 +1053,9 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
                 float Fh = 0.0f, tr = 1.0f, ts = 0.0f;
                 for (int p = 0; p < P; ++p) {
                     const int i0 = p * nb / P;
-                    Fh += tr * gld(tL + i0 * ROW + h);
-                    tr *= tld<GA>(tA + i0 * ROW + h);
-                    ts += gld(tL + (i0 + 1) * ROW + h);
+                    Fh += tr * gld(tL + LS * (i0 * ROW + h));
+                    tr *= gld(tA + LS * (i0 * ROW + h));
+                    ts += gld(tL + LS * ((i0 + 1) * ROW + h));
                 }
                 ray_done(h, Fh, ts);
             }
@@ -1246,11 +1177,11 @@ treeray_status launch_persistent(treeray_ctx* c, K kern, size_t per_warp, int ma
 // ms at 1 GB (192 rays: 436 -> 408 ms).
 constexpr size_t kGlobalTileBudget = (size_t)1 << 30;
 
-// Bytes of one team's slice of global memory (see TileSpace), 16-byte aligned.
-size_t team_tile_bytes(int npix, int nbins, bool thick, bool general) {
-    const bool tau_shared = !thick && !general && npix <= 192;
-    const int nqg = (thick ? 6 : 2) - (tau_shared ? 1 : 0);
-    return align16(align16((size_t)nqg * nbins * tile_row(npix, thick) * 4) + (thick ? (size_t)npix * 8 : 0));
+// Bytes of one team's slice of global memory (the tile, then the thick merge flags),
+// 16-byte aligned.
+size_t team_tile_bytes(int npix, int nbins, bool thick) {
+    const int nq = thick ? 6 : 2;
+    return align16(align16((size_t)nq * nbins * tile_row(npix, thick) * 4) + (thick ? (size_t)npix * 8 : 0));
 }
 
 // Teams of a launch: those asked for, at most as many as keep their tiles within the L2
@@ -1290,15 +1221,13 @@ treeray_status launch_team(treeray_ctx* c, const EvalArgs& a, const EvalArgs* bo
     EvalArgs b = a;
     b.stack_cap = (int)(stack_bytes_for(WPT, layout_lmax, 1) / sizeof(int));
     if (c->stack_limit > 0) b.stack_cap = std::min(b.stack_cap, c->stack_limit);  // test hook
-    constexpr bool TS = TileSpace<NPIX, THICK, GENERAL>::tau_shared;
-    const size_t tile_bytes = team_tile_bytes(NPIX, a.nbins, THICK, GENERAL);
-    const size_t smem = (TS ? align16((size_t)a.nbins * tile_row(NPIX, THICK) * 4) : 0) +
-                        (size_t)WPT * owner_cap_for(NPIX, THICK);
+    const size_t tile_bytes = team_tile_bytes(NPIX, a.nbins, THICK);
+    const size_t smem = (size_t)WPT * owner_cap_for(NPIX, THICK);
     int smem_optin = 0, sms = 0;
     TR_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
     TR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
     if (smem + 2048 > (size_t)smem_optin) {
-        set_error("evaluate: the per-target ray tile (npix x nbins) exceeds shared memory");
+        set_error("evaluate: a team's owner bytes exceed shared memory");
         return TREERAY_EINVAL;
     }
     // persistent grid for n targets: resident blocks of the kernel, and team stacks for them
@@ -1422,12 +1351,9 @@ treeray_status dispatch_team(treeray_ctx* c, bool thick, bool periodic, int wpt,
     return TREERAY_EINVAL;
 }
 
-// The general kernels carry periodic closest copies, mapping at the COL and float thin tiles;
-// the others map isolated grids at the geometric centres with fixed-point thin tiles.
-bool needs_general(const treeray_ctx* c) {
-    const bool thick = c->has_thick || c->force_thick;
-    return c->p.periodic != 0 || c->p.col_mapping != 0 || (!thick && c->tau_q == 0);
-}
+// The general kernels carry periodic closest copies and mapping at the COL; the others map
+// isolated grids at the geometric centres.
+bool needs_general(const treeray_ctx* c) { return c->p.periodic != 0 || c->p.col_mapping != 0; }
 
 treeray_status dispatch_eval(treeray_ctx* c, const EvalArgs& a, cudaStream_t s) {
     return dispatch_team(c, c->has_thick || c->force_thick, needs_general(c), c->wpt, a, nullptr, nullptr, 1,
@@ -1475,7 +1401,6 @@ EvalArgs make_args(treeray_ctx* c, const int32_t* targets, int64_t n) {
     a.periodic = c->p.periodic;
     a.col_mapping = c->p.col_mapping;
     a.inv_s3 = 1.0f / (float)(c->ht.s * c->ht.s * c->ht.s);
-    a.tau_scale = c->tau_q > 0 ? ldexpf(1.0f, c->tau_q) : 0.0f;
     a.u = c->u;
     a.inv_u2 = 1.0 / (c->u * c->u);
     // the stack holds at most 28 leftover groups per level plus one batch of pushes
@@ -1513,13 +1438,13 @@ treeray_status reserve_eval_stacks(treeray_ctx* c, int lmax, cudaStream_t s) {
     return TREERAY_OK;
 }
 
-// The teams' tiles for up to n targets, for each kind of tile (thin or thick, fixed-point or
-// float depth) a launch of this context can use and any team size, so that launches
-// captured in a CUDA graph find them reserved.
-treeray_status reserve_team_tiles_kind(treeray_ctx* c, int64_t n, bool thick, bool general, cudaStream_t s) {
+// The teams' tiles for up to n targets, for each kind of tile (thin or thick) a launch of
+// this context can use and any team size, so that launches captured in a CUDA graph find
+// them reserved.
+treeray_status reserve_team_tiles_kind(treeray_ctx* c, int64_t n, bool thick, cudaStream_t s) {
     int sms = 0;
     TR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
-    const size_t tb = team_tile_bytes(c->p.npix, c->p.nbins, thick, general);
+    const size_t tb = team_tile_bytes(c->p.npix, c->p.nbins, thick);
     // at most 2048 threads, i.e. 32 teams of 2 warps, per SM
     const int64_t teams = tile_blocks(tb, std::min<int64_t>(std::max<int64_t>(n, 1), 32LL * sms), sms);
     return reserve_global_tiles(c, tb * (size_t)teams, s);
@@ -1532,8 +1457,7 @@ treeray_status reserve_team_tiles(treeray_ctx* c, int64_t n, cudaStream_t s) {
         const bool tdep = c->p.kappa_model == 1;
         const bool possible = thick ? (c->has_thick || c->force_thick || tdep) : (!c->has_thick || tdep);
         if (!possible) continue;
-        const bool general = c->p.periodic != 0 || c->p.col_mapping != 0 || (!thick && c->tau_q == 0);
-        const treeray_status rc = reserve_team_tiles_kind(c, n, thick, general, s);
+        const treeray_status rc = reserve_team_tiles_kind(c, n, thick, s);
         if (rc != TREERAY_OK) return rc;
     }
     return TREERAY_OK;
@@ -1794,7 +1718,7 @@ treeray_status treeray_batch_create(const treeray_t* ctxs, int n_boxes, treeray_
         const treeray_status rs = reserve_eval_stacks(b->ctx[g.box[0]], g.max_lmax, nullptr);
         if (rs != TREERAY_OK) return fail(rs);
         const treeray_status rt =
-            reserve_team_tiles_kind(b->ctx[g.box[0]], g.start.back(), &g == &b->g[1], g.periodic, nullptr);
+            reserve_team_tiles_kind(b->ctx[g.box[0]], g.start.back(), &g == &b->g[1], nullptr);
         if (rt != TREERAY_OK) return fail(rt);
         if (cudaMalloc(&g.d_queue, sizeof(unsigned long long)) != cudaSuccess) {
             set_error("batch_create: device allocation failed");

@@ -150,7 +150,6 @@ struct treeray_ctx {
     bool orient_user = false;    // the map came from the caller (else leaf mod k)
     int64_t launches = 0;  // kernels launched by this context
     int wpt = 4;           // warps per target team of the evaluate kernel (autotuned)
-    int tau_q = 0;         // thin tiles: fixed-point optical depth in units of 2^-tau_q (0: float)
     int occ_pct = 100;     // evaluate: resident teams per SM launched, % of the maximum (autotuned)
     int stack_limit = 0;   // test hook: cap on the walk stack's entries (0: the full stack)
     int alloc_fail_at = 0; // test hook: the n-th device allocation from now fails (0: none)
@@ -170,7 +169,7 @@ treeray_status dev_alloc(treeray_ctx* c, void** p, size_t bytes);
 // `lmax` levels below the root; never allocates while `s` is being captured.
 treeray_status reserve_eval_stacks(treeray_ctx* c, int lmax, cudaStream_t s);
 treeray_status reserve_team_tiles(treeray_ctx* c, int64_t n, cudaStream_t s);
-treeray_status reserve_team_tiles_kind(treeray_ctx* c, int64_t n, bool thick, bool general, cudaStream_t s);
+treeray_status reserve_team_tiles_kind(treeray_ctx* c, int64_t n, bool thick, cudaStream_t s);
 // Apply the autotuner's choice cached for a tree of this context's shape, if any.
 void apply_cached_launch_choice(treeray_ctx* c);
 treeray_status build_tree(treeray_ctx* c, const treeray_grid* g, const float* rho, const float* Td,

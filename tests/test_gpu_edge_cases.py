@@ -1,7 +1,8 @@
 """Degenerate inputs against the FP64 oracle, through the C ABI (marked gpu): a grid of one
 cell (the root is a leaf) and of 2^3 cells, an empty target list, a single radial
 segment, the smallest and largest opening angles, a box that is thick everywhere, and
-stars outside the box (their host is the nearest edge cell on both sides)."""
+stars outside the box (their host is the nearest edge cell on both sides), and a target
+list longer than the grid."""
 import numpy as np
 import pytest
 
@@ -82,3 +83,22 @@ def test_stars_outside_the_box(orc):
     w = synth.random_uniform(8, seed=8, n_stars=3)
     w.star_pos = np.array([[-0.1, 0.5, 0.5], [0.3, 1.2, 0.9], [0.5, 0.5, 1.0]]) * w.box_cm
     _check(orc, w)
+
+
+@pytest.mark.parametrize("thick_frac", [0.0, 0.15])
+def test_target_list_longer_than_the_grid(orc, thick_frac):
+    """A target list with repeats, three times the leaf count plus a ragged tail: more
+    teams than the build reserved tiles for (up to one per leaf), so the evaluation grows
+    the teams' global scratch first; every row equals the single evaluation of its leaf
+    and the oracle's value."""
+    w = synth.random_uniform(8, seed=17, thick_frac=thick_frac, n_stars=2)
+    n = w.n_leaves
+    rng = np.random.Generator(np.random.PCG64(18))
+    targets = np.concatenate([np.arange(n), rng.integers(0, n, 2 * n + 7)]).astype(np.int32)
+    ctx, J1, F1 = _check(orc, w)
+    J, F = evaluate(ctx, targets)
+    assert np.abs(J / J1[targets] - 1).max() <= 1e-6  # FP32 reductions in any order
+    assert flux_err(F, F1[targets], J1[targets]).max() <= 1e-5
+    Jr, Fr = orc.Tree(w).evaluate(targets)
+    assert np.abs(J / Jr - 1).max() <= 1e-4
+    assert flux_err(F, Fr, Jr).max() <= 1e-4
