@@ -413,10 +413,9 @@ __host__ __device__ constexpr int owner_cap(bool thick) { return thick ? 160 : 2
 // global memory (red.global.add.f32) is native in L2 and costs the SM one fire-and-forget
 // request. So every team keeps its tile in its own slice of global memory (L2-resident: the
 // slices of one launch take 20-60 MB at 48 rays) and reads it back through L2
-// (ld.global.cg) after the team barrier. Thin tiles interleave each cell's L^ and A^, so
-// that one vector reduction (red.global.add.v2.f32) deposits both; thick tiles keep six
-// arrays (interleaving their four thick quantities into one vector reduction measured
-// slower at 48 rays).
+// (ld.global.cg) after the team barrier. Each cell's thin L^ and A^ are interleaved, so that
+// one vector reduction (red.global.add.v2.f32) deposits both; the four thick quantities keep
+// an array each (interleaving them into one vector reduction measured slower at 48 rays).
 // 768 rays (N_side 8): owner bytes for 2048 entries per warp pass, no batches
 template <int NPIX>
 struct WideRays {
@@ -429,16 +428,8 @@ __device__ __forceinline__ void gst(float* p, float v) { __stcg(p, v); }
 __device__ __forceinline__ void red_add_v2(float* p, float a, float b) {
     asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(a), "f"(b) : "memory");
 }
-// thin deposit of cell c: L^ += l, A^ += ar (thin tiles: one interleaved pair)
-template <bool THICK>
-__device__ __forceinline__ void deposit_thin(float* tL, float* tA, int c, float l, float ar) {
-    if constexpr (THICK) {
-        atomicAdd(tL + c, l);
-        atomicAdd(tA + c, ar);
-    } else {
-        red_add_v2(tL + 2 * c, l, ar);
-    }
-}
+// thin deposit of cell c: L^ += l, A^ += ar (one interleaved pair; tA = tL + 1)
+__device__ __forceinline__ void deposit_thin(float* tL, int c, float l, float ar) { red_add_v2(tL + 2 * c, l, ar); }
 __device__ __forceinline__ unsigned long long gld64(const unsigned long long* p) { return __ldcg(p); }
 __device__ __forceinline__ void gst64(unsigned long long* p, unsigned long long v) { __stcg(p, v); }
 
@@ -527,7 +518,7 @@ __device__ __noinline__ void deposit_tied_copies(const EvalArgs& A, const int32_
             const int h = (int)(ent & 0xffffu);
             const int c = i * tile_row(NPIX, THICK) + h;
             const float w = count_to_float(ent >> 16);
-            deposit_thin<THICK>(tL, tA, c, w * bL, w * bA);
+            deposit_thin(tL, c, w * bL, w * bA);
             if (thick) {
                 const float wn = w * inv_s3;
                 atomicAdd(tLk + c, wn * v1.y * wt);
@@ -566,16 +557,15 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
     constexpr int ROW = tile_row(NPIX, THICK);
     const int cells = nb * ROW;
     // layout of the team's slice of global memory (16-byte aligned parts):
-    //   thin: (L^, A^) pairs [nb][ROW][2] f32
-    //   thick: L^, A^ thin, L^, A^, V^, Q^ thick [nb][ROW] f32 each, then the merge flags
-    //   [NPIX] u64
+    //   thin (L^, A^) pairs [nb][ROW][2] f32 | THICK: L^, A^, V^, Q^ thick [nb][ROW] f32
+    //   each, then the merge flags [NPIX] u64
     // shared memory: per warp entry owners u8[owner_cap]
     // The team's stack of child groups is this block's slice of a global scratch array:
     // it stays in L1, and leaving it out of shared memory lets more teams share an SM.
     constexpr int nq = THICK ? 6 : 2;
-    constexpr int LS = THICK ? 1 : 2;  // stride of a cell's L^ and A^ (thin: interleaved)
+    constexpr int LS = 2;  // stride of a cell's L^ and A^ (interleaved)
     float* tL = a.gtile + (size_t)blockIdx.x * a.gtile_stride;
-    float* tA = THICK ? tL + cells : tL + 1;
+    float* tA = tL + 1;
     float* tLk = tL + 2 * cells;  // thick tiles only
     float* tAk = tLk + cells;
     float* tVk = tAk + cells;
@@ -830,12 +820,12 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
                         if (r < tw) {
                             const int c = nd.x + (int)(ent & 0xffffu);
                             const float w = count_to_float(ent >> 16);
-                            deposit_thin<THICK>(tL, tA, c, w * __int_as_float(nd.z), w * __int_as_float(nd.w));
+                            deposit_thin(tL, c, w * __int_as_float(nd.z), w * __int_as_float(nd.w));
                         }
                         if (r2 < tw) {
                             const int c2 = nd2.x + (int)(ent2 & 0xffffu);
                             const float w2 = count_to_float(ent2 >> 16);
-                            deposit_thin<THICK>(tL, tA, c2, w2 * __int_as_float(nd2.z), w2 * __int_as_float(nd2.w));
+                            deposit_thin(tL, c2, w2 * __int_as_float(nd2.z), w2 * __int_as_float(nd2.w));
                         }
                     }
                     __syncwarp();
@@ -844,7 +834,7 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
                         const uint32_t ent = __ldg(A.aent + e);
                         const int c = cbase + (int)(ent & 0xffffu);
                         const float w = count_to_float(ent >> 16);
-                        deposit_thin<THICK>(tL, tA, c, w * bL, w * bA);
+                        deposit_thin(tL, c, w * bL, w * bA);
                     }
                 }
             }
@@ -942,13 +932,15 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
                     if (!((fl >> i) & 1ull)) continue;
                     const int c0 = i * ROW + h, c1 = (i + 1) * ROW + h;
                     const float T = __ldg(R2 + i) / __ldg(R2 + i + 1);
-                    gst(tL + c0, gld(tL + c0) + T * gld(tL + c1));
-                    gst(tA + c0, gld(tA + c0) + T * gld(tA + c1));
+                    gst(tL + LS * c0, gld(tL + LS * c0) + T * gld(tL + LS * c1));
+                    gst(tA + LS * c0, gld(tA + LS * c0) + T * gld(tA + LS * c1));
                     gst(tQk + c0, gld(tQk + c0) + T * gld(tQk + c1));
                     gst(tLk + c0, gld(tLk + c0) + gld(tLk + c1));
                     gst(tAk + c0, gld(tAk + c0) + gld(tAk + c1));
                     gst(tVk + c0, gld(tVk + c0) + gld(tVk + c1));
-                    for (float* q : {tL, tA, tQk, tLk, tAk, tVk}) gst(q + c1, 0.0f);
+                    gst(tL + LS * c1, 0.0f);
+                    gst(tA + LS * c1, 0.0f);
+                    for (float* q : {tQk, tLk, tAk, tVk}) gst(q + c1, 0.0f);
                 }
         };
         // ---- integrate each ray from the inside out
