@@ -18,8 +18,8 @@ static thread_local std::string g_err;
 void set_error(const std::string& msg) { g_err = msg; }
 
 void free_tables(DeviceTables& t) {
-    void* ptrs[] = {t.nhat, t.alpha_off, t.alpha_ent, t.bin_thr, t.R2,   t.Rh, t.Rd, t.lvlp,
-                    t.open_max, t.str_lo, t.str_hi, t.scal, t.err, t.queue};
+    void* ptrs[] = {t.nhat, t.alpha_off, t.alpha_pair, t.alpha_ent, t.bin_thr, t.R2, t.Rh, t.Rd,
+                    t.lvlp, t.open_max, t.str_lo, t.str_hi, t.scal, t.err, t.queue};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     t = DeviceTables{};
@@ -97,6 +97,17 @@ treeray_status ensure_orient_map(treeray_ctx* c, cudaStream_t s) {
 //   straddle   : d^2 >= ceil((R_j + s)^2) -> the node's near edge lies beyond R_j;
 //                d^2 >= ceil((R_j - s)^2) (0 when R_j <= s) -> its far edge does,
 //                s = sqrt(3)/2 E (half the node's diagonal)
+namespace {
+// (first entry, end) of every key of every orientation: one 8-byte load per accepted node in
+// the evaluation instead of two 4-byte ones
+__global__ void k_alpha_pairs(const int32_t* off, int2* pair, int64_t keys, int64_t stride, int64_t k) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= keys * k) return;
+    const int64_t o = i / keys, key = i - o * keys;
+    pair[i] = make_int2(off[o * stride + key], off[o * stride + key + 1]);
+}
+}  // namespace
+
 treeray_status upload_tables(treeray_ctx* c, cudaStream_t s) {
     const int L = c->lmax, nb = c->p.nbins;
     if (c->tab_lmax == L && c->tab_amr == c->amr) {
@@ -114,6 +125,19 @@ treeray_status upload_tables(treeray_ctx* c, cudaStream_t s) {
         treeray_status rc;
         if ((rc = upload(c, &c->dt.alpha_off, c->ht.alpha_off, s)) != TREERAY_OK) return rc;
         if ((rc = upload(c, &c->dt.alpha_ent, c->ht.alpha_ent, s)) != TREERAY_OK) return rc;
+        const int64_t W = 2 * c->ht.D + 1, keys = W * W * W, stride = keys + 1;
+        const int64_t k = (int64_t)c->ht.alpha_off.size() / stride;
+        if (c->dt.alpha_pair) cudaFree(c->dt.alpha_pair);
+        c->dt.alpha_pair = nullptr;
+        if ((rc = dev_alloc(c, (void**)&c->dt.alpha_pair, sizeof(int2) * (size_t)std::max<int64_t>(1, keys * k))) !=
+            TREERAY_OK)
+            return rc;
+        if (keys * k > 0) {
+            k_alpha_pairs<<<(unsigned)((keys * k + 255) / 256), 256, 0, s>>>(c->dt.alpha_off, c->dt.alpha_pair, keys,
+                                                                             stride, k);
+            c->launches += 1;
+            TR_CUDA(cudaGetLastError());
+        }
     }
     std::vector<int64_t> thr((size_t)(L + 1) * nb), omax(L + 1);
     std::vector<float> R2((size_t)(L + 1) * nb), Rh((size_t)(L + 1) * nb);

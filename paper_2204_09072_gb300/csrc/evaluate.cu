@@ -41,6 +41,7 @@ struct __align__(16) EvalArgs {
     const double* __restrict__ jsrc;
     const float* __restrict__ nhat;     // [orientations][npix][3]
     const int32_t* __restrict__ aoff;   // [orientations][aoff_stride]
+    const int2* __restrict__ apair;     // [orientations][aoff_stride - 1] (first entry, end)
     const uint32_t* __restrict__ aent;
     const uint8_t* __restrict__ orient;  // per leaf (caller order): its ray orientation, or null
     int64_t aoff_stride;
@@ -581,6 +582,7 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
     __shared__ int s_sp, s_overflow;
     __shared__ long long s_q;
     __shared__ const int32_t* s_aoff;  // the target's orientation: angular-kernel table
+    __shared__ const int2* s_apair;
     __shared__ const float* s_nhat;    // and ray directions
     __shared__ float s_red[7][WPT];  // J, then (hi, lo) pairs of F_x, F_y, F_z
     __shared__ float s_tau[2][WPT];
@@ -657,6 +659,7 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
             }
             const int o = A.orient ? (int)A.orient[cell] : 0;
             s_aoff = A.aoff + (int64_t)o * A.aoff_stride;
+            s_apair = A.apair + (int64_t)o * (A.aoff_stride - 1);
             s_nhat = A.nhat + 3 * NPIX * o;
         }
         __syncthreads();
@@ -753,8 +756,8 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
                     atomicOr(A.err, kErrAlphaKey);
                 } else {
                     const int idx = ((Kz + A.D) * W + (Ky + A.D)) * W + (Kx + A.D);
-                    const int32_t* aoff = s_aoff;
-                    const int e0 = __ldg(aoff + idx), e1 = __ldg(aoff + idx + 1);
+                    const int2 ee = __ldg(s_apair + idx);
+                    const int e0 = ee.x, e1 = ee.y;
                     if (e1 == e0) atomicOr(A.err, kErrAlphaKey);
                     // a node without thin material (all of it thick) adds nothing to the thin
                     // tile: its entries are left out of the warp's thin deposits
@@ -1368,6 +1371,7 @@ EvalArgs make_args(treeray_ctx* c, const int32_t* targets, int64_t n) {
     a.jsrc = c->tree.jsrc;
     a.nhat = c->dt.nhat;
     a.aoff = c->dt.alpha_off;
+    a.apair = c->dt.alpha_pair;
     a.aent = c->dt.alpha_ent;
     a.orient = c->rot.empty() ? nullptr : c->orient;
     a.aoff_stride = (int64_t)(2 * c->ht.D + 1) * (2 * c->ht.D + 1) * (2 * c->ht.D + 1) + 1;

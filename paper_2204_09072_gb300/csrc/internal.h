@@ -97,6 +97,7 @@ struct DeviceTree {
 struct DeviceTables {
     float* nhat = nullptr;
     int32_t* alpha_off = nullptr;
+    int2* alpha_pair = nullptr;     // [orientations][(2D+1)^3] (first entry, end) of each key
     uint32_t* alpha_ent = nullptr;
     int64_t* bin_thr = nullptr;     // [lmax+1][nbins] ceil(R_i^2), i>=1 used
     float* R2 = nullptr;            // [lmax+1][nbins] R_i^2 (half-cells^2)
