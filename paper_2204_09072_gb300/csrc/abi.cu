@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <limits>
 #include <string>
 #include <vector>
 
@@ -18,8 +19,8 @@ static thread_local std::string g_err;
 void set_error(const std::string& msg) { g_err = msg; }
 
 void free_tables(DeviceTables& t) {
-    void* ptrs[] = {t.nhat, t.alpha_off, t.alpha_pair, t.alpha_ent, t.bin_thr, t.R2, t.Rh, t.Rd,
-                    t.lvlp, t.open_max, t.str_lo, t.str_hi, t.scal, t.err, t.queue};
+    void* ptrs[] = {t.nhat, t.alpha_off, t.alpha_pair, t.alpha_ent, t.bin_thr, t.bin_thr2, t.R2, t.Rh,
+                    t.Rd, t.lvlp, t.open_max, t.str_lo, t.str_hi, t.scal, t.err, t.queue};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     t = DeviceTables{};
@@ -190,6 +191,16 @@ treeray_status upload_tables(treeray_ctx* c, cudaStream_t s) {
     }
     treeray_status rc;
     if ((rc = upload(c, &c->dt.bin_thr, thr, s)) != TREERAY_OK) return rc;
+    {  // neighbouring thresholds side by side: one 16-byte load per segment decision
+        std::vector<longlong2> thr2(thr.size());
+        for (int lt = 0; lt <= L; ++lt)
+            for (int i = 0; i < nb; ++i) {
+                const size_t k = (size_t)lt * nb + i;
+                thr2[k].x = thr[k];
+                thr2[k].y = i + 1 < nb ? thr[k + 1] : std::numeric_limits<long long>::max();
+            }
+        if ((rc = upload(c, &c->dt.bin_thr2, thr2, s)) != TREERAY_OK) return rc;
+    }
     if ((rc = upload(c, &c->dt.R2, R2, s)) != TREERAY_OK) return rc;
     if ((rc = upload(c, &c->dt.Rh, Rh, s)) != TREERAY_OK) return rc;
     if ((rc = upload(c, &c->dt.Rd, Rd, s)) != TREERAY_OK) return rc;

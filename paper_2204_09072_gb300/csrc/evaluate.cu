@@ -46,6 +46,7 @@ struct __align__(16) EvalArgs {
     const uint8_t* __restrict__ orient;  // per leaf (caller order): its ray orientation, or null
     int64_t aoff_stride;
     const int64_t* __restrict__ bin_thr;
+    const longlong2* __restrict__ bin_thr2;  // (thr[i], thr[i+1]) side by side
     const float* __restrict__ R2;
     const float* __restrict__ Rh;       // [target level][nbins] R_i (half-cells)
     const double* __restrict__ Rd;      // [target level][nbins] R_i in FP64 (COL decisions)
@@ -105,6 +106,20 @@ __device__ __forceinline__ int alpha_key(int o, int elog) {
 
 // Largest j in [1, nb-1] with d2 >= arr[j] (arr non-decreasing), else 0, starting from a
 // guess: the fix-up loops make the result exact whatever the guess.
+// The same on the threshold pairs (thr[i], thr[i+1]) of one level: a correct guess costs one
+// 16-byte load.
+__device__ __forceinline__ int fixup_pair(int g, int64_t d2, const longlong2* __restrict__ pr, int nb) {
+    g = max(0, min(g, nb - 1));
+    const longlong2 t = __ldg(pr + g);
+    if (d2 >= t.y) {
+        do ++g;
+        while (g + 1 < nb && d2 >= __ldg(pr + g).y);
+    } else if (g > 0 && d2 < t.x) {
+        do --g;
+        while (g > 0 && d2 < __ldg(pr + g).x);
+    }
+    return g;
+}
 __device__ __forceinline__ int fixup(int g, int64_t d2, const int64_t* __restrict__ arr, int nb) {
     g = max(0, min(g, nb - 1));
     while (g + 1 < nb && d2 >= __ldg(arr + g + 1)) ++g;
@@ -637,7 +652,7 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
         const int4 tg = A.geo[tnode];
         const int tx = tg.x, ty = tg.y, tz = tg.z & 0xffffff;
         const int tl = tg.z >> 24;
-        const int64_t* thr = A.bin_thr + (int64_t)tl * nb;
+        const longlong2* thr2 = A.bin_thr2 + (int64_t)tl * nb;
         const float* R2 = A.R2 + (int64_t)tl * nb;
         const float2 lp = __ldg(A.lvlp + tl);
 
@@ -744,7 +759,7 @@ __device__ __forceinline__ void evaluate_team(const EvalArgs& a, const BatchArgs
                     cilo = cm.ilo;
                     cihi = cm.ihi;
                 } else {
-                    i = fixup(guess_bin(fd2, lp), d2, thr, nb);
+                    i = fixup_pair(guess_bin(fd2, lp), d2, thr2, nb);
                     Kx = alpha_key(ox, elog);
                     Ky = alpha_key(oy, elog);
                     Kz = alpha_key(oz, elog);
@@ -1376,6 +1391,7 @@ EvalArgs make_args(treeray_ctx* c, const int32_t* targets, int64_t n) {
     a.orient = c->rot.empty() ? nullptr : c->orient;
     a.aoff_stride = (int64_t)(2 * c->ht.D + 1) * (2 * c->ht.D + 1) * (2 * c->ht.D + 1) + 1;
     a.bin_thr = c->dt.bin_thr;
+    a.bin_thr2 = c->dt.bin_thr2;
     a.R2 = c->dt.R2;
     a.Rh = c->dt.Rh;
     a.Rd = c->dt.Rd;

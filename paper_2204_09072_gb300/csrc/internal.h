@@ -100,6 +100,7 @@ struct DeviceTables {
     int2* alpha_pair = nullptr;     // [orientations][(2D+1)^3] (first entry, end) of each key
     uint32_t* alpha_ent = nullptr;
     int64_t* bin_thr = nullptr;     // [lmax+1][nbins] ceil(R_i^2), i>=1 used
+    longlong2* bin_thr2 = nullptr;  // [lmax+1][nbins] (thr[i], thr[i+1]), thr[nbins] = INT64_MAX
     float* R2 = nullptr;            // [lmax+1][nbins] R_i^2 (half-cells^2)
     float* Rh = nullptr;            // [lmax+1][nbins] R_i (half-cells)
     double* Rd = nullptr;           // [lmax+1][nbins] R_i in FP64 (decisions at the COL)
