@@ -6,13 +6,14 @@
 // index, the angular-kernel key and straddled segment boundaries are decided in exact
 // integer arithmetic on the squared centre distance (thresholds built on the host in FP64).
 //
-// Deposit (Secs. 4.2.1-4.2.2): per (segment i, ray h) shared-memory accumulators
+// Deposit (Secs. 4.2.1-4.2.2): per (segment i, ray h) accumulators in the team's slice of
+// global memory, added to by reductions in L2
 //   thin:  L^ += a b L,  A^ += a b A~          (b = R_i^2 / r_COL^2, a = alpha_node(h))
 //   thick: L^ += a L_V,  A^ += A~,  V^ += a V,  Q^ += a b V, plus straddle flags.
-// Integration (Sec. 4.3): segments inside out per ray in FP32, with the optical-depth
-// prefix and the flux sums carried as float pairs (error-free transformations), so the
-// GB300's slow FP64 pipe is not on the path. Finalization (Sec. 4.4): J = sum_h F^h / 4 pi,
-// F = -sum_h F^h n^h, converted to CGS in FP64.
+// Integration (Sec. 4.3): segments inside out per ray in FP32, the transmission carried as
+// a product of per-segment e^-tau and the flux sums as float pairs (error-free
+// transformations), so the GB300's slow FP64 pipe is not on the path. Finalization
+// (Sec. 4.4): J = sum_h F^h / 4 pi, F = -sum_h F^h n^h, converted to CGS in FP64.
 //
 // Internal units: lengths in half-cells of the finest level (u cm), luminosities in
 // L_scale erg/s; fluxes come out in L_scale / u^2 and are converted to CGS at the end.
@@ -548,16 +549,17 @@ __device__ __noinline__ void deposit_tied_copies(const EvalArgs& A, const int32_
 }
 
 // Evaluation kernel: a team of WPT warps per target shares one walk stack (its block's
-// slice of a global scratch array, L1-resident) and one (segment x ray) tile in shared
-// memory; the block processes one target at a time and takes the next from a global
-// work counter (persistent grid).
+// slice of a global scratch array, L1-resident) and one (segment x ray) tile (its block's
+// slice of another, L2-resident); the block processes one target at a time and takes the
+// next from a global work counter (persistent grid).
 //   walk:    each step the team pops up to 4 WPT child groups (32 WPT nodes), tests them,
 //            appends the opened nodes' child groups to the stack (one shared-memory
 //            atomic per warp) and maps the accepted ones (segment, beta, angular key);
 //   deposit: the warp's thin deposits are spread one angular-kernel entry per lane, in
 //            child-major node order so that sibling nodes, which often hit the same cell,
-//            fall into different rounds; shared-memory atomics into the tile; thick
-//            deposits follow in a second pass, also one entry per lane;
+//            fall into different rounds; one L2 vector reduction of the cell's (L^, A^)
+//            pair per entry; thick deposits follow in a second pass, also one entry per
+//            lane;
 //   rays:    threads integrate the rays' segments inside out (thin tiles with spare
 //            threads cut each ray into consecutive parts joined by their transmission),
 //            then the team reduces J and F.
@@ -1159,7 +1161,7 @@ treeray_status launch_persistent(treeray_ctx* c, K kern, size_t per_warp, int ma
     int warps = max_warps;
     while (warps > 1 && per_warp * warps > (size_t)smem_optin) --warps;
     if (per_warp * warps > (size_t)smem_optin) {
-        set_error("evaluate: the per-target ray tile (npix x nbins) exceeds shared memory");
+        set_error("evaluate: a warp's walk scratch exceeds shared memory");
         return TREERAY_EINVAL;
     }
     const size_t smem = per_warp * warps;
