@@ -157,10 +157,9 @@ def test_evaluate_768_rays(orc, case):
 
 
 def test_evaluate_dense_thin_32(orc):
-    """Thin tiles of the isolated kernels keep each segment's optical depth in fixed point
-    (2^-20 per unit at this depth): every cell as close to the thick class as it gets
-    (tau_b in [0.5, 0.99]) gives the deepest segments a thin grid can have; every target
-    against the oracle."""
+    """The deepest segments a thin grid can have: every cell as close to the thick class as
+    it gets (tau_b in [0.5, 0.99]), each segment's A^ summed by FP32 reductions in any
+    order; every target against the oracle."""
     w = synth.random_uniform(32, seed=12, thick_frac=0.0, n_stars=3)
     rng = np.random.Generator(np.random.PCG64(13))
     dx = w.box_cm / 32
@@ -172,10 +171,11 @@ def test_evaluate_dense_thin_32(orc):
 
 
 def test_deep_thin_optical_depth_prefix(orc):
-    """Rays whose thin optical-depth prefix passes 50 (where a plain FP32 sum would lose the
-    small terms): 128^3 thin cells at tau_b 0.9-0.99 give central targets rays of tau 60-110.
-    The prefix is a float pair (~48 bits) and the segment depths are fixed point; 1500
-    targets, among them those with the deepest rays, against the oracle."""
+    """Rays whose thin optical depth passes 50 (where a running FP32 sum of depths would lose
+    the small terms): 128^3 thin cells at tau_b 0.9-0.99 give central targets rays of tau
+    60-110. The transmission is carried as a product of per-segment e^-tau, which keeps
+    its relative precision at any depth; 1500 targets, among them those with the deepest
+    rays, against the oracle."""
     import torch
     w = synth.random_uniform(128, seed=61, thick_frac=0.0, n_stars=2)
     dx = w.box_cm / 128
